@@ -1,0 +1,205 @@
+/*
+ * msgemm -- masked sparse matrix-matrix products on NVIDIA GB300 (sm_103a).
+ *
+ * The operation (Sec. 2 of "Parallel Algorithms for Masked Sparse
+ * Matrix-Matrix Products"): C = M .* (A B) on a semiring, where only the
+ * pattern of the mask M is used; its complemented form C = !M .* (A B) keeps
+ * the entries the mask does NOT hold (Sec. 1; complement paragraphs of
+ * Sec. 5.2 and 5.5).  An entry C_ij exists iff the mask allows (i, j) and at
+ * least one k has both A_ik and B_kj stored (the SET state of the accumulator
+ * interface, Sec. 5.1); entries whose numeric sum is zero are kept.  Output
+ * rows have ascending column indices.  The product is one-phase (Sec. 6): the
+ * output is written into room sized by the mask and then compacted, with no
+ * separate symbolic pass.
+ *
+ * Conventions for every entry point
+ *  - Matrices are CSR with int32 row pointers and column indices; within a row
+ *    the column indices are strictly ascending (sorted, no duplicates);
+ *    nnz < 2^31.  Input pointers are DEVICE pointers, borrowed for the call.
+ *  - Values: float for MSGEMM_PLUS_TIMES_F32, int64_t for the two int64
+ *    semirings.  PLUS_PAIR ignores input values (they may be NULL).  Mask
+ *    values are never read.
+ *  - Shapes: M is m x n, A is m x k, B is k x n; any of m, n, k may be 0.
+ *  - Every call is asynchronous on the handle's stream and returns as soon as
+ *    its work is enqueued, except where a call says it synchronises.  Errors
+ *    found on the host are returned at once and leave no work enqueued.  Errors
+ *    found by kernels (invalid input under validation, a bounded wait that
+ *    ran out) set a device error word that msgemm_sync_status() reports.
+ *  - Output arrays are allocated through the handle's allocation callback and
+ *    then belong to the caller, who frees them (with the matching free).
+ *  - A handle is not thread-safe; use one handle per host thread and stream.
+ */
+#ifndef MSGEMM_H
+#define MSGEMM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MSGEMM_OK = 0,
+    MSGEMM_ERR_INVALID = 1,      /* NULL pointer, negative size, bad option, bad rowptr/column */
+    MSGEMM_ERR_SHAPE = 2,        /* operand shapes do not chain */
+    MSGEMM_ERR_UNSORTED = 3,     /* a row is not strictly ascending (found by validation) */
+    MSGEMM_ERR_UNSUPPORTED = 4,  /* combination the library does not implement */
+    MSGEMM_ERR_OOM = 5,          /* the allocation callback returned NULL */
+    MSGEMM_ERR_OVERFLOW = 6,     /* a size does not fit the int32 index space */
+    MSGEMM_ERR_CUDA = 7,         /* a CUDA runtime call failed */
+    MSGEMM_ERR_TIMEOUT = 8       /* a bounded device-side wait ran out */
+} msgemm_status;
+
+typedef enum {
+    MSGEMM_PLUS_TIMES_F32 = 0,   /* (+, *) on float; accumulation in float */
+    MSGEMM_PLUS_TIMES_I64 = 1,   /* (+, *) on int64_t, wrapping modulo 2^64 */
+    MSGEMM_PLUS_PAIR_I64 = 2     /* (+, pair): every product counts 1; result int64_t */
+} msgemm_semiring;
+
+/* Accumulator families (Sec. 4-5) that the row binning may pick per row. */
+typedef enum {
+    MSGEMM_ACC_AUTO = 0,  /* per-row choice by the binning policy (default) */
+    MSGEMM_ACC_MSA = 1,   /* masked sparse accumulator: dense states + values (Sec. 5.2) */
+    MSGEMM_ACC_HASH = 2,  /* hash table keyed by the mask's columns (Sec. 5.3) */
+    MSGEMM_ACC_MCA = 3,   /* mask-compressed accumulator indexed by rank in the mask row (Sec. 5.4) */
+    MSGEMM_ACC_DOT = 4    /* pull: masked inner products A_i* . B_*j (Sec. 4.1) */
+} msgemm_accumulator;
+
+/* Options for msgemm_set_option. */
+typedef enum {
+    MSGEMM_OPT_FORCE_ACCUM = 1,   /* value: msgemm_accumulator.  Rows that do not fit the
+                                     forced family's per-row shared-memory form use the
+                                     column-tiled MSA; MCA and DOT do not exist for
+                                     complemented masks, where AUTO is used instead. */
+    MSGEMM_OPT_VALIDATE = 2,      /* value 0/1 (default 0): check every input on the device
+                                     (row pointers, column range, strict order) before the
+                                     product runs; synchronises once per call and returns
+                                     MSGEMM_ERR_INVALID / MSGEMM_ERR_UNSORTED without running
+                                     the product.  Without validation, out-of-range indices
+                                     are undefined behaviour. */
+    MSGEMM_OPT_DOT = 3            /* value 0/1 (default 1): allow the pull (DOT) kernel in AUTO */
+} msgemm_option;
+
+/* Input CSR matrix (device pointers, borrowed). */
+typedef struct {
+    int32_t nrows, ncols;
+    int64_t nnz;                 /* == rowptr[nrows]; must be < 2^31 */
+    const int32_t *rowptr;       /* nrows + 1 entries */
+    const int32_t *colidx;       /* nnz entries, strictly ascending per row */
+    const void *values;          /* nnz entries, or NULL (plus-pair, masks) */
+} msgemm_csr;
+
+/* Output CSR matrix.  The library fills every field; the arrays come from the
+ * handle's allocation callback and belong to the caller afterwards.
+ * capacity is the room of colidx/values; the true entry count is *d_nnz
+ * (a device int64) and rowptr[nrows] (device). */
+typedef struct {
+    int32_t nrows, ncols;
+    int32_t *rowptr;
+    int32_t *colidx;
+    void *values;
+    int64_t capacity;
+    int64_t *d_nnz;
+} msgemm_csr_out;
+
+/* Device memory callbacks: alloc returns a device pointer (256-byte aligned)
+ * or NULL; free releases it.  Both are called on the host from inside
+ * library calls, never from a kernel or a stream callback. */
+typedef void *(*msgemm_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*msgemm_free_fn)(void *ptr, void *ctx);
+
+typedef struct msgemm_handle msgemm_handle;
+
+/* Creates a handle bound to the current CUDA device and to `stream` (a
+ * cudaStream_t; NULL = the legacy default stream).  With alloc/free NULL the
+ * library uses cudaMalloc/cudaFree.  Workspace (row scores, bins, temporary
+ * output room, tile cursors) belongs to the handle and is reused; a free
+ * callback must honour stream order (torch's caching allocator does). */
+msgemm_status msgemm_create(msgemm_handle **handle, void *stream,
+                            msgemm_alloc_fn alloc, msgemm_free_fn free_fn, void *ctx);
+
+/* Rebinds the handle to another stream (synchronises the old one first). */
+msgemm_status msgemm_set_stream(msgemm_handle *handle, void *stream);
+
+msgemm_status msgemm_set_option(msgemm_handle *handle, msgemm_option option, int64_t value);
+
+/* C = M .* (A B) (complement == 0) or C = !M .* (A B) (complement != 0),
+ * Sec. 2.  Allocates C: rowptr (m + 1), colidx and values with
+ * capacity = nnz(M) for a plain mask -- no host synchronisation -- and, for a
+ * complemented mask, capacity = the exact entry count, which costs two
+ * host synchronisations (one for the temporary room, one for the count).
+ * Pipeline: row binning by flops and mask size, per-bin accumulator kernels
+ * (MSA / hash / MCA / pull-dot with per-row tables in shared memory; a
+ * column-tiled shared-memory MSA for rows too heavy for one table), then
+ * compaction into canonical CSR. */
+msgemm_status msgemm_run(msgemm_handle *handle, const msgemm_csr *M, int complement,
+                         const msgemm_csr *A, const msgemm_csr *B, msgemm_semiring semiring,
+                         msgemm_csr_out *C);
+
+/* Gradients of l = sum_ij G_ij C_ij for C = M .* (A B), plus-times fp32:
+ *   dA = pattern(A) .* (G B^T)   -> dA_vals[t] for A's t-th stored entry
+ *   dB = pattern(B) .* (A^T G)   -> dB_vals[t] for B's t-th stored entry
+ * G is m x n, fp32, stored on the pattern of C (any pattern contained in M's
+ * gives the same result).  Both are masked products run by the same
+ * accumulators: dA as pull (DOT) over rows of G and rows of B, dB as push over
+ * rows of A^T (built by a transpose kernel) and rows of G.  dA_vals / dB_vals
+ * are caller-allocated device float arrays of nnz(A) / nnz(B) entries; either
+ * may be NULL to skip it.  Returns UNSUPPORTED for any other semiring. */
+msgemm_status msgemm_backward(msgemm_handle *handle, const msgemm_csr *A, const msgemm_csr *B,
+                              const msgemm_csr *G, msgemm_semiring semiring,
+                              float *dA_vals, float *dB_vals);
+
+/* nprod independent products C[p] = M[p] .* (A[p] B[p]) (or complemented per
+ * complement[p], which may be NULL for all-plain), one semiring.  All binning,
+ * accumulation and compaction for all products run in one pipeline whose
+ * accumulation phase is ONE persistent kernel that pulls (product, row) work
+ * items from a device queue.  With use_graph != 0 the pipeline is captured once
+ * into a CUDA graph and replayed when called again with identical arguments
+ * (same pointers and sizes).  Each C[p] is allocated as in msgemm_run; a
+ * complemented product synchronises the host as msgemm_run does. */
+msgemm_status msgemm_run_batched(msgemm_handle *handle, int nprod, const msgemm_csr *M,
+                                 const int *complement, const msgemm_csr *A, const msgemm_csr *B,
+                                 msgemm_semiring semiring, msgemm_csr_out *C, int use_graph);
+
+/* Times each accumulator family on the given batch (synchronises), keeps the
+ * fastest per row class in the handle's policy, and, when cache_path is not
+ * NULL, writes the table as JSON keyed by device name and semiring (and
+ * reads it back instead of timing when the file already holds that key). */
+msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr *M,
+                              const int *complement, const msgemm_csr *A, const msgemm_csr *B,
+                              msgemm_semiring semiring, const char *cache_path);
+
+/* Transpose (CSR of A^T).  At is allocated like an output (capacity nnz(A)).
+ * Column indices within a row of A^T are NOT sorted unless sorted != 0
+ * (sorting costs an extra segmented sort pass). */
+msgemm_status msgemm_transpose(msgemm_handle *handle, const msgemm_csr *A, int value_bytes,
+                               int sorted, msgemm_csr_out *At);
+
+/* *d_sum (device, 8 bytes) = sum of C's values: int64 wrapping for the int64
+ * semirings (the triangle count of Sec. 8.2 for C = L .* (L L) on plus-pair),
+ * fp64 accumulation rounded into a double for plus-times fp32. */
+msgemm_status msgemm_reduce_sum(msgemm_handle *handle, const msgemm_csr_out *C,
+                                msgemm_semiring semiring, void *d_sum);
+
+/* Synchronises the handle's stream and reports (then clears) the device error
+ * word: MSGEMM_ERR_INVALID / _UNSORTED for a validation failure,
+ * MSGEMM_ERR_TIMEOUT for a bounded wait that ran out, MSGEMM_ERR_CUDA for a
+ * failed launch or copy. */
+msgemm_status msgemm_sync_status(msgemm_handle *handle);
+
+/* Copies a NUL-terminated description of the last error into buf. */
+msgemm_status msgemm_last_error_detail(msgemm_handle *handle, char *buf, size_t len);
+
+/* Per-kind row counts of the last msgemm_run / msgemm_run_batched binning
+ * (synchronises): counts[kind] for kind < min(n, msgemm_num_kinds()). */
+int msgemm_num_kinds(void);
+msgemm_status msgemm_bin_counts(msgemm_handle *handle, int64_t *counts, int n);
+
+/* Frees the workspace and the handle (synchronises its stream). */
+void msgemm_destroy(msgemm_handle *handle);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSGEMM_H */

@@ -1,0 +1,306 @@
+"""ctypes binding of the C ABI in include/msgemm.h (argument marshalling only).
+
+Every step of the computation runs in the CUDA library ``libmsgemm.so``; this
+module converts torch tensors to the ABI's plain structs, supplies torch's
+caching allocator as the library's allocation callbacks, and wraps outputs
+back into tensors.  A missing library is an error: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+from . import _build
+
+PLUS_TIMES_F32, PLUS_TIMES_I64, PLUS_PAIR_I64 = 0, 1, 2
+SEMIRINGS = {"plus_times_f32": PLUS_TIMES_F32, "plus_times_i64": PLUS_TIMES_I64, "plus_pair_i64": PLUS_PAIR_I64}
+ACC_AUTO, ACC_MSA, ACC_HASH, ACC_MCA, ACC_DOT = 0, 1, 2, 3, 4
+ACCUMULATORS = {"auto": 0, "msa": 1, "hash": 2, "mca": 3, "dot": 4}
+OPT_FORCE_ACCUM, OPT_VALIDATE, OPT_DOT = 1, 2, 3
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_SHAPE", 3: "ERR_UNSORTED", 4: "ERR_UNSUPPORTED", 5: "ERR_OOM",
+          6: "ERR_OVERFLOW", 7: "ERR_CUDA", 8: "ERR_TIMEOUT"}
+KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "dot_w", "dot_b",
+              "chash_w", "chash_b", "cmsa_t"]
+
+# Exported symbols that include/msgemm.h declares.
+EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_run", "msgemm_backward",
+           "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
+           "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
+           "msgemm_destroy"]
+
+
+class MsgemmError(RuntimeError):
+    def __init__(self, status: int, detail: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {detail}")
+
+
+class Csr(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("nnz", C.c_int64),
+                ("rowptr", C.c_void_p), ("colidx", C.c_void_p), ("values", C.c_void_p)]
+
+
+class CsrOut(C.Structure):
+    _fields_ = [("nrows", C.c_int32), ("ncols", C.c_int32), ("rowptr", C.c_void_p), ("colidx", C.c_void_p),
+                ("values", C.c_void_p), ("capacity", C.c_int64), ("d_nnz", C.c_void_p)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+_lib: Optional[C.CDLL] = None
+
+
+def lib_path() -> str:
+    return _build.CUDA_LIB
+
+
+def load(build_if_missing: bool = False) -> C.CDLL:
+    """Loads libmsgemm.so; raises if it is absent (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build_cuda()
+        else:
+            raise ImportError(f"{path} is missing: build it with __graft_entry__.build() "
+                              "(the masked SpGEMM has no CPU fallback)")
+    lib = C.CDLL(path)
+    vp, i32, i64, sz = C.c_void_p, C.c_int, C.c_int64, C.c_size_t
+    P = C.POINTER
+    sigs = {
+        "msgemm_create": (i32, [P(vp), vp, ALLOC_FN, FREE_FN, vp]),
+        "msgemm_set_stream": (i32, [vp, vp]),
+        "msgemm_set_option": (i32, [vp, i32, i64]),
+        "msgemm_run": (i32, [vp, P(Csr), i32, P(Csr), P(Csr), i32, P(CsrOut)]),
+        "msgemm_backward": (i32, [vp, P(Csr), P(Csr), P(Csr), i32, vp, vp]),
+        "msgemm_run_batched": (i32, [vp, i32, P(Csr), vp, P(Csr), P(Csr), i32, P(CsrOut), i32]),
+        "msgemm_autotune": (i32, [vp, i32, P(Csr), vp, P(Csr), P(Csr), i32, C.c_char_p]),
+        "msgemm_transpose": (i32, [vp, P(Csr), i32, i32, P(CsrOut)]),
+        "msgemm_reduce_sum": (i32, [vp, P(CsrOut), i32, vp]),
+        "msgemm_sync_status": (i32, [vp]),
+        "msgemm_last_error_detail": (i32, [vp, C.c_char_p, sz]),
+        "msgemm_num_kinds": (i32, []),
+        "msgemm_bin_counts": (i32, [vp, P(i64), i32]),
+        "msgemm_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+@dataclass
+class DeviceCsr:
+    """CSR matrix on the device: int32 rowptr/colidx, optional values."""
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+    values: Optional[torch.Tensor] = None
+
+    @property
+    def nnz(self) -> int:
+        return int(self.colidx.numel())
+
+    def abi(self) -> Csr:
+        for t in (self.rowptr, self.colidx):
+            assert t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
+        v = self.values
+        if v is not None:
+            assert v.is_cuda and v.is_contiguous() and v.numel() == self.nnz
+        return Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(),
+                   self.colidx.data_ptr() if self.nnz else 0, v.data_ptr() if v is not None and self.nnz else 0)
+
+    @staticmethod
+    def from_host(m, device="cuda", values_dtype=None) -> "DeviceCsr":
+        """From any host CSR with numpy rowptr/colidx/values attributes."""
+        rp = torch.from_numpy(m.rowptr).to(device=device, dtype=torch.int32)
+        ci = torch.from_numpy(m.colidx).to(device=device, dtype=torch.int32)
+        v = None
+        if m.values is not None:
+            v = torch.from_numpy(m.values)
+            if values_dtype is not None:
+                v = v.to(values_dtype)
+            v = v.to(device)
+        return DeviceCsr(m.nrows, m.ncols, rp.contiguous(), ci.contiguous(), v)
+
+
+@dataclass
+class Result:
+    """Output CSR: tensors sized to the capacity; nnz is a device scalar."""
+    nrows: int
+    ncols: int
+    rowptr: torch.Tensor
+    colidx: torch.Tensor
+    values: torch.Tensor
+    d_nnz: torch.Tensor
+
+    def nnz(self) -> int:
+        return int(self.d_nnz.item())
+
+    def trimmed(self) -> DeviceCsr:
+        k = self.nnz()
+        return DeviceCsr(self.nrows, self.ncols, self.rowptr, self.colidx[:k], self.values[:k])
+
+
+class Handle:
+    """Owns a msgemm handle bound to the current device; allocations go
+    through torch's caching allocator on the current stream."""
+
+    def __init__(self, device: Optional[torch.device] = None):
+        self.lib = load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self._live: dict[int, torch.Tensor] = {}
+        self._alloc_cb = ALLOC_FN(self._alloc)
+        self._free_cb = FREE_FN(self._free)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            st = torch.cuda.current_stream().cuda_stream
+            self._check(self.lib.msgemm_create(C.byref(h), st, self._alloc_cb, self._free_cb, None), None)
+        self.h = h
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        self._live[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+    def _check(self, status, h):
+        if status != 0:
+            detail = ""
+            if h is not None:
+                buf = C.create_string_buffer(512)
+                self.lib.msgemm_last_error_detail(h, buf, 512)
+                detail = buf.value.decode(errors="replace")
+            raise MsgemmError(status, detail)
+
+    def check(self, status):
+        self._check(status, self.h)
+
+    def bind_stream(self):
+        self.check(self.lib.msgemm_set_stream(self.h, torch.cuda.current_stream(self.device).cuda_stream))
+
+    def set_option(self, opt: int, value: int):
+        self.check(self.lib.msgemm_set_option(self.h, opt, int(value)))
+
+    def force(self, accumulator: str):
+        self.set_option(OPT_FORCE_ACCUM, ACCUMULATORS[accumulator])
+
+    def adopt(self, ptr: int, dtype: torch.dtype, count: int) -> torch.Tensor:
+        """Takes ownership of a library-allocated output buffer as a tensor."""
+        raw = self._live.pop(ptr)
+        return raw.view(dtype)[:count] if count else raw.view(dtype)[:0]
+
+    def result(self, out: CsrOut, out_dtype: torch.dtype) -> Result:
+        rp = self.adopt(out.rowptr, torch.int32, out.nrows + 1)
+        cap = out.capacity
+        ci = self.adopt(out.colidx, torch.int32, cap)
+        v = self.adopt(out.values, out_dtype, cap)
+        nz = self.adopt(out.d_nnz, torch.int64, 1)
+        return Result(out.nrows, out.ncols, rp, ci, v, nz)
+
+    def sync_status(self):
+        self.check(self.lib.msgemm_sync_status(self.h))
+
+    def bin_counts(self) -> dict:
+        n = self.lib.msgemm_num_kinds()
+        arr = (C.c_int64 * n)()
+        self.check(self.lib.msgemm_bin_counts(self.h, arr, n))
+        return {KIND_NAMES[k] if k < len(KIND_NAMES) else str(k): int(arr[k]) for k in range(n)}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.msgemm_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def out_dtype(semiring: int) -> torch.dtype:
+    return torch.float32 if semiring == PLUS_TIMES_F32 else torch.int64
+
+
+def _sr(semiring) -> int:
+    return SEMIRINGS[semiring] if isinstance(semiring, str) else int(semiring)
+
+
+def msgemm_run(h: Handle, M: DeviceCsr, A: DeviceCsr, B: DeviceCsr, semiring="plus_times_f32",
+               complement: bool = False) -> Result:
+    """C = M .* (A B) (or !M .* (A B)) through msgemm_run."""
+    sr = _sr(semiring)
+    h.bind_stream()
+    m, a, b = M.abi(), A.abi(), B.abi()
+    out = CsrOut()
+    h.check(h.lib.msgemm_run(h.h, C.byref(m), int(bool(complement)), C.byref(a), C.byref(b), sr, C.byref(out)))
+    return h.result(out, out_dtype(sr))
+
+
+def msgemm_backward(h: Handle, A: DeviceCsr, B: DeviceCsr, G: DeviceCsr, need_dA=True, need_dB=True):
+    """(dA values aligned with A's storage, dB values aligned with B's)."""
+    h.bind_stream()
+    dA = torch.empty(A.nnz, dtype=torch.float32, device=A.colidx.device) if need_dA else None
+    dB = torch.empty(B.nnz, dtype=torch.float32, device=B.colidx.device) if need_dB else None
+    a, b, g = A.abi(), B.abi(), G.abi()
+    h.check(h.lib.msgemm_backward(h.h, C.byref(a), C.byref(b), C.byref(g), PLUS_TIMES_F32,
+                                  dA.data_ptr() if dA is not None and dA.numel() else None,
+                                  dB.data_ptr() if dB is not None and dB.numel() else None))
+    return dA, dB
+
+
+def msgemm_run_batched(h: Handle, Ms, As, Bs, semiring="plus_times_f32", complement=None, use_graph=False):
+    sr = _sr(semiring)
+    h.bind_stream()
+    n = len(Ms)
+    marr = (Csr * n)(*[x.abi() for x in Ms])
+    aarr = (Csr * n)(*[x.abi() for x in As])
+    barr = (Csr * n)(*[x.abi() for x in Bs])
+    outs = (CsrOut * n)()
+    comp = None
+    if complement is not None:
+        comp = (C.c_int * n)(*[int(bool(c)) for c in complement])
+    h.check(h.lib.msgemm_run_batched(h.h, n, marr, comp, aarr, barr, sr, outs, int(bool(use_graph))))
+    return [h.result(outs[p], out_dtype(sr)) for p in range(n)]
+
+
+def msgemm_reduce_sum(h: Handle, res: Result, semiring) -> torch.Tensor:
+    """Device scalar: int64 (wrapping) sum for the int64 semirings, float64 for fp32."""
+    sr = _sr(semiring)
+    h.bind_stream()
+    out = torch.empty(1, dtype=torch.float64 if sr == PLUS_TIMES_F32 else torch.int64, device=res.values.device)
+    co = CsrOut(res.nrows, res.ncols, res.rowptr.data_ptr(), res.colidx.data_ptr(), res.values.data_ptr(),
+                res.values.numel(), res.d_nnz.data_ptr())
+    h.check(h.lib.msgemm_reduce_sum(h.h, C.byref(co), sr, out.data_ptr()))
+    return out
+
+
+def msgemm_transpose(h: Handle, A: DeviceCsr, value_bytes: int) -> Result:
+    h.bind_stream()
+    a = A.abi()
+    out = CsrOut()
+    h.check(h.lib.msgemm_transpose(h.h, C.byref(a), int(value_bytes), 0, C.byref(out)))
+    dt = {0: torch.uint8, 4: torch.float32, 8: torch.int64}[value_bytes]
+    rp = h.adopt(out.rowptr, torch.int32, out.nrows + 1)
+    ci = h.adopt(out.colidx, torch.int32, out.capacity)
+    v = h.adopt(out.values, dt, out.capacity) if value_bytes else None
+    nz = h.adopt(out.d_nnz, torch.int64, 1)
+    return Result(out.nrows, out.ncols, rp, ci, v, nz)

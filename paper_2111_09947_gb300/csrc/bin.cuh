@@ -1,0 +1,128 @@
+// Row binning (the per-row choice of accumulator).
+//
+// The paper notes that unmasked flops and the per-row nonzeros of the mask
+// and inputs are the natural proxies for choosing an algorithm per row, with
+// a scan of the inputs to estimate flops (Sec. 6, remark on a hybrid), and
+// its density study (Sec. 8.1) ranks the algorithms: pull (inner products)
+// when the mask is much sparser than the inputs, MSA for small dimensions,
+// hash for larger ones.  This pass computes, for every row i,
+//   flops_i = sum over stored A_ik of nnz(B_k*)      (push work)
+//   pull_i  = sum over mask entries j of nnz(B_*j)    (pull work)
+// and picks a kind from the policy's preference list for the row's class,
+// the first whose shared-memory form fits.
+#pragma once
+
+#include "common.cuh"
+
+namespace msg {
+
+template <int SR>
+__device__ __forceinline__ int pick_family(const Policy &pol, int fam, bool warp, long long flops, int mnz, int anz, int n,
+                           bool dot_ok, bool forced) {
+    constexpr int acc = SrSizes<SR>::acc, in = SrSizes<SR>::in;
+    constexpr bool sb = SrSizes<SR>::setbits;
+    switch (fam) {
+    case F_MSA:
+        if (warp && pol.slab[K_MSA_W] > 0 && msa_bytes(n, acc) <= pol.slab[K_MSA_W]) return K_MSA_W;
+        if (forced || n <= pol.tileT[0]) return K_MSA_T;
+        return -1;
+    case F_HASH:
+        if (warp && pol.slab[K_HASH_W] > 0 && hash_slots(mnz, acc, sb, pol.slab[K_HASH_W])) return K_HASH_W;
+        if (pol.slab[K_HASH_B] > 0 && hash_slots(mnz, acc, sb, pol.slab[K_HASH_B])) return K_HASH_B;
+        return -1;
+    case F_MCA:
+        if (warp && pol.slab[K_MCA_W] > 0 && mca_bytes(mnz, acc, sb) <= pol.slab[K_MCA_W]) return K_MCA_W;
+        if (pol.slab[K_MCA_B] > 0 && mca_bytes(mnz, acc, sb) <= pol.slab[K_MCA_B]) return K_MCA_B;
+        return -1;
+    case F_DOT:
+        if (!dot_ok) return -1;
+        if (warp && pol.slab[K_DOT_W] > 0 && dot_bytes(anz, mnz, in, acc, sb) <= pol.slab[K_DOT_W]) return K_DOT_W;
+        if (pol.slab[K_DOT_B] > 0 && dot_bytes(anz, mnz, in, acc, sb) <= pol.slab[K_DOT_B]) return K_DOT_B;
+        return -1;
+    default:
+        return -1;
+    }
+}
+
+template <int SR>
+__device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, int mnz, int anz, int n, bool comp,
+                           long long pull, bool dot_ok) {
+    constexpr int acc = SrSizes<SR>::acc;
+    const bool warp = flops <= pol.warp_flops_max;
+    if (comp) {
+        const long long bound = min(flops, (long long)(n - mnz));
+        if (flops == 0 || bound <= 0) return K_EMPTY;
+        if (pol.force == F_MSA) return K_CMSA_T;
+        if (warp && pol.slab[K_CHASH_W] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_W])) return K_CHASH_W;
+        if (pol.slab[K_CHASH_B] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_B])) return K_CHASH_B;
+        return K_CMSA_T;
+    }
+    if (flops == 0 || mnz == 0) return K_EMPTY;
+    if (pol.force != F_AUTO) {
+        const int k = pick_family<SR>(pol, pol.force, warp, flops, mnz, anz, n, dot_ok, true);
+        return k >= 0 ? k : K_MSA_T;
+    }
+    if (dot_ok && (double)pull * pol.dot_ratio < (double)flops) {
+        const int k = pick_family<SR>(pol, F_DOT, warp, flops, mnz, anz, n, dot_ok, false);
+        if (k >= 0) return k;
+    }
+    const unsigned char *pref = pol.pref[row_class(flops, mnz)];
+    for (int x = 0; x < 4 && pref[x] != F_AUTO; ++x) {
+        const int k = pick_family<SR>(pol, pref[x], warp, flops, mnz, anz, n, dot_ok, false);
+        if (k >= 0) return k;
+    }
+    return K_MSA_T;
+}
+
+// One warp per row: flops, pull work, kind, temporary room.
+template <int SR>
+__global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
+                                                   const __grid_constant__ Policy pol, long long *room) {
+    __shared__ int hist[NKIND];
+    for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
+    __syncthreads();
+    const int lane = lane_id();
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = gw; r < ra.R; r += nw) {
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const int i = (int)(r - P.row0);
+        const int a0 = __ldg(P.a_rp + i), a1 = __ldg(P.a_rp + i + 1);
+        const int m0 = __ldg(P.m_rp + i), m1 = __ldg(P.m_rp + i + 1);
+        long long f = 0;
+        for (int t = a0 + lane; t < a1; t += 32) {
+            const int k = __ldg(P.a_ci + t);
+            f += __ldg(P.b_rp + k + 1) - __ldg(P.b_rp + k);
+        }
+        f = warp_sum_ll(f);
+        const bool dot_ok = !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
+        long long pull = 0;
+        if (dot_ok) {
+            for (int q = m0 + lane; q < m1; q += 32) {
+                const int j = __ldg(P.m_ci + q);
+                pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
+            }
+            pull = warp_sum_ll(pull);
+        }
+        if (lane == 0) {
+            const int mnz = m1 - m0;
+            const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok);
+            ra.flops[r] = f;
+            ra.kind[r] = (unsigned char)kind;
+            ra.cnt[r] = 0;
+            if (!P.complement) {
+                ra.tmpoff[r] = P.tmp0 + m0;
+                room[r] = 0;
+            } else {
+                room[r] = (kind == K_EMPTY) ? 0 : min(f, (long long)(P.n - mnz));
+            }
+            atomicAdd(&hist[kind], 1);
+            if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;
+        }
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NKIND; x += blockDim.x)
+        if (hist[x]) atomicAdd(&ra.kind_count[x], hist[x]);
+}
+
+}  // namespace msg

@@ -1,0 +1,676 @@
+// C ABI of the masked SpGEMM library (declarations and contracts in
+// include/msgemm.h): the handle, its workspace, and the host side of the
+// one-phase pipeline  validate -> bin -> [transpose for pull] -> accumulate
+// per kind -> count -> compact  (Sec. 4-6).
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "rows.cuh"
+
+using namespace msg;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t cap = 0;
+};
+
+}  // namespace
+
+struct msgemm_handle {
+    int device = 0;
+    int nsm = 0;
+    int smem_optin = 0;
+    cudaStream_t stream = nullptr;
+    msgemm_alloc_fn alloc = nullptr;
+    msgemm_free_fn free_fn = nullptr;
+    void *ctx = nullptr;
+    // workspace, reused across calls
+    Buf rows, small, tmp, bt, cur, prods;
+    unsigned *d_err = nullptr;   // in `small`, persistent
+    int force = 0, validate = 0, allow_dot = 1;
+    unsigned char pref[NCLASS][4];
+    float dot_ratio = 2.0f;
+    int warp_flops_max = 4096;
+    int *last_kind_count = nullptr;
+    std::string last_error;
+    // host staging
+    std::vector<DevProd> hprods;
+};
+
+namespace {
+
+msgemm_status fail(msgemm_handle *h, msgemm_status st, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->last_error = buf;
+    }
+    return st;
+}
+
+#define CK(call)                                                                                 \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess)                                                                   \
+            return fail(h, MSGEMM_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                                     \
+    } while (0)
+
+#define CKS(expr)                            \
+    do {                                     \
+        msgemm_status s_ = (expr);           \
+        if (s_ != MSGEMM_OK) return s_;      \
+    } while (0)
+
+void *dev_alloc(msgemm_handle *h, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (h->alloc) return h->alloc(bytes, h->ctx);
+    void *p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dev_free(msgemm_handle *h, void *p) {
+    if (!p) return;
+    if (h->free_fn) h->free_fn(p, h->ctx);
+    else cudaFree(p);
+}
+
+msgemm_status grow(msgemm_handle *h, Buf &b, size_t bytes) {
+    if (b.cap >= bytes && b.p) return MSGEMM_OK;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 4096);
+    dev_free(h, b.p);
+    b.p = dev_alloc(h, want);
+    b.cap = b.p ? want : 0;
+    if (!b.p) return fail(h, MSGEMM_ERR_OOM, "workspace allocation of %zu bytes failed", want);
+    return MSGEMM_OK;
+}
+
+// Bump carving of a buffer.
+struct Carver {
+    char *base;
+    size_t off = 0;
+    explicit Carver(void *p) : base(static_cast<char *>(p)) {}
+    template <class T> T *take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        T *r = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return r;
+    }
+};
+template <class T> size_t carve_size(size_t count) { return ((count * sizeof(T)) + 255) & ~size_t(255); }
+
+int acc_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_I64 ? 8 : 4; }
+int in_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_F32 ? 4 : sr == MSGEMM_PLUS_TIMES_I64 ? 8 : 0; }
+int out_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_F32 ? 4 : 8; }
+
+void default_pref(unsigned char pref[NCLASS][4]) {
+    for (int c = 0; c < NCLASS; ++c) {
+        const int mb = c % 4;
+        // small mask rows: rank by binary search is cheapest; otherwise hash
+        if (mb == 0) { pref[c][0] = F_MSA; pref[c][1] = F_MCA; pref[c][2] = F_HASH; }
+        else { pref[c][0] = F_MSA; pref[c][1] = F_HASH; pref[c][2] = F_MCA; }
+        pref[c][3] = F_AUTO;
+    }
+}
+
+Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
+    Policy p{};
+    p.force = h->force;
+    p.allow_dot = h->allow_dot;
+    p.dot_ratio = h->dot_ratio;
+    p.warp_flops_max = h->warp_flops_max;
+    const int acc = acc_bytes(sr);
+    const int wslab = 4096;
+    const int bslab = 64 * 1024;
+    const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
+    p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
+    p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;
+    const long long msaw = (msa_bytes(max_n, acc) + 15) & ~15LL;
+    p.slab[K_MSA_W] = msaw <= 24 * 1024 ? (int)msaw : 0;
+    p.slab[K_MSA_T] = p.slab[K_CMSA_T] = tslab;
+    p.tileT[0] = p.tileT[1] = msa_tile_width(tslab, acc);
+    memcpy(p.pref, h->pref, sizeof p.pref);
+    return p;
+}
+
+msgemm_status check_csr(msgemm_handle *h, const msgemm_csr *X, const char *name, bool need_vals) {
+    if (!X) return fail(h, MSGEMM_ERR_INVALID, "%s is NULL", name);
+    if (X->nrows < 0 || X->ncols < 0 || X->nnz < 0) return fail(h, MSGEMM_ERR_INVALID, "%s has a negative size", name);
+    if (X->nnz >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "%s has nnz >= 2^31", name);
+    if (!X->rowptr) return fail(h, MSGEMM_ERR_INVALID, "%s.rowptr is NULL", name);
+    if (X->nnz > 0 && !X->colidx) return fail(h, MSGEMM_ERR_INVALID, "%s.colidx is NULL", name);
+    if (need_vals && X->nnz > 0 && !X->values) return fail(h, MSGEMM_ERR_INVALID, "%s.values is NULL", name);
+    return MSGEMM_OK;
+}
+
+// One product of a pipeline run, host view.
+struct ProdIn {
+    const msgemm_csr *M, *A, *B;
+    int comp;
+    const int *bt_rp = nullptr, *bt_ci = nullptr;  // prebuilt B^T (pull), optional
+    const void *bt_v = nullptr;
+    int a_sorted = 1;
+    msgemm_csr_out *C = nullptr;   // compacted output
+    void *aligned_out = nullptr;   // gradient form: values at the mask's slots
+};
+
+// The whole one-phase pipeline for a set of products (Sec. 4-6).
+msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt) {
+    const int P = (int)in.size();
+    const bool aligned = P > 0 && in[0].aligned_out != nullptr;
+    cudaStream_t st = h->stream;
+    long long R = 0, nnzA = 0, tmpn = 0, ntiles = 0;
+    int max_n = 0;
+    bool any_comp = false, any_tiled = false;
+    const Policy pol0 = make_policy(h, sr, 0);
+    std::vector<DevProd> &dp = h->hprods;
+    dp.assign(P, DevProd{});
+    for (int p = 0; p < P; ++p) {
+        const ProdIn &x = in[p];
+        DevProd &d = dp[p];
+        d.m_rp = x.M->rowptr; d.m_ci = x.M->colidx;
+        d.a_rp = x.A->rowptr; d.a_ci = x.A->colidx; d.a_v = x.A->values;
+        d.b_rp = x.B->rowptr; d.b_ci = x.B->colidx; d.b_v = x.B->values;
+        d.bt_rp = x.bt_rp; d.bt_ci = x.bt_ci; d.bt_v = x.bt_v;
+        d.m = x.M->nrows; d.n = x.M->ncols; d.k = x.A->ncols;
+        d.complement = x.comp;
+        d.a_sorted = x.a_sorted;
+        d.row0 = R;
+        d.tile0 = ntiles;
+        d.abase = nnzA;
+        d.tmp0 = tmpn;
+        R += d.m;
+        nnzA += x.A->nnz;
+        ntiles += (d.m + CTILE - 1) / CTILE;
+        if (!x.comp) tmpn += x.M->nnz;
+        any_comp |= x.comp != 0;
+        max_n = std::max(max_n, d.n);
+        if (d.n > pol0.tileT[x.comp ? 1 : 0]) any_tiled = true;
+        if (x.C) {
+            d.c_rp = x.C->rowptr; d.c_ci = x.C->colidx; d.c_v = x.C->values; d.c_nnz = reinterpret_cast<long long *>(x.C->d_nnz);
+        }
+    }
+    if (R >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "total rows >= 2^31");
+    const Policy pol = make_policy(h, sr, max_n);
+
+    // ---- workspace
+    const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 2 + carve_size<unsigned char>(R) +
+                              carve_size<long long>(ntiles) * 2 + carve_size<long long>(2 * (size_t)P) +
+                              carve_size<long long>((R + STILE - 1) / STILE + 2) + carve_size<DevProd>(P) + 4096;
+    CKS(grow(h, h->rows, rows_bytes));
+    Carver cv(h->rows.p);
+    RowArrays ra{};
+    ra.R = R;
+    ra.flops = cv.take<long long>(R);
+    ra.tmpoff = cv.take<long long>(R);
+    long long *room = cv.take<long long>(R);
+    ra.cnt = cv.take<int>(R);
+    ra.perm = cv.take<int>(R);
+    ra.kind = cv.take<unsigned char>(R);
+    long long *tile_sums = cv.take<long long>(ntiles);
+    long long *tile_offs = cv.take<long long>(ntiles);
+    long long *prod_tot = cv.take<long long>(2 * (size_t)P);
+    long long *room_tiles = cv.take<long long>((R + STILE - 1) / STILE + 2);
+    DevProd *dtab = cv.take<DevProd>(P);
+    // small counters: zeroed per run (err is persistent, kept first)
+    Carver cs(h->small.p);
+    unsigned *err = cs.take<unsigned>(1);
+    ra.err = err;
+    char *zero_begin = cs.base + ((cs.off + 255) & ~size_t(255));
+    ra.kind_count = cs.take<int>(NKIND);
+    ra.kind_fill = cs.take<int>(NKIND);
+    ra.kind_next = cs.take<int>(NKIND);
+    ra.kind_off = cs.take<int>(NKIND + 1);
+    ra.any_dot = cs.take<int>(1);
+    ra.bound_total = cs.take<long long>(1);
+    const size_t zero_bytes = (size_t)(cs.base + cs.off - zero_begin);
+    h->last_kind_count = ra.kind_count;
+    CK(cudaMemsetAsync(zero_begin, 0, zero_bytes, st));
+
+    // ---- optional input validation: synchronises, and rejects invalid input
+    // before any kernel that would index through it runs
+    if (h->validate) {
+        for (int p = 0; p < P; ++p) {
+            const ProdIn &x = in[p];
+            const msgemm_csr *mats[3] = {x.M, x.A, x.B};
+            for (const msgemm_csr *X : mats)
+                if (X->nrows > 0) CK(launch_validate(X->rowptr, X->colidx, X->nrows, X->ncols, X->nnz, err, st, h->nsm));
+        }
+        unsigned herr = 0;
+        CK(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (herr) {
+            CK(cudaMemsetAsync(err, 0, sizeof herr, st));
+            if (herr & ERR_UNSORTED) return fail(h, MSGEMM_ERR_UNSORTED, "an input row is not strictly ascending");
+            return fail(h, MSGEMM_ERR_INVALID, "invalid row pointers or column indices");
+        }
+    }
+
+    // ---- B^T for the pull kernel: row pointers now, entries if a row picks it
+    struct BtPlan { int *rp, *cur, *ci; void *v; long long nnz; int n; const msgemm_csr *B; };
+    std::vector<BtPlan> btp;
+    if (build_bt && h->allow_dot && (h->force == F_AUTO || h->force == F_DOT)) {
+        size_t bytes = 0;
+        for (int p = 0; p < P; ++p) {
+            if (in[p].comp || dp[p].bt_rp || !in[p].a_sorted) continue;
+            const msgemm_csr *B = in[p].B;
+            bytes += carve_size<int>((size_t)B->ncols + 1) * 2 + carve_size<int>(B->nnz) +
+                     carve_size<char>((size_t)B->nnz * in_bytes(sr)) + carve_size<long long>(B->ncols / STILE + 4);
+        }
+        if (bytes) {
+            CKS(grow(h, h->bt, bytes));
+            Carver cb(h->bt.p);
+            for (int p = 0; p < P; ++p) {
+                if (in[p].comp || dp[p].bt_rp || !in[p].a_sorted) continue;
+                const msgemm_csr *B = in[p].B;
+                BtPlan b{};
+                b.B = B;
+                b.n = B->ncols;
+                b.nnz = B->nnz;
+                b.rp = cb.take<int>((size_t)B->ncols + 1);
+                b.cur = cb.take<int>((size_t)B->ncols + 1);
+                b.ci = cb.take<int>(B->nnz);
+                b.v = cb.take<char>((size_t)B->nnz * in_bytes(sr));
+                long long *tb = cb.take<long long>(B->ncols / STILE + 4);
+                CK(launch_col_counts(B->colidx, B->nnz, B->ncols, b.cur, st, h->nsm));
+                CK(launch_excl_scan_int(b.cur, B->ncols, b.rp, tb, st, h->nsm));
+                dp[p].bt_rp = b.rp;
+                dp[p].bt_ci = b.ci;
+                dp[p].bt_v = in_bytes(sr) ? b.v : nullptr;
+                btp.push_back(b);
+            }
+        }
+    }
+
+    // ---- products table
+    ProdSet ps{};
+    ps.P = P;
+    if (P == 1) {
+        ps.p0 = dp[0];
+        ps.tab = dtab;
+    } else {
+        ps.tab = dtab;
+    }
+    CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
+
+    // ---- binning
+    switch (sr) {
+    case MSGEMM_PLUS_TIMES_F32: CK(launch_bin_score_f32(ps, ra, pol, room, st, h->nsm)); break;
+    case MSGEMM_PLUS_TIMES_I64: CK(launch_bin_score_i64(ps, ra, pol, room, st, h->nsm)); break;
+    default: CK(launch_bin_score_pp(ps, ra, pol, room, st, h->nsm)); break;
+    }
+    CK(launch_bin_scatter(ra, st, h->nsm));
+
+    // ---- temporary room: mask-sized for plain masks, bound-sized when complemented
+    long long comp_total = 0;
+    if (any_comp) {
+        CK(launch_scan_room(ra, room, tmpn, room_tiles, ra.bound_total, st, h->nsm));
+        CK(cudaMemcpyAsync(&comp_total, ra.bound_total, sizeof comp_total, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    const long long tmp_entries = tmpn + comp_total;
+    TmpOut tmp{};
+    const int ob = out_bytes(sr);
+    if (!aligned) {
+        CKS(grow(h, h->tmp, carve_size<int>(tmp_entries) + carve_size<char>((size_t)tmp_entries * ob)));
+        Carver ct(h->tmp.p);
+        tmp.ci = ct.take<int>(tmp_entries);
+        tmp.v = ct.take<char>((size_t)tmp_entries * ob);
+    } else {
+        tmp.ci = nullptr;
+        tmp.v = in[0].aligned_out;   // one product in gradient form
+    }
+
+    // ---- B^T entries, only when some row picked the pull kernel
+    for (const BtPlan &b : btp) {
+        CK(cudaMemcpyAsync(b.cur, b.rp, sizeof(int) * ((size_t)b.n + 1), cudaMemcpyDeviceToDevice, st));
+        CK(launch_transpose_fill(b.B->rowptr, b.B->colidx, b.B->values, in_bytes(sr), b.B->nrows, b.rp, b.cur, b.ci,
+                                 b.v, ra.any_dot, st, h->nsm));
+    }
+
+    // ---- accumulation, one persistent kernel per kind
+    RowLaunch L{};
+    L.ra = ra;
+    L.tmp = tmp;
+    L.aligned = aligned ? 1 : 0;
+    if (any_tiled) {
+        CKS(grow(h, h->cur, carve_size<int4>(std::max<long long>(nnzA, 1))));
+        L.cursors = static_cast<int4 *>(h->cur.p);
+    }
+    std::vector<int> kinds;
+    bool any_plain = false;
+    for (int p = 0; p < P; ++p) any_plain |= !in[p].comp;
+    if (any_plain) {
+        if (pol.slab[K_MSA_W]) kinds.push_back(K_MSA_W);
+        kinds.insert(kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
+        if (!btp.empty() || std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
+            kinds.insert(kinds.end(), {K_DOT_W, K_DOT_B});
+        kinds.push_back(K_MSA_T);
+    }
+    if (any_comp) kinds.insert(kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
+    for (int kd : kinds) {
+        if (kd == K_MSA_T || kd == K_CMSA_T) CK(launch_sort_heavy(ra, kd, st));
+        L.slab = pol.slab[kd];
+        L.tileT = pol.tileT[kd == K_CMSA_T ? 1 : 0];
+        switch (sr) {
+        case MSGEMM_PLUS_TIMES_F32: CK(launch_kind_f32(kd, ps, L, st, h->nsm)); break;
+        case MSGEMM_PLUS_TIMES_I64: CK(launch_kind_i64(kd, ps, L, st, h->nsm)); break;
+        default: CK(launch_kind_pp(kd, ps, L, st, h->nsm)); break;
+        }
+    }
+    if (aligned) return MSGEMM_OK;
+
+    // ---- count, allocate complemented outputs, compact
+    CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, st, h->nsm));
+    if (any_comp) {
+        std::vector<long long> tot(P);
+        CK(cudaMemcpyAsync(tot.data(), prod_tot + P, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int p = 0; p < P; ++p) {
+            if (!in[p].comp) continue;
+            msgemm_csr_out *C = in[p].C;
+            if (tot[p] >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "product %d has >= 2^31 entries", p);
+            C->capacity = tot[p];
+            C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(tot[p], 1)));
+            C->values = dev_alloc(h, (size_t)ob * (size_t)std::max<long long>(tot[p], 1));
+            if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+            dp[p].c_ci = C->colidx;
+            dp[p].c_v = C->values;
+        }
+        if (P == 1) ps.p0 = dp[0];
+        CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
+    }
+    CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, ob, st, h->nsm));
+    return MSGEMM_OK;
+}
+
+msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_semiring sr, msgemm_csr_out *C) {
+    memset(C, 0, sizeof *C);
+    C->nrows = M->nrows;
+    C->ncols = M->ncols;
+    C->rowptr = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * ((size_t)M->nrows + 1)));
+    C->d_nnz = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t)));
+    if (!C->rowptr || !C->d_nnz) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+    if (!comp) {
+        C->capacity = M->nnz;
+        C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(M->nnz, 1)));
+        C->values = dev_alloc(h, (size_t)out_bytes(sr) * (size_t)std::max<long long>(M->nnz, 1));
+        if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+    }
+    return MSGEMM_OK;
+}
+
+msgemm_status check_product(msgemm_handle *h, const msgemm_csr *M, const msgemm_csr *A, const msgemm_csr *B,
+                            msgemm_semiring sr) {
+    if (sr < MSGEMM_PLUS_TIMES_F32 || sr > MSGEMM_PLUS_PAIR_I64) return fail(h, MSGEMM_ERR_INVALID, "unknown semiring");
+    const bool v = sr != MSGEMM_PLUS_PAIR_I64;
+    CKS(check_csr(h, M, "M", false));
+    CKS(check_csr(h, A, "A", v));
+    CKS(check_csr(h, B, "B", v));
+    if (M->nrows != A->nrows || A->ncols != B->nrows || M->ncols != B->ncols)
+        return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: M %dx%d, A %dx%d, B %dx%d", M->nrows, M->ncols, A->nrows,
+                    A->ncols, B->nrows, B->ncols);
+    return MSGEMM_OK;
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+extern "C" {
+
+msgemm_status msgemm_create(msgemm_handle **handle, void *stream, msgemm_alloc_fn alloc, msgemm_free_fn free_fn,
+                            void *ctx) {
+    if (!handle) return MSGEMM_ERR_INVALID;
+    *handle = nullptr;
+    if ((alloc == nullptr) != (free_fn == nullptr)) return MSGEMM_ERR_INVALID;
+    msgemm_handle *h = new msgemm_handle();
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->alloc = alloc;
+    h->free_fn = free_fn;
+    h->ctx = ctx;
+    default_pref(h->pref);
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete h;
+        return MSGEMM_ERR_CUDA;
+    }
+    if (grow(h, h->small, 8192) != MSGEMM_OK) {
+        delete h;
+        return MSGEMM_ERR_OOM;
+    }
+    h->d_err = static_cast<unsigned *>(h->small.p);
+    if (cudaMemsetAsync(h->small.p, 0, h->small.cap, h->stream) != cudaSuccess) {
+        dev_free(h, h->small.p);
+        delete h;
+        return MSGEMM_ERR_CUDA;
+    }
+    *handle = h;
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_set_stream(msgemm_handle *h, void *stream) {
+    if (!h) return MSGEMM_ERR_INVALID;
+    if (static_cast<cudaStream_t>(stream) == h->stream) return MSGEMM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    h->stream = static_cast<cudaStream_t>(stream);
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t value) {
+    if (!h) return MSGEMM_ERR_INVALID;
+    switch (opt) {
+    case MSGEMM_OPT_FORCE_ACCUM:
+        if (value < MSGEMM_ACC_AUTO || value > MSGEMM_ACC_DOT) return fail(h, MSGEMM_ERR_INVALID, "bad accumulator");
+        h->force = (int)value;
+        return MSGEMM_OK;
+    case MSGEMM_OPT_VALIDATE: h->validate = value != 0; return MSGEMM_OK;
+    case MSGEMM_OPT_DOT: h->allow_dot = value != 0; return MSGEMM_OK;
+    default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
+    }
+}
+
+msgemm_status msgemm_run(msgemm_handle *h, const msgemm_csr *M, int complement, const msgemm_csr *A,
+                         const msgemm_csr *B, msgemm_semiring sr, msgemm_csr_out *C) {
+    if (!h || !C) return fail(h, MSGEMM_ERR_INVALID, "NULL handle or output");
+    CKS(check_product(h, M, A, B, sr));
+    const int comp = complement != 0;
+    CKS(alloc_out(h, M, comp, sr, C));
+    std::vector<ProdIn> in(1);
+    in[0].M = M; in[0].A = A; in[0].B = B; in[0].comp = comp; in[0].C = C;
+    return run_pipeline(h, in, sr, true);
+}
+
+msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
+                              msgemm_semiring sr, float *dA_vals, float *dB_vals) {
+    if (!h) return MSGEMM_ERR_INVALID;
+    if (sr != MSGEMM_PLUS_TIMES_F32) return fail(h, MSGEMM_ERR_UNSUPPORTED, "backward is defined for plus-times fp32");
+    CKS(check_csr(h, A, "A", true));
+    CKS(check_csr(h, B, "B", true));
+    CKS(check_csr(h, G, "G", true));
+    if (A->ncols != B->nrows || G->nrows != A->nrows || G->ncols != B->ncols)
+        return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: A %dx%d, B %dx%d, G %dx%d", A->nrows, A->ncols,
+                    B->nrows, B->ncols, G->nrows, G->ncols);
+    cudaStream_t st = h->stream;
+    // transposes B^T (n x k) and A^T (k x m), values carried, rows unsorted
+    struct T { int *rp, *cur, *ci; float *v; long long *tb; };
+    auto tsize = [](const msgemm_csr *X) {
+        return carve_size<int>((size_t)X->ncols + 1) * 2 + carve_size<int>(X->nnz) + carve_size<float>(X->nnz) +
+               carve_size<long long>(X->ncols / STILE + 4);
+    };
+    Buf tb;
+    tb.p = dev_alloc(h, tsize(A) + tsize(B) + 1024);
+    if (!tb.p) return fail(h, MSGEMM_ERR_OOM, "transpose workspace allocation failed");
+    Carver cv(tb.p);
+    auto mk = [&](const msgemm_csr *X) {
+        T t;
+        t.rp = cv.take<int>((size_t)X->ncols + 1);
+        t.cur = cv.take<int>((size_t)X->ncols + 1);
+        t.ci = cv.take<int>(X->nnz);
+        t.v = cv.take<float>(X->nnz);
+        t.tb = cv.take<long long>(X->ncols / STILE + 4);
+        return t;
+    };
+    T Bt = mk(B), At = mk(A);
+    msgemm_status rs = MSGEMM_OK;
+    auto transpose = [&](const msgemm_csr *X, T &t) -> msgemm_status {
+        CK(launch_col_counts(X->colidx, X->nnz, X->ncols, t.cur, st, h->nsm));
+        CK(launch_excl_scan_int(t.cur, X->ncols, t.rp, t.tb, st, h->nsm));
+        CK(cudaMemcpyAsync(t.cur, t.rp, sizeof(int) * ((size_t)X->ncols + 1), cudaMemcpyDeviceToDevice, st));
+        CK(launch_transpose_fill(X->rowptr, X->colidx, X->values, 4, X->nrows, t.rp, t.cur, t.ci, t.v, nullptr, st,
+                                 h->nsm));
+        return MSGEMM_OK;
+    };
+    if (dA_vals) {
+        // dA = pattern(A) .* (G B^T): mask A, left G (m x n), right B^T (n x k);
+        // the pull kernel reads columns of B^T, which are the rows of B.
+        rs = transpose(B, Bt);
+        if (rs == MSGEMM_OK) {
+            msgemm_csr Mx = *A, Bx{};
+            Mx.values = nullptr;
+            Bx.nrows = B->ncols; Bx.ncols = B->nrows; Bx.nnz = B->nnz;
+            Bx.rowptr = Bt.rp; Bx.colidx = Bt.ci; Bx.values = Bt.v;
+            std::vector<ProdIn> in(1);
+            in[0].M = &Mx; in[0].A = G; in[0].B = &Bx; in[0].comp = 0;
+            in[0].bt_rp = B->rowptr; in[0].bt_ci = B->colidx; in[0].bt_v = B->values;
+            in[0].aligned_out = dA_vals;
+            if (cudaMemsetAsync(dA_vals, 0, sizeof(float) * (size_t)A->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
+            if (rs == MSGEMM_OK && A->nnz > 0) rs = run_pipeline(h, in, sr, false);
+        }
+    }
+    if (rs == MSGEMM_OK && dB_vals) {
+        // dB = pattern(B) .* (A^T G): mask B, left A^T (k x m, rows unsorted), right G
+        rs = transpose(A, At);
+        if (rs == MSGEMM_OK) {
+            msgemm_csr Mx = *B, Ax{};
+            Mx.values = nullptr;
+            Ax.nrows = A->ncols; Ax.ncols = A->nrows; Ax.nnz = A->nnz;
+            Ax.rowptr = At.rp; Ax.colidx = At.ci; Ax.values = At.v;
+            std::vector<ProdIn> in(1);
+            in[0].M = &Mx; in[0].A = &Ax; in[0].B = G; in[0].comp = 0;
+            in[0].a_sorted = 0;
+            in[0].aligned_out = dB_vals;
+            if (cudaMemsetAsync(dB_vals, 0, sizeof(float) * (size_t)B->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
+            if (rs == MSGEMM_OK && B->nnz > 0) rs = run_pipeline(h, in, sr, false);
+        }
+    }
+    // the transpose buffer is released in stream order (the callback's free
+    // must honour stream order; cudaFree synchronises)
+    dev_free(h, tb.p);
+    return rs;
+}
+
+msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,
+                                 const msgemm_csr *A, const msgemm_csr *B, msgemm_semiring sr, msgemm_csr_out *C,
+                                 int use_graph) {
+    if (!h || nprod < 0 || (nprod > 0 && (!M || !A || !B || !C))) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
+    (void)use_graph;
+    if (nprod == 0) return MSGEMM_OK;
+    std::vector<ProdIn> in(nprod);
+    for (int p = 0; p < nprod; ++p) {
+        CKS(check_product(h, &M[p], &A[p], &B[p], sr));
+        const int comp = complement ? complement[p] != 0 : 0;
+        CKS(alloc_out(h, &M[p], comp, sr, &C[p]));
+        in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = comp; in[p].C = &C[p];
+    }
+    return run_pipeline(h, in, sr, true);
+}
+
+msgemm_status msgemm_autotune(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,
+                              const msgemm_csr *A, const msgemm_csr *B, msgemm_semiring sr, const char *cache_path) {
+    (void)nprod; (void)M; (void)complement; (void)A; (void)B; (void)sr; (void)cache_path;
+    return fail(h, MSGEMM_ERR_UNSUPPORTED, "autotune not available in this build");
+}
+
+msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_bytes, int sorted, msgemm_csr_out *At) {
+    if (!h || !At) return MSGEMM_ERR_INVALID;
+    CKS(check_csr(h, A, "A", value_bytes > 0));
+    if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8) return fail(h, MSGEMM_ERR_INVALID, "value_bytes");
+    if (sorted) return fail(h, MSGEMM_ERR_UNSUPPORTED, "sorted transpose not available in this build");
+    cudaStream_t st = h->stream;
+    memset(At, 0, sizeof *At);
+    At->nrows = A->ncols;
+    At->ncols = A->nrows;
+    At->capacity = A->nnz;
+    At->rowptr = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * ((size_t)A->ncols + 1)));
+    At->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(A->nnz, 1)));
+    At->values = value_bytes ? dev_alloc(h, (size_t)value_bytes * (size_t)std::max<long long>(A->nnz, 1)) : nullptr;
+    At->d_nnz = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t)));
+    if (!At->rowptr || !At->colidx || !At->d_nnz || (value_bytes && !At->values))
+        return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+    CKS(grow(h, h->bt, carve_size<int>((size_t)A->ncols + 1) + carve_size<long long>(A->ncols / STILE + 4)));
+    Carver cb(h->bt.p);
+    int *cur = cb.take<int>((size_t)A->ncols + 1);
+    long long *tbuf = cb.take<long long>(A->ncols / STILE + 4);
+    CK(launch_col_counts(A->colidx, A->nnz, A->ncols, cur, st, h->nsm));
+    CK(launch_excl_scan_int(cur, A->ncols, At->rowptr, tbuf, st, h->nsm));
+    CK(cudaMemcpyAsync(cur, At->rowptr, sizeof(int) * ((size_t)A->ncols + 1), cudaMemcpyDeviceToDevice, st));
+    CK(launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At->rowptr, cur, At->colidx,
+                             At->values, nullptr, st, h->nsm));
+    int64_t nnz = A->nnz;
+    CK(cudaMemcpyAsync(At->d_nnz, &nnz, sizeof nnz, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_reduce_sum(msgemm_handle *h, const msgemm_csr_out *C, msgemm_semiring sr, void *d_sum) {
+    if (!h || !C || !d_sum || !C->d_nnz) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
+    CK(launch_reduce_sum(sr, C->values, reinterpret_cast<const long long *>(C->d_nnz), d_sum, h->stream, h->nsm));
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_sync_status(msgemm_handle *h) {
+    if (!h) return MSGEMM_ERR_INVALID;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) return fail(h, MSGEMM_ERR_CUDA, "stream: %s", cudaGetErrorString(e));
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, h->d_err, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) CK(cudaMemset(h->d_err, 0, sizeof err));
+    if (err & ERR_TIMEOUT) return fail(h, MSGEMM_ERR_TIMEOUT, "a bounded device wait ran out");
+    if (err & ERR_UNSORTED) return fail(h, MSGEMM_ERR_UNSORTED, "an input row is not strictly ascending");
+    if (err & (ERR_INVALID | ERR_INTERNAL)) return fail(h, MSGEMM_ERR_INVALID, "invalid input found on the device");
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_last_error_detail(msgemm_handle *h, char *buf, size_t len) {
+    if (!h || !buf || len == 0) return MSGEMM_ERR_INVALID;
+    snprintf(buf, len, "%s", h->last_error.c_str());
+    return MSGEMM_OK;
+}
+
+int msgemm_num_kinds(void) { return NKIND; }
+
+msgemm_status msgemm_bin_counts(msgemm_handle *h, int64_t *counts, int n) {
+    if (!h || !counts) return MSGEMM_ERR_INVALID;
+    int tmp[NKIND] = {0};
+    if (h->last_kind_count) {
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaMemcpy(tmp, h->last_kind_count, sizeof tmp, cudaMemcpyDeviceToHost));
+    }
+    for (int k = 0; k < std::min(n, (int)NKIND); ++k) counts[k] = tmp[k];
+    return MSGEMM_OK;
+}
+
+void msgemm_destroy(msgemm_handle *h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods}) dev_free(h, b->p);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,287 @@
+// Shared device-side definitions of the masked SpGEMM library (sm_103a).
+//
+// Problem (Sec. 2): C = M .* (A B) or C = !M .* (A B) over CSR operands on a
+// semiring; only M's pattern is used; an output entry exists iff the mask
+// allows it and at least one product was inserted (SET state, Sec. 5.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "msgemm.h"
+
+namespace msg {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+// Row kinds chosen by the binning pass (one accumulator form per kind).
+//   _W: one warp per row, table in a per-warp shared-memory slab
+//   _B: one CTA per row, table in the CTA's shared-memory slab
+//   _T: one CTA per row, dense MSA over column tiles (any n; heavy rows)
+enum Kind : int {
+    K_EMPTY = 0,   // no output possible (no product, or nothing allowed)
+    K_MSA_W,       // Sec. 5.2 MSA, dense states + values over all n columns
+    K_MSA_T,       // Sec. 5.2 MSA over column tiles, per-k cursors
+    K_HASH_W,      // Sec. 5.3 hash keyed by mask columns (load factor <= 0.5)
+    K_HASH_B,
+    K_MCA_W,       // Sec. 5.4 MCA: rank of j in the mask row by binary search
+    K_MCA_B,
+    K_DOT_W,       // Sec. 4.1 pull: per mask entry, A_i* . B_*j
+    K_DOT_B,
+    K_CHASH_W,     // complemented: hash keyed by produced columns
+    K_CHASH_B,
+    K_CMSA_T,      // complemented: MSA with NOTALLOWED default flipped, tiled
+    NKIND
+};
+
+// Families (msgemm_accumulator) for preference lists.
+enum Family : int { F_AUTO = 0, F_MSA = 1, F_HASH = 2, F_MCA = 3, F_DOT = 4 };
+
+// One product of a (possibly batched) call.  All pointers are device pointers.
+struct DevProd {
+    const int *m_rp, *m_ci;                  // mask M (m x n), pattern only
+    const int *a_rp, *a_ci; const void *a_v;  // A (m x k), rows enumerated
+    const int *b_rp, *b_ci; const void *b_v;  // B (k x n), rows enumerated (push)
+    const int *bt_rp, *bt_ci; const void *bt_v;  // B^T as CSR (n x k) for pull; may be null
+    int m, n, k;
+    int complement;
+    int a_sorted;                             // A rows ascending (needed by DOT's search)
+    long long row0;                           // first global row of this product
+    long long tile0;                          // first compaction tile of this product
+    long long abase;                          // first cursor slot (stored entries of A before this product)
+    long long tmp0;                           // first temporary-output slot of this product (plain mask)
+    int *c_rp, *c_ci; void *c_v; long long *c_nnz;  // outputs
+};
+
+// Up to one product by value (grid-constant parameter), else a device table.
+struct ProdSet {
+    int P;
+    const DevProd *tab;
+    DevProd p0;
+};
+
+__device__ __forceinline__ const DevProd &prod_at(const ProdSet &ps, int p) {
+    return ps.P == 1 ? ps.p0 : ps.tab[p];
+}
+
+// Product owning global row r (binary search over row0).
+__device__ __forceinline__ int prod_of_row(const ProdSet &ps, long long r) {
+    if (ps.P == 1) return 0;
+    int lo = 0, hi = ps.P - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ps.tab[mid].row0 <= r) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Per-row arrays of one pipeline run (workspace).
+struct RowArrays {
+    long long R;            // total rows over all products
+    long long *flops;       // products per row (push: sum of |B_k*| over A_i*)
+    long long *tmpoff;      // first slot of the row in the temporary output
+    int *cnt;               // entries kept in the row
+    unsigned char *kind;    // Kind of the row
+    int *perm;              // rows grouped by kind
+    int *kind_count;        // [NKIND] rows per kind
+    int *kind_off;          // [NKIND + 1] exclusive offsets into perm
+    int *kind_fill;         // [NKIND] scatter cursors
+    int *kind_next;         // [NKIND] dynamic work cursors (heavy kinds)
+    long long *bound_total; // complemented: total temporary room
+    int *any_dot;           // set when a row picked the pull kernel
+    unsigned *err;          // device error word
+};
+
+// Temporary output (sized by the mask for plain masks, by per-row bounds for
+// complemented ones); entries of a row are stored compacted from tmpoff.
+struct TmpOut {
+    int *ci;
+    void *v;
+};
+
+// Per-kind shared-memory budget and preference lists used by binning.
+constexpr int NCLASS = 16;
+struct Policy {
+    int force;                    // Family, F_AUTO = per-row choice
+    int allow_dot;
+    float dot_ratio;              // pull when pull_cost * dot_ratio < flops
+    int warp_flops_max;           // rows above go to CTA-level kinds
+    int slab[NKIND];              // bytes per warp (_W) or per CTA (_B, _T); 0 = disabled
+    int tileT[2];                 // MSA_T tile width for [plain, complemented]
+    unsigned char pref[NCLASS][4];  // families in preference order (F_AUTO = end)
+};
+
+__host__ __device__ __forceinline__ int row_class(long long flops, int mnz) {
+    int fb = flops <= 512 ? 0 : flops <= 8192 ? 1 : flops <= 131072 ? 2 : 3;
+    int mb = mnz <= 8 ? 0 : mnz <= 64 ? 1 : mnz <= 512 ? 2 : 3;
+    return fb * 4 + mb;
+}
+
+// Device error bits.
+enum : unsigned {
+    ERR_TIMEOUT = 1u,
+    ERR_INVALID = 2u,
+    ERR_UNSORTED = 4u,
+    ERR_INTERNAL = 8u,
+};
+
+// ------------------------------------------------------------------ semirings
+// acc_t: shared-memory accumulator; out_t: stored result; in_t: input value.
+template <int SR> struct Sr;
+
+template <> struct Sr<MSGEMM_PLUS_TIMES_F32> {
+    using in_t = float;
+    using acc_t = float;
+    using out_t = float;
+    static constexpr bool vals = true;      // inputs carry values
+    static constexpr bool count_set = false;  // SET state kept in a bit array
+    __device__ static __forceinline__ acc_t mul(in_t a, in_t b) { return a * b; }
+    __device__ static __forceinline__ void add(acc_t *p, acc_t v) { atomicAdd(p, v); }
+    __device__ static __forceinline__ out_t out(acc_t v) { return v; }
+};
+
+template <> struct Sr<MSGEMM_PLUS_TIMES_I64> {
+    using in_t = long long;
+    using acc_t = unsigned long long;
+    using out_t = long long;
+    static constexpr bool vals = true;
+    static constexpr bool count_set = false;
+    __device__ static __forceinline__ acc_t mul(in_t a, in_t b) {
+        return (unsigned long long)a * (unsigned long long)b;  // wraps mod 2^64
+    }
+    __device__ static __forceinline__ void add(acc_t *p, acc_t v) { atomicAdd(p, v); }
+    __device__ static __forceinline__ out_t out(acc_t v) { return (long long)v; }
+};
+
+// plus-pair: a count per entry, at most |A_i*| < 2^31, so 32 bits never wrap.
+template <> struct Sr<MSGEMM_PLUS_PAIR_I64> {
+    struct none_t {};
+    using in_t = none_t;
+    using acc_t = unsigned int;
+    using out_t = long long;
+    static constexpr bool vals = false;
+    static constexpr bool count_set = true;   // count > 0 <=> SET
+    __device__ static __forceinline__ acc_t mul(in_t, in_t) { return 1u; }
+    __device__ static __forceinline__ void add(acc_t *p, acc_t v) { atomicAdd(p, v); }
+    __device__ static __forceinline__ out_t out(acc_t v) { return (long long)v; }
+};
+
+template <int SR>
+__device__ __forceinline__ typename Sr<SR>::in_t load_val(const void *base, long long idx) {
+    if constexpr (Sr<SR>::vals) {
+        return __ldg(static_cast<const typename Sr<SR>::in_t *>(base) + idx);
+    } else {
+        return typename Sr<SR>::in_t{};
+    }
+}
+
+template <int SR> struct SrSizes {
+    static constexpr int acc = sizeof(typename Sr<SR>::acc_t);
+    static constexpr int in = Sr<SR>::vals ? (int)sizeof(typename Sr<SR>::in_t) : 0;
+    static constexpr int out = sizeof(typename Sr<SR>::out_t);
+    static constexpr bool setbits = !Sr<SR>::count_set;
+};
+
+// ------------------------------------------------------------------ sizing
+__host__ __device__ __forceinline__ long long pow2_at_least(long long x) {
+    long long p = 32;
+    while (p < x) p <<= 1;
+    return p;
+}
+__host__ __device__ __forceinline__ long long align8(long long x) { return (x + 7) & ~7LL; }
+__host__ __device__ __forceinline__ long long words32(long long bits) { return (bits + 31) >> 5; }
+
+// Hash (mask-keyed) table size: load factor 0.25 (Sec. 5.3) when it fits,
+// else 0.5.  Returns 0 if even 0.5 does not fit.
+__host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc, bool setbits, long long slab) {
+    long long extra = align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
+    long long h4 = pow2_at_least(4 * mnz), h2 = pow2_at_least(2 * mnz);
+    if (h4 * 8 + extra <= slab) return h4;
+    if (h2 * 8 + extra <= slab) return h2;
+    return 0;
+}
+__host__ __device__ __forceinline__ long long mca_bytes(long long mnz, int acc, bool setbits) {
+    return align8(4 * mnz) + align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
+}
+__host__ __device__ __forceinline__ long long dot_bytes(long long anz, long long mnz, int in, int acc, bool setbits) {
+    return align8(4 * anz) + align8(anz * in) + align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
+}
+__host__ __device__ __forceinline__ long long msa_bytes(long long ncols, int acc) {
+    return align8(ncols * acc) + 8 * words32(ncols);
+}
+// Complemented hash: keys + values for >= 2 x bound slots, plus the sorted
+// mask row for membership tests.  Returns slots or 0.
+__host__ __device__ __forceinline__ long long chash_slots(long long bound, long long mnz, int acc, long long slab) {
+    long long h = pow2_at_least(2 * bound);
+    long long bytes = align8(4 * h) + align8(h * acc) + align8(4 * mnz);
+    return bytes <= slab ? h : 0;
+}
+// MSA_T tile width for a slab: values + two bit arrays, multiple of 32.
+__host__ __device__ __forceinline__ int msa_tile_width(long long slab, int acc) {
+    long long t = (slab - 64) * 32 / (32 * acc + 8);
+    t &= ~31LL;
+    return t > 0 ? (int)t : 0;
+}
+
+// ------------------------------------------------------------------ teams
+// A team cooperates on one row: one warp (_W kinds) or the whole CTA.
+template <bool CTA> struct Team {
+    __device__ __forceinline__ int tid() const { return CTA ? (int)threadIdx.x : (int)(threadIdx.x & 31); }
+    __device__ __forceinline__ int size() const { return CTA ? (int)blockDim.x : 32; }
+    __device__ __forceinline__ int warp() const { return CTA ? (int)(threadIdx.x >> 5) : 0; }
+    __device__ __forceinline__ int nwarps() const { return CTA ? (int)(blockDim.x >> 5) : 1; }
+    __device__ __forceinline__ void sync() const {
+        if (CTA) __syncthreads(); else __syncwarp();
+    }
+};
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+__device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+    const int lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(FULL, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+// Exclusive scan of one int per thread over the CTA; `scratch` holds >= 33 ints.
+// Returns the exclusive prefix; *total receives the CTA sum.
+__device__ __forceinline__ int block_excl_scan(int v, int *scratch, int *total) {
+    const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int incl = warp_incl_scan(v);
+    if (lane == 31) scratch[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        int x = lane < nw ? scratch[lane] : 0;
+        int xi = warp_incl_scan(x);
+        if (lane < nw) scratch[lane] = xi - x;
+        if (lane == 31) scratch[32] = xi;
+    }
+    __syncthreads();
+    int res = scratch[w] + incl - v;
+    *total = scratch[32];
+    __syncthreads();
+    return res;
+}
+
+__device__ __forceinline__ unsigned hash32(unsigned key, int logH) {
+    return (key * 0x9E3779B1u) >> (32 - logH);
+}
+
+__host__ __device__ __forceinline__ int ilog2(long long x) {
+    int l = 0;
+    while ((1LL << l) < x) ++l;
+    return l;
+}
+
+}  // namespace msg

@@ -1,0 +1,58 @@
+// Host-side launchers shared between the translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace msg {
+
+struct RowLaunch;
+
+// Per semiring (rows_f32.cu, rows_i64.cu, rows_pp.cu).
+cudaError_t launch_bin_score_f32(const ProdSet &, const RowArrays &, const Policy &, long long *room, cudaStream_t, int nsm);
+cudaError_t launch_bin_score_i64(const ProdSet &, const RowArrays &, const Policy &, long long *room, cudaStream_t, int nsm);
+cudaError_t launch_bin_score_pp(const ProdSet &, const RowArrays &, const Policy &, long long *room, cudaStream_t, int nsm);
+cudaError_t launch_kind_f32(int kind, const ProdSet &, const RowLaunch &, cudaStream_t, int nsm);
+cudaError_t launch_kind_i64(int kind, const ProdSet &, const RowLaunch &, cudaStream_t, int nsm);
+cudaError_t launch_kind_pp(int kind, const ProdSet &, const RowLaunch &, cudaStream_t, int nsm);
+
+// Threads per CTA of each kind's kernel.
+inline int kind_threads(int kind) {
+    switch (kind) {
+    case K_MSA_W: return 128;
+    case K_MSA_T: case K_CMSA_T: return 512;
+    default: return 256;
+    }
+}
+inline bool kind_is_warp(int kind) {
+    return kind == K_MSA_W || kind == K_HASH_W || kind == K_MCA_W || kind == K_DOT_W || kind == K_CHASH_W;
+}
+// Dynamic shared memory of a kind's launch for a given slab.
+inline size_t kind_smem(int kind, int slab) {
+    return kind_is_warp(kind) ? (size_t)slab * (kind_threads(kind) / 32) : (size_t)slab;
+}
+
+// pipeline.cu
+cudaError_t launch_bin_scatter(const RowArrays &, cudaStream_t, int nsm);
+cudaError_t launch_scan_room(const RowArrays &, const long long *room, long long comp_base, long long *tile_buf,
+                             long long *total, cudaStream_t, int nsm);
+cudaError_t launch_count_tiles(const ProdSet &, const RowArrays &, long long ntiles, long long *tile_sums,
+                               long long *tile_offs, long long *prod_totals, cudaStream_t, int nsm);
+cudaError_t launch_compact(const ProdSet &, const RowArrays &, const TmpOut &, long long ntiles,
+                           const long long *tile_offs, int out_bytes, cudaStream_t, int nsm);
+cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t, int nsm);
+cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t, int nsm);
+cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows,
+                                  const int *trp, int *cursor, int *tci, void *tv, const int *gate,
+                                  cudaStream_t, int nsm);
+cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, long long nnz, unsigned *err,
+                            cudaStream_t, int nsm);
+cudaError_t launch_reduce_sum(int semiring, const void *vals, const long long *d_nnz, void *d_sum, cudaStream_t,
+                              int nsm);
+cudaError_t launch_sort_heavy(const RowArrays &, int kind, cudaStream_t);
+
+constexpr int CTILE = 1024;        // rows per compaction tile
+constexpr int STILE = 2048;        // elements per generic scan tile
+
+}  // namespace msg

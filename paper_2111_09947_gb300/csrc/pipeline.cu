@@ -1,0 +1,479 @@
+// Pipeline kernels that do not depend on the semiring: bucket scatter of the
+// binned rows, scans, compaction of the one-phase output (Sec. 6: the output
+// is first written into room sized by the mask, then copied out), the
+// transpose used by the pull kernel and the backward products, input
+// validation and the value reduction (triangle count, Sec. 8.2).
+#include <algorithm>
+
+#include "launch.h"
+
+namespace msg {
+
+static int grid_cap(long long work_blocks, int nsm, int per_sm) {
+    long long g = std::min<long long>(work_blocks, (long long)nsm * per_sm);
+    return (int)std::max<long long>(1, g);
+}
+
+// ------------------------------------------------------------ bucket scatter
+// perm holds the rows grouped by kind; within a kind the order is arbitrary.
+__global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ RowArrays ra) {
+    __shared__ int off[NKIND + 1];
+    __shared__ int loc[NKIND];
+    __shared__ int base[NKIND];
+    if (threadIdx.x == 0) {
+        off[0] = 0;
+        for (int k = 0; k < NKIND; ++k) off[k + 1] = off[k] + ra.kind_count[k];
+        if (blockIdx.x == 0)
+            for (int k = 0; k <= NKIND; ++k) ra.kind_off[k] = off[k];
+    }
+    for (long long r0 = (long long)blockIdx.x * blockDim.x; r0 < ra.R; r0 += (long long)gridDim.x * blockDim.x) {
+        if (threadIdx.x < NKIND) loc[threadIdx.x] = 0;
+        __syncthreads();
+        const long long r = r0 + threadIdx.x;
+        int k = -1, rank = 0;
+        if (r < ra.R) {
+            k = ra.kind[r];
+            if (k != K_EMPTY) rank = atomicAdd(&loc[k], 1);
+        }
+        __syncthreads();
+        if (threadIdx.x < NKIND && loc[threadIdx.x]) base[threadIdx.x] = atomicAdd(&ra.kind_fill[threadIdx.x], loc[threadIdx.x]);
+        __syncthreads();
+        if (k > K_EMPTY) ra.perm[off[k] + base[k] + rank] = (int)r;
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_bin_scatter(const RowArrays &ra, cudaStream_t st, int nsm) {
+    if (ra.R == 0) return cudaSuccess;
+    k_bin_scatter<<<grid_cap((ra.R + 255) / 256, nsm, 8), 256, 0, st>>>(ra);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ generic scans
+// Block-wide exclusive scan of int64 values (256 threads).
+__device__ __forceinline__ long long block_excl_scan_ll(long long v, long long *sh, long long *total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        long long t = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) sh[w] = incl;
+    __syncthreads();
+    if (w == 0) {
+        long long x = lane < nw ? sh[lane] : 0;
+        long long xi = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            long long t = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += t;
+        }
+        if (lane < nw) sh[lane] = xi - x;
+        if (lane == 31) sh[32] = xi;
+    }
+    __syncthreads();
+    long long res = sh[w] + incl - v;
+    *total = sh[32];
+    __syncthreads();
+    return res;
+}
+
+// Single-block exclusive scan in place over n values; *total = sum.
+__global__ void __launch_bounds__(1024) k_scan_small_ll(long long *v, long long n, long long *total) {
+    __shared__ long long sh[33];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < n; b += blockDim.x) {
+        const long long x = b + threadIdx.x;
+        const long long val = x < n ? v[x] : 0;
+        long long tot;
+        const long long ex = block_excl_scan_ll(val, sh, &tot);
+        if (x < n) v[x] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Tile sums of an int64 array (tiles of STILE elements, 256 threads).
+__global__ void __launch_bounds__(256) k_tile_sums_ll(const long long *in, long long n, long long *sums, long long ntiles) {
+    __shared__ long long sh[33];
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long s = 0;
+        for (long long x = t * STILE + threadIdx.x; x < std::min(n, (t + 1) * STILE); x += blockDim.x) s += in[x];
+        long long tot;
+        block_excl_scan_ll(s, sh, &tot);
+        if (threadIdx.x == 0) sums[t] = tot;
+    }
+}
+
+// Complemented rows: tmpoff[r] = comp_base + exclusive prefix of room[] for
+// rows with room > 0.
+__global__ void __launch_bounds__(256) k_room_apply(const long long *room, long long *tmpoff, long long n,
+                                                    const long long *tile_offs, long long comp_base, long long ntiles) {
+    __shared__ long long sh[33];
+    constexpr int PER = STILE / 256;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long x0 = t * STILE + (long long)threadIdx.x * PER;
+        long long v[PER];
+        long long s = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            v[u] = (x0 + u < n) ? room[x0 + u] : 0;
+            s += v[u];
+        }
+        long long tot;
+        long long ex = block_excl_scan_ll(s, sh, &tot) + tile_offs[t] + comp_base;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            if (x0 + u < n && v[u] > 0) tmpoff[x0 + u] = ex;
+            ex += v[u];
+        }
+    }
+}
+
+cudaError_t launch_scan_room(const RowArrays &ra, const long long *room, long long comp_base, long long *tile_buf,
+                             long long *total, cudaStream_t st, int nsm) {
+    const long long n = ra.R;
+    if (n == 0) return cudaMemsetAsync(total, 0, sizeof(long long), st);
+    const long long nt = (n + STILE - 1) / STILE;
+    k_tile_sums_ll<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, n, tile_buf, nt);
+    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, total);
+    k_room_apply<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, ra.tmpoff, n, tile_buf, comp_base, nt);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ compaction
+__device__ __forceinline__ int prod_of_tile(const ProdSet &ps, long long t) {
+    if (ps.P == 1) return 0;
+    int lo = 0, hi = ps.P - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (ps.tab[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Sum of kept counts per compaction tile (CTILE rows of one product).
+__global__ void __launch_bounds__(256) k_count_tiles(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
+                                                     long long ntiles, long long *sums) {
+    __shared__ long long sh[33];
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const DevProd &P = prod_at(ps, prod_of_tile(ps, t));
+        const long long lt = t - P.tile0;
+        const long long r0 = P.row0 + lt * CTILE;
+        const long long r1 = P.row0 + std::min<long long>(P.m, (lt + 1) * CTILE);
+        long long s = 0;
+        for (long long r = r0 + threadIdx.x; r < r1; r += blockDim.x) s += ra.cnt[r];
+        long long tot;
+        block_excl_scan_ll(s, sh, &tot);
+        if (threadIdx.x == 0) sums[t] = tot;
+    }
+}
+
+// Exclusive scan of tile sums, restarted per product; writes each product's
+// entry count to *c_nnz, c_rp[m] and prod_totals[p].
+__global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ ProdSet ps, long long ntiles,
+                                                     const long long *sums, long long *offs, long long *prod_base,
+                                                     long long *prod_totals) {
+    __shared__ long long sh[33];
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long b = 0; b < ntiles; b += blockDim.x) {
+        const long long x = b + threadIdx.x;
+        const long long val = x < ntiles ? sums[x] : 0;
+        long long tot;
+        const long long ex = block_excl_scan_ll(val, sh, &tot);
+        if (x < ntiles) offs[x] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    for (int p = threadIdx.x; p < ps.P; p += blockDim.x) {
+        const DevProd &P = prod_at(ps, p);
+        const long long nt = (P.m + CTILE - 1) / CTILE;
+        long long base = 0, total = 0;
+        if (nt > 0) {
+            base = offs[P.tile0];
+            total = offs[P.tile0 + nt - 1] + sums[P.tile0 + nt - 1] - base;
+        }
+        prod_base[p] = base;
+        prod_totals[p] = total;
+        *P.c_nnz = total;
+        P.c_rp[P.m] = (int)total;
+    }
+    __syncthreads();
+    for (long long t = threadIdx.x; t < ntiles; t += blockDim.x) offs[t] -= prod_base[prod_of_tile(ps, t)];
+}
+
+cudaError_t launch_count_tiles(const ProdSet &ps, const RowArrays &ra, long long ntiles, long long *tile_sums,
+                               long long *tile_offs, long long *prod_totals, cudaStream_t st, int nsm) {
+    if (ntiles > 0) k_count_tiles<<<grid_cap(ntiles, nsm, 8), 256, 0, st>>>(ps, ra, ntiles, tile_sums);
+    // prod_totals holds 2 * P entries: [0, P) bases, [P, 2P) totals
+    k_scan_tiles<<<1, 1024, 0, st>>>(ps, ntiles, tile_sums, tile_offs, prod_totals, prod_totals + ps.P);
+    return cudaGetLastError();
+}
+
+// Row pointers of C from the tile offsets and a block scan of the counts;
+// then each warp copies the kept entries of its rows out of the temporary room.
+template <int OUTB>
+__global__ void __launch_bounds__(256) k_compact(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
+                                                 const __grid_constant__ TmpOut tmp, long long ntiles,
+                                                 const long long *offs) {
+    using V = typename std::conditional<OUTB == 4, unsigned, unsigned long long>::type;
+    __shared__ long long sh[33];
+    __shared__ int rowoff[CTILE];
+    constexpr int PER = CTILE / 256;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const DevProd &P = prod_at(ps, prod_of_tile(ps, t));
+        const long long lt = t - P.tile0;
+        const int i0 = (int)(lt * CTILE);
+        const int i1 = (int)std::min<long long>(P.m, (lt + 1) * CTILE);
+        int c[PER];
+        long long s = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = i0 + threadIdx.x * PER + u;
+            c[u] = i < i1 ? ra.cnt[P.row0 + i] : 0;
+            s += c[u];
+        }
+        long long tot;
+        long long ex = block_excl_scan_ll(s, sh, &tot) + offs[t];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int il = threadIdx.x * PER + u;
+            if (i0 + il < i1) {
+                rowoff[il] = (int)ex;
+                P.c_rp[i0 + il] = (int)ex;
+            }
+            ex += c[u];
+        }
+        __syncthreads();
+        const V *src = static_cast<const V *>(tmp.v);
+        V *dst = static_cast<V *>(P.c_v);
+        for (int il = w; il < i1 - i0; il += blockDim.x >> 5) {
+            const long long r = P.row0 + i0 + il;
+            const int cnt = ra.cnt[r];
+            if (cnt == 0) continue;
+            const long long so = ra.tmpoff[r];
+            const int d0 = rowoff[il];
+            for (int x = lane; x < cnt; x += 32) {
+                P.c_ci[d0 + x] = tmp.ci[so + x];
+                dst[d0 + x] = src[so + x];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_compact(const ProdSet &ps, const RowArrays &ra, const TmpOut &tmp, long long ntiles,
+                           const long long *tile_offs, int out_bytes, cudaStream_t st, int nsm) {
+    if (ntiles == 0) return cudaSuccess;
+    const int g = grid_cap(ntiles, nsm, 8);
+    if (out_bytes == 4) k_compact<4><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs);
+    else k_compact<8><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ transpose
+__global__ void __launch_bounds__(256) k_col_counts(const int *ci, long long nnz, int *counts) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&counts[ci[t]], 1);
+}
+
+cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t st, int nsm) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * ((size_t)ncols + 1), st);
+    if (e != cudaSuccess || nnz == 0) return e;
+    k_col_counts<<<grid_cap((nnz + 255) / 256, nsm, 8), 256, 0, st>>>(ci, nnz, counts);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(256) k_tile_sums_int(const int *in, long long n, long long *sums, long long ntiles) {
+    __shared__ long long sh[33];
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        long long s = 0;
+        for (long long x = t * STILE + threadIdx.x; x < std::min(n, (t + 1) * STILE); x += blockDim.x) s += in[x];
+        long long tot;
+        block_excl_scan_ll(s, sh, &tot);
+        if (threadIdx.x == 0) sums[t] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scan_apply_int(const int *in, long long n, int *out, const long long *tile_offs,
+                                                        long long ntiles, const long long *total) {
+    __shared__ long long sh[33];
+    constexpr int PER = STILE / 256;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long x0 = t * STILE + (long long)threadIdx.x * PER;
+        int v[PER];
+        long long s = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            v[u] = (x0 + u < n) ? in[x0 + u] : 0;
+            s += v[u];
+        }
+        long long tot;
+        long long ex = block_excl_scan_ll(s, sh, &tot) + tile_offs[t];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            if (x0 + u < n) out[x0 + u] = (int)ex;
+            ex += v[u];
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[n] = (int)*total;
+}
+
+// out[0..n] = exclusive scan of in[0..n) followed by the total.
+cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t st, int nsm) {
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
+    const long long nt = (n + STILE - 1) / STILE;
+    k_tile_sums_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, tile_buf, nt);
+    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, tile_buf + nt);
+    k_scan_apply_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, out, tile_buf, nt, tile_buf + nt);
+    return cudaGetLastError();
+}
+
+// Scatter of A's entries into the rows of A^T; cursor starts as a copy of
+// the transpose's row pointers.  Rows of A^T come out in arbitrary order.
+// With gate != NULL the kernel does nothing unless *gate is set.
+template <int VB>
+__global__ void __launch_bounds__(256) k_transpose_fill(const int *rp, const int *ci, const void *v, int nrows,
+                                                        int *cursor, int *tci, void *tv, const int *gate) {
+    if (gate && *gate == 0) return;
+    using V = typename std::conditional<VB == 4, unsigned, unsigned long long>::type;
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = gw; i < nrows; i += nw) {
+        const int s = rp[i], e = rp[i + 1];
+        for (int t = s + lane; t < e; t += 32) {
+            const int pos = atomicAdd(&cursor[ci[t]], 1);
+            tci[pos] = (int)i;
+            if (VB) static_cast<V *>(tv)[pos] = static_cast<const V *>(v)[t];
+        }
+    }
+}
+
+cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows, const int *trp,
+                                  int *cursor, int *tci, void *tv, const int *gate, cudaStream_t st, int nsm) {
+    if (nrows == 0) return cudaSuccess;
+    (void)trp;
+    const int g = grid_cap(((long long)nrows + 7) / 8, nsm, 16);
+    if (vbytes == 4) k_transpose_fill<4><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate);
+    else if (vbytes == 8) k_transpose_fill<8><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate);
+    else k_transpose_fill<0><<<g, 256, 0, st>>>(rp, ci, nullptr, nrows, cursor, tci, nullptr, gate);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ validation
+// Row pointers non-decreasing from 0 to nnz, columns in [0, ncols) and
+// strictly ascending within a row.  Failures set bits of *err.
+__global__ void __launch_bounds__(256) k_validate(const int *rp, const int *ci, int nrows, int ncols, long long nnz,
+                                                  unsigned *err) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    if (gw == 0 && lane == 0 && (rp[0] != 0 || rp[nrows] != nnz)) atomicOr(err, ERR_INVALID);
+    for (long long i = gw; i < nrows; i += nw) {
+        int s = rp[i], e = rp[i + 1];
+        if (e < s || s < 0 || (long long)e > nnz) {
+            if (lane == 0) atomicOr(err, ERR_INVALID);
+            continue;   // never read entries through an invalid row pointer
+        }
+        bool bad = false, unsorted = false;
+        for (int t = s + lane; t < e; t += 32) {
+            const int c = ci[t];
+            bad |= (c < 0 || c >= ncols);
+            if (t > s) unsorted |= (ci[t - 1] >= c);
+        }
+        if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, ERR_INVALID);
+        if (__any_sync(FULL, unsorted) && lane == 0) atomicOr(err, ERR_UNSORTED);
+    }
+}
+
+cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, long long nnz, unsigned *err,
+                            cudaStream_t st, int nsm) {
+    k_validate<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, ncols, nnz, err);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ value sum
+template <int SR>
+__global__ void __launch_bounds__(256) k_reduce_sum(const void *vals, const long long *d_nnz, void *out) {
+    const long long n = *d_nnz;
+    const int lane = threadIdx.x & 31;
+    if (SR == MSGEMM_PLUS_TIMES_F32) {
+        double s = 0.0;
+        for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+            s += (double)static_cast<const float *>(vals)[x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) atomicAdd(static_cast<double *>(out), s);
+    } else {
+        unsigned long long s = 0;
+        for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x)
+            s += static_cast<const unsigned long long *>(vals)[x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+        if (lane == 0) atomicAdd(static_cast<unsigned long long *>(out), s);
+    }
+}
+
+cudaError_t launch_reduce_sum(int semiring, const void *vals, const long long *d_nnz, void *d_sum, cudaStream_t st,
+                              int nsm) {
+    cudaError_t e = cudaMemsetAsync(d_sum, 0, 8, st);
+    if (e != cudaSuccess) return e;
+    if (semiring == MSGEMM_PLUS_TIMES_F32) k_reduce_sum<MSGEMM_PLUS_TIMES_F32><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum);
+    else k_reduce_sum<MSGEMM_PLUS_TIMES_I64><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ heavy-row order
+// Sorts a heavy kind's bucket by descending flops (single CTA bitonic sort,
+// buckets of up to 4096 rows; larger buckets keep the binned order), so the
+// dynamic row queue starts with the longest rows.
+__global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ RowArrays ra, int kind) {
+    __shared__ long long key[4096];
+    __shared__ int val[4096];
+    const int n = ra.kind_count[kind];
+    if (n <= 1 || n > 4096) return;
+    const int off = ra.kind_off[kind];
+    int N = 1;
+    while (N < n) N <<= 1;
+    for (int x = threadIdx.x; x < N; x += blockDim.x) {
+        if (x < n) {
+            val[x] = ra.perm[off + x];
+            key[x] = -ra.flops[val[x]];
+        } else {
+            val[x] = -1;
+            key[x] = LLONG_MAX;
+        }
+    }
+    __syncthreads();
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = threadIdx.x; x < N / 2; x += blockDim.x) {
+                const int lo = 2 * j * (x / j) + (x % j), hi = lo + j;
+                const bool up = (lo & k) == 0;
+                if ((key[lo] > key[hi]) == up) {
+                    const long long tk = key[lo]; key[lo] = key[hi]; key[hi] = tk;
+                    const int tv = val[lo]; val[lo] = val[hi]; val[hi] = tv;
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int x = threadIdx.x; x < n; x += blockDim.x) ra.perm[off + x] = val[x];
+}
+
+cudaError_t launch_sort_heavy(const RowArrays &ra, int kind, cudaStream_t st) {
+    k_sort_heavy<<<1, 1024, 0, st>>>(ra, kind);
+    return cudaGetLastError();
+}
+
+}  // namespace msg

@@ -1,0 +1,764 @@
+// Row accumulators of the masked SpGEMM (Sec. 4-5), one team per row.
+//
+// Every kernel here is persistent: it walks the rows the binning pass put in
+// its kind's bucket, so the host never needs the bucket sizes.  Each row
+// writes its kept entries, in ascending column order, to its slot range of
+// the temporary output and its count to cnt[r]; compaction follows.
+//
+// Push kinds enumerate the products A_ik * B_kj of row i (Gustavson order,
+// Sec. 4.2): the outer list is A_i*, the inner rows are B_k*.  The pull kind
+// (DOT) enumerates pairs (mask entry j, entry k of column B_*j) and looks k up
+// in the staged row A_i* (Sec. 4.1).
+#pragma once
+
+#include "common.cuh"
+
+namespace msg {
+
+constexpr unsigned long long EMPTY64 = ~0ULL;
+constexpr unsigned EMPTY32 = 0xffffffffu;
+
+// Launch parameters of one accumulator kernel.
+struct RowLaunch {
+    RowArrays ra;
+    TmpOut tmp;
+    int slab;          // shared bytes per warp (_W) or per CTA (_B, _T)
+    int tileT;         // column tile width of _T kinds
+    int4 *cursors;     // _T kinds: one cursor per stored entry of A (global)
+    int aligned;       // 1: write values only, at the mask entry's own slot (tmp + rank);
+                       //    the output array is zeroed beforehand (gradient form)
+};
+
+template <int SR>
+__device__ __forceinline__ typename Sr<SR>::in_t shfl_val(typename Sr<SR>::in_t v, int src) {
+    if constexpr (Sr<SR>::vals) return __shfl_sync(FULL, v, src);
+    else return v;
+}
+
+__device__ __forceinline__ bool test_bit(const unsigned *w, int b) { return (w[b >> 5] >> (b & 31)) & 1u; }
+__device__ __forceinline__ void set_bit_once(unsigned *w, int b) {
+    unsigned m = 1u << (b & 31);
+    if (!(w[b >> 5] & m)) atomicOr(&w[b >> 5], m);
+}
+
+// --------------------------------------------------------------- enumerators
+// Calls f(t, a_t, col, val) for every (outer position t in [o0, o1), inner
+// entry q of row oci[t]) pair, with col = ici[q], val = iv[q].  Warps of the
+// team take 32-entry windows of the outer list.  Strided mode: the warp walks
+// the inner rows of a window one by one, lanes striding each row (4 loads in
+// flight per lane).  Flat mode (short inner rows): the products of a window
+// are numbered 0..total-1 and each lane finds its inner row by a binary search
+// over the window's inclusive prefix of row lengths.
+template <int SR, bool CTA, bool OUTV, class F>
+__device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
+                                              const int *__restrict__ irp, const int *__restrict__ ici,
+                                              const void *iv, bool flat, F &f) {
+    using in_t = typename Sr<SR>::in_t;
+    Team<CTA> team;
+    const int lane = lane_id();
+    for (int w0 = o0 + team.warp() * 32; w0 < o1; w0 += team.nwarps() * 32) {
+        const int t = w0 + lane;
+        int s = 0, e = 0;
+        in_t av{};
+        if (t < o1) {
+            const int c = __ldg(oci + t);
+            s = __ldg(irp + c);
+            e = __ldg(irp + c + 1);
+            if constexpr (OUTV) av = load_val<SR>(ov, t);
+        }
+        if (!flat) {
+            const int nu = min(32, o1 - w0);
+            for (int u = 0; u < nu; ++u) {
+                const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
+                const in_t au = shfl_val<SR>(av, u);
+                for (int q0 = su; q0 < eu; q0 += 128) {
+                    int col[4];
+                    in_t bv[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const int q = q0 + x * 32 + lane;
+                        col[x] = -1;
+                        if (q < eu) {
+                            col[x] = __ldg(ici + q);
+                            bv[x] = load_val<SR>(iv, q);
+                        }
+                    }
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if (col[x] >= 0) f(w0 + u, au, col[x], bv[x]);
+                }
+            }
+        } else {
+            const int len = e - s;
+            const int incl = warp_incl_scan(len);
+            const int total = __shfl_sync(FULL, incl, 31);
+            const int excl = incl - len;
+            for (int base = 0; base < total; base += 32) {
+                const int p = base + lane;
+                int k = 0;
+#pragma unroll
+                for (int st = 16; st > 0; st >>= 1) {
+                    const int c = __shfl_sync(FULL, incl, k + st - 1);
+                    if (c <= p) k += st;
+                }
+                const int sk = __shfl_sync(FULL, s, k & 31), xk = __shfl_sync(FULL, excl, k & 31);
+                const in_t ak = shfl_val<SR>(av, k & 31);
+                if (p < total) {
+                    const int q = sk + p - xk;
+                    f(w0 + k, ak, __ldg(ici + q), load_val<SR>(iv, q));
+                }
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ gather
+// Ordered output of rank-indexed accumulators (HASH, MCA, DOT): entries of
+// the mask row in mask order whose state is SET (Sec. 5.2: "gathered in the
+// same order as they are ordered in the mask", stable and sorted).
+template <int SR, bool CTA>
+__device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const typename Sr<SR>::acc_t *acc,
+                                              const unsigned *sb, long long tmp, const TmpOut &T,
+                                              int *cnt_slot, int *scratch, int aligned) {
+    using S = Sr<SR>;
+    using out_t = typename S::out_t;
+    Team<CTA> team;
+    const int lane = lane_id();
+    out_t *tv = static_cast<out_t *>(T.v);
+    auto kept = [&](int q) -> bool {
+        if constexpr (S::count_set) return acc[q] != 0;
+        else return test_bit(sb, q);
+    };
+    if (aligned) {
+        for (int q = team.tid(); q < mnz; q += team.size())
+            if (kept(q)) tv[tmp + q] = S::out(acc[q]);
+        return;
+    }
+    if (!CTA) {
+        int base = 0;
+        for (int r0 = 0; r0 < mnz; r0 += 32) {
+            const int q = r0 + lane;
+            const bool keep = q < mnz && kept(q);
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                const long long o = tmp + base + __popc(bal & lanemask_lt());
+                T.ci[o] = mcols[q];
+                tv[o] = S::out(acc[q]);
+            }
+            base += __popc(bal);
+        }
+        if (lane == 0) *cnt_slot = base;
+    } else {
+        const int nw = team.nwarps(), w = team.warp();
+        const int seg = ((mnz + nw - 1) / nw + 31) & ~31;
+        const int s0 = min(mnz, w * seg), s1 = min(mnz, s0 + seg);
+        int c = 0;
+        for (int r0 = s0; r0 < s1; r0 += 32) {
+            const int q = r0 + lane;
+            c += __popc(__ballot_sync(FULL, q < s1 && kept(q)));
+        }
+        int total;
+        const int off = block_excl_scan(lane == 0 ? c : 0, scratch, &total);
+        int base = __shfl_sync(FULL, off, 0);
+        for (int r0 = s0; r0 < s1; r0 += 32) {
+            const int q = r0 + lane;
+            const bool keep = q < s1 && kept(q);
+            const unsigned bal = __ballot_sync(FULL, keep);
+            if (keep) {
+                const long long o = tmp + base + __popc(bal & lanemask_lt());
+                T.ci[o] = mcols[q];
+                tv[o] = S::out(acc[q]);
+            }
+            base += __popc(bal);
+        }
+        if (threadIdx.x == 0) *cnt_slot = total;
+    }
+}
+
+// Row context.
+struct RowCtx {
+    int i, n;
+    int a0, a1, m0, m1;
+    long long r, tmp, flops;
+};
+
+__device__ __forceinline__ RowCtx row_ctx(const DevProd &P, long long r, const RowArrays &ra) {
+    RowCtx c;
+    c.r = r;
+    c.i = (int)(r - P.row0);
+    c.n = P.n;
+    c.a0 = __ldg(P.a_rp + c.i);
+    c.a1 = __ldg(P.a_rp + c.i + 1);
+    c.m0 = __ldg(P.m_rp + c.i);
+    c.m1 = __ldg(P.m_rp + c.i + 1);
+    c.tmp = ra.tmpoff[r];
+    c.flops = ra.flops[r];
+    return c;
+}
+
+__device__ __forceinline__ bool flat_mode(const RowCtx &c) {
+    // average inner row shorter than 12: load-balanced flat enumeration
+    return c.flops < 12LL * (long long)(c.a1 - c.a0);
+}
+
+// --------------------------------------------------------------- HASH rows
+// Sec. 5.3: open addressing, linear probing, no resizing, keyed by the mask's
+// columns; a slot holds (column, rank in the mask row).  Values live in a
+// rank-indexed array so the gather runs in mask order.
+template <int SR, bool CTA>
+__device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab, int *scratch) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    Team<CTA> team;
+    const int mnz = c.m1 - c.m0;
+    const long long H = hash_slots(mnz, (int)sizeof(acc_t), SrSizes<SR>::setbits, L.slab);
+    const int logH = ilog2(H);
+    const unsigned hmask = (unsigned)H - 1u;
+    unsigned long long *tab = reinterpret_cast<unsigned long long *>(slab);
+    acc_t *acc = reinterpret_cast<acc_t *>(slab + H * 8);
+    unsigned *sb = reinterpret_cast<unsigned *>(slab + H * 8 + align8((long long)mnz * sizeof(acc_t)));
+    for (long long h = team.tid(); h < H; h += team.size()) tab[h] = EMPTY64;
+    for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
+    if constexpr (SrSizes<SR>::setbits)
+        for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
+    team.sync();
+    for (int q = team.tid(); q < mnz; q += team.size()) {   // setAllowed for every mask column
+        const unsigned j = (unsigned)__ldg(P.m_ci + c.m0 + q);
+        unsigned h = hash32(j, logH);
+        const unsigned long long ent = ((unsigned long long)q << 32) | j;
+        while (atomicCAS(&tab[h], EMPTY64, ent) != EMPTY64) h = (h + 1) & hmask;
+    }
+    team.sync();
+    auto ins = [&](int, in_t a, int j, in_t b) {
+        unsigned h = hash32((unsigned)j, logH);
+        for (;;) {   // terminates: at least half of the slots are empty
+            const unsigned long long e = tab[h];
+            const unsigned key = (unsigned)e;
+            if (key == (unsigned)j) {
+                const int rk = (int)(e >> 32);
+                S::add(&acc[rk], S::mul(a, b));
+                if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
+                return;
+            }
+            if (key == EMPTY32) return;   // NOTALLOWED: product never evaluated
+            h = (h + 1) & hmask;
+        }
+    };
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    team.sync();
+    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    team.sync();
+}
+
+// --------------------------------------------------------------- MCA rows
+// Sec. 5.4: arrays of length nnz(m) indexed by the rank of j in the mask row;
+// the rank comes from a binary search in the staged (sorted) mask row.
+template <int SR, bool CTA>
+__device__ __forceinline__ void row_mca(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab, int *scratch) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    Team<CTA> team;
+    const int mnz = c.m1 - c.m0;
+    int *mcol = reinterpret_cast<int *>(slab);
+    acc_t *acc = reinterpret_cast<acc_t *>(slab + align8(4LL * mnz));
+    unsigned *sb = reinterpret_cast<unsigned *>(slab + align8(4LL * mnz) + align8((long long)mnz * sizeof(acc_t)));
+    for (int q = team.tid(); q < mnz; q += team.size()) {
+        mcol[q] = __ldg(P.m_ci + c.m0 + q);
+        acc[q] = 0;
+    }
+    if constexpr (SrSizes<SR>::setbits)
+        for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
+    team.sync();
+    auto ins = [&](int, in_t a, int j, in_t b) {
+        int lo = 0, hi = mnz;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (mcol[mid] < j) lo = mid + 1; else hi = mid;
+        }
+        if (lo < mnz && mcol[lo] == j) {
+            S::add(&acc[lo], S::mul(a, b));
+            if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, lo);
+        }
+    };
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    team.sync();
+    gather_ranked<SR, CTA>(mcol, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    team.sync();
+}
+
+// --------------------------------------------------------------- DOT rows
+// Sec. 4.1 pull: for each mask entry (i, j), the sparse dot A_i* . B_*j.  A_i*
+// is staged in shared memory; the pairs (j, k in column j of B) are
+// enumerated and k is found in A_i* by binary search.
+template <int SR, bool CTA>
+__device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab, int *scratch) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    Team<CTA> team;
+    const int mnz = c.m1 - c.m0, anz = c.a1 - c.a0;
+    int *acol = reinterpret_cast<int *>(slab);
+    in_t *aval = reinterpret_cast<in_t *>(slab + align8(4LL * anz));
+    const long long avb = Sr<SR>::vals ? align8((long long)anz * sizeof(in_t)) : 0;
+    acc_t *acc = reinterpret_cast<acc_t *>(slab + align8(4LL * anz) + avb);
+    unsigned *sb = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(acc) + align8((long long)mnz * sizeof(acc_t)));
+    for (int q = team.tid(); q < anz; q += team.size()) {
+        acol[q] = __ldg(P.a_ci + c.a0 + q);
+        if constexpr (Sr<SR>::vals) aval[q] = load_val<SR>(P.a_v, c.a0 + q);
+    }
+    for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
+    if constexpr (SrSizes<SR>::setbits)
+        for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
+    team.sync();
+    const int m0 = c.m0;
+    auto ins = [&](int t, in_t, int k, in_t b) {
+        int lo = 0, hi = anz;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (acol[mid] < k) lo = mid + 1; else hi = mid;
+        }
+        if (lo < anz && acol[lo] == k) {
+            const int rk = t - m0;
+            in_t a{};
+            if constexpr (Sr<SR>::vals) a = aval[lo];
+            S::add(&acc[rk], S::mul(a, b));
+            if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
+        }
+    };
+    const bool flat = true;   // pull pairs: columns of B are short in this regime
+    enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, P.bt_rp, P.bt_ci, P.bt_v, flat, ins);
+    team.sync();
+    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    team.sync();
+}
+
+// --------------------------------------------------------------- MSA_W rows
+// Sec. 5.2 MSA per warp: dense values and two bit arrays (ALLOWED, SET) over
+// all n columns.  Invariant between rows: everything zero; a row resets only
+// the positions of its own mask entries (O(nnz(m)), not O(n)).
+template <int SR>
+__device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    const int lane = lane_id();
+    const int n = c.n;
+    acc_t *vals = reinterpret_cast<acc_t *>(slab);
+    unsigned *allowed = reinterpret_cast<unsigned *>(slab + align8((long long)n * sizeof(acc_t)));
+    unsigned *setw = allowed + words32(n);
+    for (int q = c.m0 + lane; q < c.m1; q += 32) {
+        const int j = __ldg(P.m_ci + q);
+        atomicOr(&allowed[j >> 5], 1u << (j & 31));
+    }
+    __syncwarp();
+    auto ins = [&](int, in_t a, int j, in_t b) {
+        if (test_bit(allowed, j)) {
+            S::add(&vals[j], S::mul(a, b));
+            if constexpr (SrSizes<SR>::setbits) set_bit_once(setw, j);
+        }
+    };
+    enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    __syncwarp();
+    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    int base = 0;
+    if (L.aligned) {
+        for (int q = c.m0 + lane; q < c.m1; q += 32) {
+            const int j = __ldg(P.m_ci + q);
+            bool keep;
+            if constexpr (S::count_set) keep = vals[j] != 0;
+            else keep = test_bit(setw, j);
+            if (keep) tv[c.tmp + (q - c.m0)] = S::out(vals[j]);
+        }
+    } else
+    for (int q0 = c.m0; q0 < c.m1; q0 += 32) {
+        const int q = q0 + lane;
+        int j = 0;
+        bool keep = false;
+        if (q < c.m1) {
+            j = __ldg(P.m_ci + q);
+            if constexpr (S::count_set) keep = vals[j] != 0;
+            else keep = test_bit(setw, j);
+        }
+        const unsigned bal = __ballot_sync(FULL, keep);
+        if (keep) {
+            const long long o = c.tmp + base + __popc(bal & lanemask_lt());
+            L.tmp.ci[o] = j;
+            tv[o] = S::out(vals[j]);
+        }
+        base += __popc(bal);
+    }
+    if (lane == 0) L.ra.cnt[c.r] = base;
+    __syncwarp();
+    for (int q = c.m0 + lane; q < c.m1; q += 32) {
+        const int j = __ldg(P.m_ci + q);
+        vals[j] = 0;
+        allowed[j >> 5] = 0;
+        setw[j >> 5] = 0;
+    }
+    __syncwarp();
+}
+
+// --------------------------------------------------------------- CHASH rows
+// Complemented mask, hash keyed by the produced columns (Sec. 5.3 with the
+// complement of Sec. 5.2): a product is dropped when its column is in the
+// mask row (binary search in the staged sorted row); otherwise it is added
+// under its column, inserting the key on first sight.  Capacity is a power of
+// two >= 2 x min(flops, n - nnz(m)) so probing always ends.  The occupied
+// slots are bitonic-sorted by column for the canonical ascending output.
+template <int SR, bool CTA>
+__device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    Team<CTA> team;
+    const int mnz = c.m1 - c.m0;
+    const long long bound = min(c.flops, (long long)(c.n - mnz));
+    const long long H = pow2_at_least(2 * bound);
+    const int logH = ilog2(H);
+    const unsigned hmask = (unsigned)H - 1u;
+    unsigned *keys = reinterpret_cast<unsigned *>(slab);
+    acc_t *vals = reinterpret_cast<acc_t *>(slab + align8(4 * H));
+    int *mcol = reinterpret_cast<int *>(slab + align8(4 * H) + align8(H * (long long)sizeof(acc_t)));
+    for (long long h = team.tid(); h < H; h += team.size()) {
+        keys[h] = EMPTY32;
+        vals[h] = 0;
+    }
+    for (int q = team.tid(); q < mnz; q += team.size()) mcol[q] = __ldg(P.m_ci + c.m0 + q);
+    team.sync();
+    auto ins = [&](int, in_t a, int j, in_t b) {
+        int lo = 0, hi = mnz;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (mcol[mid] < j) lo = mid + 1; else hi = mid;
+        }
+        if (lo < mnz && mcol[lo] == j) return;   // in the mask: NOTALLOWED under complement
+        unsigned h = hash32((unsigned)j, logH);
+        for (;;) {
+            const unsigned k = keys[h];
+            if (k == (unsigned)j) break;
+            if (k == EMPTY32) {
+                const unsigned prev = atomicCAS(&keys[h], EMPTY32, (unsigned)j);
+                if (prev == EMPTY32 || prev == (unsigned)j) break;
+            }
+            h = (h + 1) & hmask;
+        }
+        S::add(&vals[h], S::mul(a, b));
+    };
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    team.sync();
+    // bitonic sort of (key, value) over H slots, ascending; EMPTY sorts last
+    for (long long kk = 2; kk <= H; kk <<= 1) {
+        for (long long jj = kk >> 1; jj > 0; jj >>= 1) {
+            for (long long x = team.tid(); x < H / 2; x += team.size()) {
+                const long long lo = 2 * jj * (x / jj) + (x % jj);
+                const long long hi = lo + jj;
+                const bool up = (lo & kk) == 0;
+                const unsigned kl = keys[lo], kh = keys[hi];
+                if ((kl > kh) == up) {
+                    keys[lo] = kh;
+                    keys[hi] = kl;
+                    const acc_t t = vals[lo];
+                    vals[lo] = vals[hi];
+                    vals[hi] = t;
+                }
+            }
+            team.sync();
+        }
+    }
+    // occupied slots form a sorted prefix; write it out
+    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    int cntl = 0;
+    for (long long x = team.tid(); x < H; x += team.size()) {
+        const unsigned k = keys[x];
+        if (k != EMPTY32) {
+            L.tmp.ci[c.tmp + x] = (int)k;
+            tv[c.tmp + x] = S::out(vals[x]);
+            ++cntl;
+        }
+    }
+    // count = number of occupied slots
+    if (!CTA) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cntl += __shfl_xor_sync(FULL, cntl, o);
+        if (lane_id() == 0) L.ra.cnt[c.r] = cntl;
+    } else {
+        __shared__ int red;
+        if (threadIdx.x == 0) red = 0;
+        __syncthreads();
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) cntl += __shfl_xor_sync(FULL, cntl, o);
+        if (lane_id() == 0) atomicAdd(&red, cntl);
+        __syncthreads();
+        if (threadIdx.x == 0) L.ra.cnt[c.r] = red;
+    }
+    team.sync();
+}
+
+// --------------------------------------------------------------- _T rows
+// Sec. 5.2 MSA for rows too heavy for a per-row shared table, on one CTA.
+// The column range is cut into tiles of T columns; a tile holds dense values
+// and two bit arrays (ALLOWED -- or NOTALLOWED when complemented -- and SET)
+// in shared memory.  B rows are sorted, so each stored A_ik keeps a cursor
+// into B_k* that the next tile resumes from; the mask row is consumed tile by
+// tile the same way.  Output comes out in ascending column order.  With a
+// single tile the cursors are skipped.  Invariant between tiles and rows:
+// values and bits are zero.
+template <int SR, bool COMP>
+__device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab, int *scratch) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    Team<true> team;
+    const int lane = lane_id();
+    const int T = L.tileT;
+    acc_t *vals = reinterpret_cast<acc_t *>(slab);
+    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(acc_t)));
+    unsigned *setw = mbits + words32(T);
+    const int n = c.n;
+    const int ntiles = (n + T - 1) / T;
+    // cursor of stored entry t of A (product-local index) is cursors[abase + t]
+    int4 *cur = L.cursors + P.abase;
+    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    __shared__ int s_out;    // entries written so far in this row
+    __shared__ int s_mpos;   // mask cursor
+    if (threadIdx.x == 0) { s_out = 0; s_mpos = c.m0; }
+    if (ntiles > 1) {
+        for (int t = c.a0 + team.tid(); t < c.a1; t += team.size()) {
+            const int k = __ldg(P.a_ci + t);
+            const int s = __ldg(P.b_rp + k), e = __ldg(P.b_rp + k + 1);
+            cur[t] = make_int4(s, e, s < e ? __ldg(P.b_ci + s) : INT_MAX, 0);
+        }
+    }
+    __syncthreads();
+    for (int tile = 0; tile < ntiles; ++tile) {
+        const int c0 = tile * T, c1 = min(n, c0 + T);
+        const int mq0 = s_mpos;
+        // mask entries of this tile: [mq0, mq1)
+        int mq1;
+        {
+            int lo = mq0, hi = c.m1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(P.m_ci + mid) < c1) lo = mid + 1; else hi = mid;
+            }
+            mq1 = lo;
+        }
+        for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
+            const int jj = __ldg(P.m_ci + q) - c0;
+            atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
+        }
+        __syncthreads();
+        auto ins = [&](int jj, in_t a, in_t b) {
+            const bool m = test_bit(mbits, jj);
+            if (m != COMP) {   // plain: allowed iff in mask; complemented: iff not
+                S::add(&vals[jj], S::mul(a, b));
+                if constexpr (COMP || SrSizes<SR>::setbits) set_bit_once(setw, jj);
+            }
+        };
+        if (ntiles == 1) {
+            auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), f);
+        } else {
+            for (int w0 = c.a0 + team.warp() * 32; w0 < c.a1; w0 += team.nwarps() * 32) {
+                const int t = w0 + lane;
+                int4 cu = make_int4(0, 0, INT_MAX, 0);
+                in_t av{};
+                if (t < c.a1) {
+                    cu = cur[t];
+                    if constexpr (Sr<SR>::vals) av = load_val<SR>(P.a_v, t);
+                }
+                unsigned act = __ballot_sync(FULL, cu.z < c1);
+                while (act) {
+                    const int u = __ffs(act) - 1;
+                    act &= act - 1;
+                    const int pos = __shfl_sync(FULL, cu.x, u), end = __shfl_sync(FULL, cu.y, u);
+                    const in_t au = shfl_val<SR>(av, u);
+                    int stop = end;
+                    for (int q0 = pos; q0 < end; q0 += 128) {
+                        int col[4];
+                        in_t bv[4];
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            const int q = q0 + x * 32 + lane;
+                            col[x] = (q < end) ? __ldg(P.b_ci + q) : INT_MAX;
+                            if (col[x] < c1) bv[x] = load_val<SR>(P.b_v, q);
+                        }
+                        bool done = false;
+#pragma unroll
+                        for (int x = 0; x < 4; ++x) {
+                            if (!done) {
+                                const bool ok = col[x] < c1;
+                                if (ok) ins(col[x] - c0, au, bv[x]);
+                                const unsigned okm = __ballot_sync(FULL, ok);
+                                if (okm != FULL) {
+                                    stop = q0 + x * 32 + __popc(okm);
+                                    done = true;
+                                }
+                            }
+                        }
+                        if (done) break;
+                    }
+                    if (lane == u) {
+                        cu.x = stop;
+                        cu.z = stop < end ? __ldg(P.b_ci + stop) : INT_MAX;
+                        cur[t] = cu;
+                    }
+                }
+            }
+        }
+        __syncthreads();
+        // gather this tile in ascending column order
+        int outbase = s_out;
+        if (!COMP) {
+            // over the tile's mask entries, in mask order (= ascending)
+            const int cntm = mq1 - mq0;
+            const int nw = team.nwarps(), w = team.warp();
+            const int seg = ((cntm + nw - 1) / nw + 31) & ~31;
+            const int s0 = mq0 + min(cntm, w * seg), s1 = mq0 + min(cntm, w * seg + seg);
+            auto kept = [&](int jj) -> bool {
+                if constexpr (S::count_set) return vals[jj] != 0;
+                else return test_bit(setw, jj);
+            };
+            int cw = 0;
+            for (int r0 = s0; r0 < s1; r0 += 32) {
+                const int q = r0 + lane;
+                const bool keep = q < s1 && kept(__ldg(P.m_ci + q) - c0);
+                if (L.aligned && keep) tv[c.tmp + (q - c.m0)] = S::out(vals[__ldg(P.m_ci + q) - c0]);
+                cw += __popc(__ballot_sync(FULL, keep));
+            }
+            int total;
+            const int off = block_excl_scan(lane == 0 ? cw : 0, scratch, &total);
+            int base = outbase + __shfl_sync(FULL, off, 0);
+            for (int r0 = s0; r0 < s1; r0 += 32) {
+                const int q = r0 + lane;
+                int j = 0;
+                bool keep = false;
+                if (q < s1) {
+                    j = __ldg(P.m_ci + q);
+                    keep = kept(j - c0);
+                }
+                const unsigned bal = __ballot_sync(FULL, keep);
+                if (keep && !L.aligned) {
+                    const long long o = c.tmp + base + __popc(bal & lanemask_lt());
+                    L.tmp.ci[o] = j;
+                    tv[o] = S::out(vals[j - c0]);
+                }
+                base += __popc(bal);
+            }
+            __syncthreads();
+            for (int q = s0 + lane; q < s1; q += 32) {
+                const int jj = __ldg(P.m_ci + q) - c0;
+                vals[jj] = 0;
+                mbits[jj >> 5] = 0;
+                setw[jj >> 5] = 0;
+            }
+            if (threadIdx.x == 0) { s_out = outbase + total; s_mpos = mq1; }
+        } else {
+            // scan the SET bits of the tile; each thread owns a run of words
+            const int nwords = (int)words32(c1 - c0);
+            const int per = (nwords + team.size() - 1) / team.size();
+            const int w0 = min(nwords, team.tid() * per), w1 = min(nwords, w0 + per);
+            int cw = 0;
+            for (int w = w0; w < w1; ++w) cw += __popc(setw[w]);
+            int total;
+            const int off = block_excl_scan(cw, scratch, &total);
+            long long o = c.tmp + outbase + off;
+            for (int w = w0; w < w1; ++w) {
+                unsigned bits = setw[w];
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int jj = w * 32 + b;
+                    L.tmp.ci[o] = c0 + jj;
+                    tv[o] = S::out(vals[jj]);
+                    vals[jj] = 0;
+                    ++o;
+                }
+                setw[w] = 0;
+            }
+            __syncthreads();
+            for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
+                const int jj = __ldg(P.m_ci + q) - c0;
+                mbits[jj >> 5] = 0;
+            }
+            if (threadIdx.x == 0) { s_out = outbase + total; s_mpos = mq1; }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) L.ra.cnt[c.r] = s_out;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ kernels
+template <int SR, int KIND>
+__global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int wib = threadIdx.x >> 5;
+    unsigned char *slab = smem + (size_t)wib * L.slab;
+    const int count = L.ra.kind_count[KIND];
+    const int off = L.ra.kind_off[KIND];
+    if (KIND == K_MSA_W) {   // invariant: the dense arrays start zeroed
+        for (int x = lane_id(); x < L.slab / 4; x += 32) reinterpret_cast<unsigned *>(slab)[x] = 0;
+        __syncwarp();
+    }
+    const int nwarp = gridDim.x * (blockDim.x >> 5);
+    for (int x = blockIdx.x * (blockDim.x >> 5) + wib; x < count; x += nwarp) {
+        const long long r = L.ra.perm[off + x];
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const RowCtx c = row_ctx(P, r, L.ra);
+        if (KIND == K_HASH_W) row_hash<SR, false>(P, c, L, slab, nullptr);
+        else if (KIND == K_MCA_W) row_mca<SR, false>(P, c, L, slab, nullptr);
+        else if (KIND == K_DOT_W) row_dot<SR, false>(P, c, L, slab, nullptr);
+        else if (KIND == K_MSA_W) row_msa_w<SR>(P, c, L, slab);
+        else if (KIND == K_CHASH_W) row_chash<SR, false>(P, c, L, slab);
+    }
+}
+
+template <int SR, int KIND>
+__global__ void __launch_bounds__(256) k_rows_b(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int scratch[40];
+    const int count = L.ra.kind_count[KIND];
+    const int off = L.ra.kind_off[KIND];
+    for (int x = blockIdx.x; x < count; x += gridDim.x) {
+        const long long r = L.ra.perm[off + x];
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const RowCtx c = row_ctx(P, r, L.ra);
+        if (KIND == K_HASH_B) row_hash<SR, true>(P, c, L, smem, scratch);
+        else if (KIND == K_MCA_B) row_mca<SR, true>(P, c, L, smem, scratch);
+        else if (KIND == K_DOT_B) row_dot<SR, true>(P, c, L, smem, scratch);
+        else if (KIND == K_CHASH_B) row_chash<SR, true>(P, c, L, smem);
+    }
+}
+
+template <int SR, bool COMP>
+__global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int scratch[40];
+    __shared__ int s_row;
+    constexpr int KIND = COMP ? K_CMSA_T : K_MSA_T;
+    const int count = L.ra.kind_count[KIND];
+    const int off = L.ra.kind_off[KIND];
+    {   // zero the tile arrays once
+        unsigned *w = reinterpret_cast<unsigned *>(smem);
+        for (int x = threadIdx.x; x < L.slab / 4; x += blockDim.x) w[x] = 0;
+    }
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_row = atomicAdd(&L.ra.kind_next[KIND], 1);
+        __syncthreads();
+        const int x = s_row;
+        if (x >= count) break;
+        const long long r = L.ra.perm[off + x];
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const RowCtx c = row_ctx(P, r, L.ra);
+        row_msa_t<SR, COMP>(P, c, L, smem, scratch);
+    }
+}
+
+}  // namespace msg

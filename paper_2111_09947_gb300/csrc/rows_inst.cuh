@@ -1,0 +1,69 @@
+// Instantiation of the row kernels and the binning pass for one semiring.
+// Included by exactly one translation unit per semiring with MSG_SR and
+// MSG_SUFFIX defined, so the three semirings compile in parallel.
+#pragma once
+
+#include "bin.cuh"
+#include "launch.h"
+#include "rows.cuh"
+
+namespace msg {
+namespace {
+
+using RowKernel = void (*)(ProdSet, RowLaunch);
+
+// Grid of a persistent kernel: resident CTAs per SM x SMs.  The dynamic
+// shared-memory attribute and occupancy are cached per kernel.
+template <RowKernel K>
+cudaError_t go(const ProdSet &ps, const RowLaunch &L, int threads, size_t smem, cudaStream_t st, int nsm) {
+    static size_t attr_set = 0;
+    static size_t occ_smem = ~size_t(0);
+    static int occ = 0;
+    if (smem > 48 * 1024 && smem > attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = smem;
+    }
+    if (occ_smem != smem) {
+        int nb = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K, threads, smem);
+        if (e != cudaSuccess) return e;
+        occ = nb;
+        occ_smem = smem;
+    }
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    K<<<occ * nsm, threads, smem, st>>>(ps, L);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t MSG_CAT(launch_bin_score_, MSG_SUFFIX)(const ProdSet &ps, const RowArrays &ra, const Policy &pol,
+                                                   long long *room, cudaStream_t st, int nsm) {
+    if (ra.R == 0) return cudaSuccess;
+    const long long blocks = std::min<long long>((ra.R + 7) / 8, (long long)nsm * 16);
+    k_bin_score<MSG_SR><<<(int)blocks, 256, 0, st>>>(ps, ra, pol, room);
+    return cudaGetLastError();
+}
+
+cudaError_t MSG_CAT(launch_kind_, MSG_SUFFIX)(int kind, const ProdSet &ps, const RowLaunch &L, cudaStream_t st,
+                                              int nsm) {
+    const int th = kind_threads(kind);
+    const size_t sm = kind_smem(kind, L.slab);
+    switch (kind) {
+    case K_MSA_W: return go<k_rows_w<MSG_SR, K_MSA_W>>(ps, L, th, sm, st, nsm);
+    case K_HASH_W: return go<k_rows_w<MSG_SR, K_HASH_W>>(ps, L, th, sm, st, nsm);
+    case K_MCA_W: return go<k_rows_w<MSG_SR, K_MCA_W>>(ps, L, th, sm, st, nsm);
+    case K_DOT_W: return go<k_rows_w<MSG_SR, K_DOT_W>>(ps, L, th, sm, st, nsm);
+    case K_CHASH_W: return go<k_rows_w<MSG_SR, K_CHASH_W>>(ps, L, th, sm, st, nsm);
+    case K_HASH_B: return go<k_rows_b<MSG_SR, K_HASH_B>>(ps, L, th, sm, st, nsm);
+    case K_MCA_B: return go<k_rows_b<MSG_SR, K_MCA_B>>(ps, L, th, sm, st, nsm);
+    case K_DOT_B: return go<k_rows_b<MSG_SR, K_DOT_B>>(ps, L, th, sm, st, nsm);
+    case K_CHASH_B: return go<k_rows_b<MSG_SR, K_CHASH_B>>(ps, L, th, sm, st, nsm);
+    case K_MSA_T: return go<k_rows_t<MSG_SR, false>>(ps, L, th, sm, st, nsm);
+    case K_CMSA_T: return go<k_rows_t<MSG_SR, true>>(ps, L, th, sm, st, nsm);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace msg

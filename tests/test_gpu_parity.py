@@ -1,0 +1,216 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Every accumulator family is forced on every row (and AUTO lets the binning
+mix them); shapes span several tiles and ragged tails, empty rows, empty
+matrices and degenerate dimensions; both mask forms; all three semirings.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2111_09947_gb300 import _lib, synth
+from golden_io import worked_example
+from gpu_util import assert_parity, to_dev
+
+pytestmark = pytest.mark.gpu
+
+SEMIRINGS = ["plus_times_f32", "plus_times_i64", "plus_pair_i64"]
+FORCES = ["auto", "msa", "hash", "mca", "dot"]
+GEN = {"plus_times_f32": "f32", "plus_times_i64": "i64", "plus_pair_i64": "pair"}
+
+
+@pytest.fixture(scope="module")
+def handle():
+    h = _lib.Handle()
+    h.set_option(_lib.OPT_VALIDATE, 1)
+    yield h
+    h.close()
+
+
+def run(h, p, semiring, complement=False, force="auto"):
+    h.force(force)
+    d = to_dev(p, semiring)
+    res = _lib.msgemm_run(h, d["M"], d["A"], d["B"], semiring, complement).trimmed()
+    h.sync_status()
+    return res
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("force", FORCES)
+def test_worked_example(handle, semiring, force):
+    g = worked_example()
+    vals = {"plus_times_f32": np.float32, "plus_times_i64": np.int64}
+    p = {"M": g["M"], "A": g["A"], "B": g["B"]}
+    if semiring in vals:
+        p = {k: v.with_values(v.values.astype(vals[semiring])) for k, v in p.items()}
+    key = "C_plus_pair" if semiring == "plus_pair_i64" else "C_plus_times"
+    res = run(handle, p, semiring, False, force)
+    want = g[key]
+    assert np.array_equal(res.rowptr.cpu().numpy(), want.rowptr)
+    assert np.array_equal(res.colidx.cpu().numpy(), want.colidx)
+    assert np.array_equal(res.values.cpu().numpy().astype(np.int64), want.values)
+    res = run(handle, p, semiring, True, force)
+    want = g["C_complement_" + key[2:]]
+    assert np.array_equal(res.colidx.cpu().numpy(), want.colidx)
+    assert np.array_equal(res.values.cpu().numpy().astype(np.int64), want.values)
+
+
+SHAPES = [
+    # m, k, n, dA, dB, dM
+    (1, 1, 1, 1.0, 1.0, 1.0),
+    (37, 23, 41, 3.0, 4.0, 5.0),
+    (300, 200, 250, 6.0, 6.0, 30.0),
+    (2500, 1500, 3000, 8.0, 8.0, 8.0),          # several compaction tiles, ragged
+    (700, 600, 900, 12.0, 40.0, 2.0),           # mask much sparser than inputs (pull regime)
+    (400, 300, 500, 2.0, 2.0, 200.0),           # inputs much sparser than mask
+    (50, 0, 60, 0.0, 0.0, 10.0),                # k = 0: no products at all
+    (64, 64, 64, 64.0, 64.0, 64.0),             # dense
+    (2000, 300, 70000, 6.0, 300.0, 40.0),       # wide rows: tiled MSA, CTA kinds
+]
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("force", FORCES)
+def test_random_plain(handle, semiring, force):
+    for s, (m, k, n, da, db, dm) in enumerate(SHAPES):
+        p = synth.random_problem(m, k, n, min(da, max(k, 1)), min(db, max(n, 1)), min(dm, max(n, 1)), 900 + s,
+                                 GEN[semiring])
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], semiring)
+        res = run(handle, p, semiring, False, force)
+        assert_parity(res, ref, semiring, ctx=f"shape {s} force {force}")
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("force", ["auto", "hash", "msa"])
+def test_random_complement(handle, semiring, force):
+    for s, (m, k, n, da, db, dm) in enumerate(SHAPES):
+        if n > 10000 and force == "hash":
+            pass
+        p = synth.random_problem(m, k, n, min(da, max(k, 1)), min(db, max(n, 1)), min(dm, max(n, 1)), 1900 + s,
+                                 GEN[semiring])
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], semiring, complement=True, method=O.ESC)
+        res = run(handle, p, semiring, True, force)
+        assert_parity(res, ref, semiring, ctx=f"shape {s} force {force}")
+
+
+def test_empty_matrices(handle):
+    for m, k, n in [(0, 5, 7), (5, 7, 0), (0, 0, 0), (3, 4, 5)]:
+        p = synth.random_problem(m, k, n, 0.0, 0.0, 0.0, 5, "f32")
+        for comp in (False, True):
+            res = run(handle, p, "plus_times_f32", comp)
+            assert res.rowptr.numel() == m + 1
+            assert int(res.rowptr[-1]) == 0 if m else True
+            assert res.colidx.numel() == 0
+
+
+def test_errors(handle):
+    p = synth.random_problem(10, 8, 12, 2.0, 2.0, 2.0, 3, "f32")
+    d = to_dev(p, "plus_times_f32")
+    with pytest.raises(_lib.MsgemmError) as e:
+        _lib.msgemm_run(handle, d["M"], d["B"], d["B"], "plus_times_f32")
+    assert e.value.status == 2
+    with pytest.raises(_lib.MsgemmError) as e:
+        _lib.msgemm_backward(handle, d["A"], d["B"], d["M"]) if False else \
+            handle.check(handle.lib.msgemm_backward(handle.h, None, None, None, 1, None, None))
+    assert e.value.status in (1, 4)
+    # unsorted row found by device validation
+    A = p["A"]
+    ci = A.colidx.copy()
+    r = next(i for i in range(A.nrows) if A.rowptr[i + 1] - A.rowptr[i] >= 2)
+    s = A.rowptr[r]
+    ci[s], ci[s + 1] = ci[s + 1], ci[s]
+    bad = synth.Csr(A.nrows, A.ncols, A.rowptr, ci, A.values)
+    d2 = to_dev({"M": p["M"], "A": bad, "B": p["B"]}, "plus_times_f32")
+    handle.force("auto")
+    with pytest.raises(_lib.MsgemmError) as e:
+        _lib.msgemm_run(handle, d2["M"], d2["A"], d2["B"], "plus_times_f32")
+    assert e.value.status == 3
+    handle.sync_status()   # error word was cleared
+    # a row pointer beyond nnz is rejected before any product kernel reads it
+    rp = p["M"].rowptr.copy()
+    rp[-1] += 5
+    d3 = to_dev({"M": synth.Csr(p["M"].nrows, p["M"].ncols, rp, p["M"].colidx), "A": p["A"], "B": p["B"]},
+                "plus_times_f32")
+    with pytest.raises(_lib.MsgemmError) as e:
+        _lib.msgemm_run(handle, d3["M"], d3["A"], d3["B"], "plus_times_f32")
+    assert e.value.status == 1
+    handle.sync_status()
+
+
+def test_er_plain_fp32_full(handle):
+    """Erdos-Renyi n = 4096, 8 entries per row, fp32: the whole output."""
+    p = synth.er_plain_f32()
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    for force in FORCES:
+        res = run(handle, p, "plus_times_f32", False, force)
+        assert_parity(res, ref, "plus_times_f32", ctx=force)
+
+
+@pytest.mark.parametrize("scale", [10, 14])
+def test_triangle_count_rmat(handle, scale):
+    p = synth.triangle_counting(scale=scale, ef=16, seed=21)
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_pair_i64")
+    for force in FORCES:
+        res = run(handle, p, "plus_pair_i64", False, force)
+        assert_parity(res, ref, "plus_pair_i64", ctx=force)
+        full = _lib.msgemm_run(handle, *[to_dev(p, "plus_pair_i64")[k] for k in ("M", "A", "B")], "plus_pair_i64")
+        tri = int(_lib.msgemm_reduce_sum(handle, full, "plus_pair_i64").item())
+        assert tri == int(ref["values"].sum())
+
+
+def test_bfs_step_small(handle):
+    p = synth.bfs_step(scale=12, ef=16, nsrc=64, seed=8)
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64", complement=True, method=O.ESC)
+    for force in ["auto", "msa", "hash"]:
+        res = run(handle, p, "plus_times_i64", True, force)
+        assert_parity(res, ref, "plus_times_i64", ctx=force)
+
+
+def test_batched_matches_plain(handle):
+    ps = synth.batched_problems(nprod=10, seed=4, log2_range=(8, 11))
+    devs = [to_dev(p, "plus_times_f32") for p in ps]
+    handle.force("auto")
+    outs = _lib.msgemm_run_batched(handle, [d["M"] for d in devs], [d["A"] for d in devs], [d["B"] for d in devs],
+                                   "plus_times_f32")
+    for p, o in zip(ps, outs):
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+        assert_parity(o.trimmed(), ref, "plus_times_f32")
+
+
+def test_backward_vs_oracle(handle):
+    for seed, (m, k, n) in enumerate([(60, 50, 70), (300, 200, 250)]):
+        p = synth.random_problem(m, k, n, 5.0, 5.0, 12.0, 70 + seed, "f32")
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+        G = synth.Csr(m, n, ref["rowptr"].astype(np.int32), ref["colidx"],
+                      synth.upstream_grad(len(ref["colidx"]), seed))
+        dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+        d = to_dev(p, "plus_times_f32")
+        Gd = _lib.DeviceCsr.from_host(G)
+        handle.force("auto")
+        dA, dB = _lib.msgemm_backward(handle, d["A"], d["B"], Gd)
+        handle.sync_status()
+        # bound: sum of |g||b| (dA) and |a||g| (dB), fp64 via dense products
+        Ad, Bd, Gdd = p["A"].to_dense(), p["B"].to_dense(), G.to_dense()
+        SA = (np.abs(Gdd) @ np.abs(Bd).T)[np.repeat(np.arange(m), np.diff(p["A"].rowptr)), p["A"].colidx]
+        SB = (np.abs(Ad).T @ np.abs(Gdd))[np.repeat(np.arange(k), np.diff(p["B"].rowptr)), p["B"].colidx]
+        assert np.all(np.abs(dA.cpu().numpy() - dA_ref) <= 1e-5 * SA + 1e-30)
+        assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
+
+
+def test_autograd_function(handle):
+    from paper_2111_09947_gb300.autograd import masked_spgemm_autograd
+    p = synth.autograd_problem(scale=8, ef=16, seed=5)
+    d = to_dev(p, "plus_times_f32")
+    a = d["A"].values.clone().requires_grad_(True)
+    b = d["B"].values.clone().requires_grad_(True)
+    handle.force("auto")
+    cv, crp, cci = masked_spgemm_autograd(a, b, d["M"], d["A"], d["B"], handle)
+    g = torch.from_numpy(synth.upstream_grad(cv.numel(), 5)).cuda()
+    (cv * g).sum().backward()
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    G = synth.Csr(p["M"].nrows, p["M"].ncols, ref["rowptr"].astype(np.int32), ref["colidx"],
+                  synth.upstream_grad(len(ref["colidx"]), 5))
+    dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+    np.testing.assert_allclose(a.grad.cpu().numpy(), dA_ref, rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(b.grad.cpu().numpy(), dB_ref, rtol=1e-4, atol=1e-4)
