@@ -78,7 +78,10 @@ typedef enum {
                                      MSGEMM_ERR_INVALID / MSGEMM_ERR_UNSORTED without running
                                      the product.  Without validation, out-of-range indices
                                      are undefined behaviour. */
-    MSGEMM_OPT_DOT = 3            /* value 0/1 (default 1): allow the pull (DOT) kernel in AUTO */
+    MSGEMM_OPT_DOT = 3,           /* value 0/1 (default 1): allow the pull (DOT) kernel in AUTO */
+    MSGEMM_OPT_PROFILE = 4        /* value 0/1 (default 0): record CUDA events around every
+                                     phase and kernel launch of a call, on the handle's stream
+                                     (read back with msgemm_profile_entry) */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */
@@ -170,9 +173,10 @@ msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr
                               const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                               msgemm_semiring semiring, const char *cache_path);
 
-/* Transpose (CSR of A^T).  At is allocated like an output (capacity nnz(A)).
- * Column indices within a row of A^T are NOT sorted unless sorted != 0
- * (sorting costs an extra segmented sort pass). */
+/* Transpose (CSR of A^T), value_bytes in {0, 4, 8}.  At is allocated like an
+ * output (capacity nnz(A)).  Column indices within a row of A^T are in
+ * arbitrary order unless sorted != 0, which adds a segmented sort pass
+ * (bitonic per row) and gives strictly ascending rows.  Synchronises. */
 msgemm_status msgemm_transpose(msgemm_handle *handle, const msgemm_csr *A, int value_bytes,
                                int sorted, msgemm_csr_out *At);
 
@@ -195,6 +199,20 @@ msgemm_status msgemm_last_error_detail(msgemm_handle *handle, char *buf, size_t 
  * (synchronises): counts[kind] for kind < min(n, msgemm_num_kinds()). */
 int msgemm_num_kinds(void);
 msgemm_status msgemm_bin_counts(msgemm_handle *handle, int64_t *counts, int n);
+
+/* Phase timings of the last call made with MSGEMM_OPT_PROFILE on (synchronises).
+ * msgemm_profile_count returns the number of entries; entry idx gives the
+ * phase name (NUL-terminated, truncated to len) and its device time in ms. */
+int msgemm_profile_count(msgemm_handle *handle);
+msgemm_status msgemm_profile_entry(msgemm_handle *handle, int idx, char *name, size_t len, float *ms);
+
+/* Kind (msgemm row kind index, as counted by msgemm_bin_counts) of each row of
+ * the last msgemm_run / msgemm_run_batched, copied to host memory `kinds`
+ * (nrows bytes; rows of all products concatenated).  Synchronises. */
+msgemm_status msgemm_last_row_kinds(msgemm_handle *handle, uint8_t *kinds, int64_t nrows);
+
+/* Process-wide number of kernels this library has launched so far. */
+int64_t msgemm_kernel_launches(void);
 
 /* Frees the workspace and the handle (synchronises its stream). */
 void msgemm_destroy(msgemm_handle *handle);

@@ -20,7 +20,7 @@ PLUS_TIMES_F32, PLUS_TIMES_I64, PLUS_PAIR_I64 = 0, 1, 2
 SEMIRINGS = {"plus_times_f32": PLUS_TIMES_F32, "plus_times_i64": PLUS_TIMES_I64, "plus_pair_i64": PLUS_PAIR_I64}
 ACC_AUTO, ACC_MSA, ACC_HASH, ACC_MCA, ACC_DOT = 0, 1, 2, 3, 4
 ACCUMULATORS = {"auto": 0, "msa": 1, "hash": 2, "mca": 3, "dot": 4}
-OPT_FORCE_ACCUM, OPT_VALIDATE, OPT_DOT = 1, 2, 3
+OPT_FORCE_ACCUM, OPT_VALIDATE, OPT_DOT, OPT_PROFILE = 1, 2, 3, 4
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_SHAPE", 3: "ERR_UNSORTED", 4: "ERR_UNSUPPORTED", 5: "ERR_OOM",
           6: "ERR_OVERFLOW", 7: "ERR_CUDA", 8: "ERR_TIMEOUT"}
 KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "dot_w", "dot_b",
@@ -30,6 +30,7 @@ KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "
 EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_run", "msgemm_backward",
            "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
            "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
+           "msgemm_profile_count", "msgemm_profile_entry", "msgemm_last_row_kinds", "msgemm_kernel_launches",
            "msgemm_destroy"]
 
 
@@ -88,6 +89,10 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "msgemm_last_error_detail": (i32, [vp, C.c_char_p, sz]),
         "msgemm_num_kinds": (i32, []),
         "msgemm_bin_counts": (i32, [vp, P(i64), i32]),
+        "msgemm_profile_count": (i32, [vp]),
+        "msgemm_profile_entry": (i32, [vp, i32, C.c_char_p, sz, P(C.c_float)]),
+        "msgemm_last_row_kinds": (i32, [vp, vp, i64]),
+        "msgemm_kernel_launches": (i64, []),
         "msgemm_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
@@ -223,6 +228,22 @@ class Handle:
         self.check(self.lib.msgemm_bin_counts(self.h, arr, n))
         return {KIND_NAMES[k] if k < len(KIND_NAMES) else str(k): int(arr[k]) for k in range(n)}
 
+    def profile(self) -> list:
+        """[(phase name, device ms)] of the last call made with profiling on."""
+        out = []
+        for i in range(self.lib.msgemm_profile_count(self.h)):
+            buf = C.create_string_buffer(64)
+            ms = C.c_float()
+            self.check(self.lib.msgemm_profile_entry(self.h, i, buf, 64, C.byref(ms)))
+            out.append((buf.value.decode(), float(ms.value)))
+        return out
+
+    def row_kinds(self, nrows: int):
+        import numpy as np
+        out = np.empty(nrows, np.uint8)
+        self.check(self.lib.msgemm_last_row_kinds(self.h, out.ctypes.data if nrows else None, nrows))
+        return out
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.msgemm_destroy(self.h)
@@ -293,11 +314,11 @@ def msgemm_reduce_sum(h: Handle, res: Result, semiring) -> torch.Tensor:
     return out
 
 
-def msgemm_transpose(h: Handle, A: DeviceCsr, value_bytes: int) -> Result:
+def msgemm_transpose(h: Handle, A: DeviceCsr, value_bytes: int, sorted_rows: bool = False) -> Result:
     h.bind_stream()
     a = A.abi()
     out = CsrOut()
-    h.check(h.lib.msgemm_transpose(h.h, C.byref(a), int(value_bytes), 0, C.byref(out)))
+    h.check(h.lib.msgemm_transpose(h.h, C.byref(a), int(value_bytes), int(bool(sorted_rows)), C.byref(out)))
     dt = {0: torch.uint8, 4: torch.float32, 8: torch.int64}[value_bytes]
     rp = h.adopt(out.rowptr, torch.int32, out.nrows + 1)
     ci = h.adopt(out.colidx, torch.int32, out.capacity)

@@ -39,7 +39,14 @@ struct msgemm_handle {
     float dot_ratio = 2.0f;
     int warp_flops_max = 4096;
     int *last_kind_count = nullptr;
+    unsigned char *last_kind = nullptr;
+    long long last_R = 0;
     std::string last_error;
+    // phase profiling (MSGEMM_OPT_PROFILE)
+    int profile = 0;
+    struct Phase { std::string name; cudaEvent_t a = nullptr, b = nullptr; };
+    std::vector<Phase> prof;
+    int nprof = 0;
     // host staging
     std::vector<DevProd> hprods;
 };
@@ -97,6 +104,32 @@ msgemm_status grow(msgemm_handle *h, Buf &b, size_t bytes) {
     b.cap = b.p ? want : 0;
     if (!b.p) return fail(h, MSGEMM_ERR_OOM, "workspace allocation of %zu bytes failed", want);
     return MSGEMM_OK;
+}
+
+// Records events around a phase on the handle's stream when profiling is on.
+struct PScope {
+    msgemm_handle *h;
+    int idx = -1;
+    PScope(msgemm_handle *h_, const char *name) : h(h_) {
+        if (!h->profile) return;
+        if (h->nprof == (int)h->prof.size()) {
+            h->prof.emplace_back();
+            cudaEventCreate(&h->prof.back().a);
+            cudaEventCreate(&h->prof.back().b);
+        }
+        idx = h->nprof++;
+        h->prof[idx].name = name;
+        cudaEventRecord(h->prof[idx].a, h->stream);
+    }
+    ~PScope() {
+        if (idx >= 0) cudaEventRecord(h->prof[idx].b, h->stream);
+    }
+};
+
+const char *kind_name(int k) {
+    static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
+                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t"};
+    return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
 // Bump carving of a buffer.
@@ -168,8 +201,26 @@ struct ProdIn {
     void *aligned_out = nullptr;   // gradient form: values at the mask's slots
 };
 
+// Device check of user inputs (row pointers, column range, strict order);
+// synchronises.  Internal operands (transposes with unsorted rows) never pass here.
+msgemm_status validate_inputs(msgemm_handle *h, const std::vector<const msgemm_csr *> &mats) {
+    cudaStream_t st = h->stream;
+    for (const msgemm_csr *X : mats)
+        if (X->nrows > 0) CK(launch_validate(X->rowptr, X->colidx, X->nrows, X->ncols, X->nnz, h->d_err, st, h->nsm));
+    unsigned herr = 0;
+    CK(cudaMemcpyAsync(&herr, h->d_err, sizeof herr, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) {
+        CK(cudaMemsetAsync(h->d_err, 0, sizeof herr, st));
+        if (herr & ERR_UNSORTED) return fail(h, MSGEMM_ERR_UNSORTED, "an input row is not strictly ascending");
+        return fail(h, MSGEMM_ERR_INVALID, "invalid row pointers or column indices");
+    }
+    return MSGEMM_OK;
+}
+
 // The whole one-phase pipeline for a set of products (Sec. 4-6).
-msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt) {
+msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
+                           bool validate) {
     const int P = (int)in.size();
     const bool aligned = P > 0 && in[0].aligned_out != nullptr;
     cudaStream_t st = h->stream;
@@ -243,21 +294,11 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
 
     // ---- optional input validation: synchronises, and rejects invalid input
     // before any kernel that would index through it runs
-    if (h->validate) {
-        for (int p = 0; p < P; ++p) {
-            const ProdIn &x = in[p];
-            const msgemm_csr *mats[3] = {x.M, x.A, x.B};
-            for (const msgemm_csr *X : mats)
-                if (X->nrows > 0) CK(launch_validate(X->rowptr, X->colidx, X->nrows, X->ncols, X->nnz, err, st, h->nsm));
-        }
-        unsigned herr = 0;
-        CK(cudaMemcpyAsync(&herr, err, sizeof herr, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (herr) {
-            CK(cudaMemsetAsync(err, 0, sizeof herr, st));
-            if (herr & ERR_UNSORTED) return fail(h, MSGEMM_ERR_UNSORTED, "an input row is not strictly ascending");
-            return fail(h, MSGEMM_ERR_INVALID, "invalid row pointers or column indices");
-        }
+    if (validate) {
+        PScope ph(h, "validate");
+        std::vector<const msgemm_csr *> mats;
+        for (int p = 0; p < P; ++p) mats.insert(mats.end(), {in[p].M, in[p].A, in[p].B});
+        CKS(validate_inputs(h, mats));
     }
 
     // ---- B^T for the pull kernel: row pointers now, entries if a row picks it
@@ -272,6 +313,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
                      carve_size<char>((size_t)B->nnz * in_bytes(sr)) + carve_size<long long>(B->ncols / STILE + 4);
         }
         if (bytes) {
+            PScope ph(h, "bt_counts");
             CKS(grow(h, h->bt, bytes));
             Carver cb(h->bt.p);
             for (int p = 0; p < P; ++p) {
@@ -308,16 +350,22 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
 
     // ---- binning
+    {
+    PScope ph(h, "bin");
     switch (sr) {
     case MSGEMM_PLUS_TIMES_F32: CK(launch_bin_score_f32(ps, ra, pol, room, st, h->nsm)); break;
     case MSGEMM_PLUS_TIMES_I64: CK(launch_bin_score_i64(ps, ra, pol, room, st, h->nsm)); break;
     default: CK(launch_bin_score_pp(ps, ra, pol, room, st, h->nsm)); break;
     }
     CK(launch_bin_scatter(ra, st, h->nsm));
+    }
+    h->last_kind = ra.kind;
+    h->last_R = R;
 
     // ---- temporary room: mask-sized for plain masks, bound-sized when complemented
     long long comp_total = 0;
     if (any_comp) {
+        PScope ph(h, "room");
         CK(launch_scan_room(ra, room, tmpn, room_tiles, ra.bound_total, st, h->nsm));
         CK(cudaMemcpyAsync(&comp_total, ra.bound_total, sizeof comp_total, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
@@ -337,6 +385,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
 
     // ---- B^T entries, only when some row picked the pull kernel
     for (const BtPlan &b : btp) {
+        PScope ph(h, "bt_fill");
         CK(cudaMemcpyAsync(b.cur, b.rp, sizeof(int) * ((size_t)b.n + 1), cudaMemcpyDeviceToDevice, st));
         CK(launch_transpose_fill(b.B->rowptr, b.B->colidx, b.B->values, in_bytes(sr), b.B->nrows, b.rp, b.cur, b.ci,
                                  b.v, ra.any_dot, st, h->nsm));
@@ -363,7 +412,11 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     }
     if (any_comp) kinds.insert(kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
     for (int kd : kinds) {
-        if (kd == K_MSA_T || kd == K_CMSA_T) CK(launch_sort_heavy(ra, kd, st));
+        if (kd == K_MSA_T || kd == K_CMSA_T) {
+            PScope ph(h, "sort_heavy");
+            CK(launch_sort_heavy(ra, kd, st));
+        }
+        PScope ph(h, kind_name(kd));
         L.slab = pol.slab[kd];
         L.tileT = pol.tileT[kd == K_CMSA_T ? 1 : 0];
         switch (sr) {
@@ -375,7 +428,10 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (aligned) return MSGEMM_OK;
 
     // ---- count, allocate complemented outputs, compact
-    CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, st, h->nsm));
+    {
+        PScope ph(h, "count");
+        CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, st, h->nsm));
+    }
     if (any_comp) {
         std::vector<long long> tot(P);
         CK(cudaMemcpyAsync(tot.data(), prod_tot + P, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
@@ -394,7 +450,10 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         if (P == 1) ps.p0 = dp[0];
         CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
     }
-    CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, ob, st, h->nsm));
+    {
+        PScope ph(h, "compact");
+        CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, ob, st, h->nsm));
+    }
     return MSGEMM_OK;
 }
 
@@ -481,6 +540,7 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
         return MSGEMM_OK;
     case MSGEMM_OPT_VALIDATE: h->validate = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_DOT: h->allow_dot = value != 0; return MSGEMM_OK;
+    case MSGEMM_OPT_PROFILE: h->profile = value != 0; return MSGEMM_OK;
     default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
     }
 }
@@ -488,24 +548,27 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
 msgemm_status msgemm_run(msgemm_handle *h, const msgemm_csr *M, int complement, const msgemm_csr *A,
                          const msgemm_csr *B, msgemm_semiring sr, msgemm_csr_out *C) {
     if (!h || !C) return fail(h, MSGEMM_ERR_INVALID, "NULL handle or output");
+    h->nprof = 0;
     CKS(check_product(h, M, A, B, sr));
     const int comp = complement != 0;
     CKS(alloc_out(h, M, comp, sr, C));
     std::vector<ProdIn> in(1);
     in[0].M = M; in[0].A = A; in[0].B = B; in[0].comp = comp; in[0].C = C;
-    return run_pipeline(h, in, sr, true);
+    return run_pipeline(h, in, sr, true, h->validate);
 }
 
 msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
                               msgemm_semiring sr, float *dA_vals, float *dB_vals) {
     if (!h) return MSGEMM_ERR_INVALID;
     if (sr != MSGEMM_PLUS_TIMES_F32) return fail(h, MSGEMM_ERR_UNSUPPORTED, "backward is defined for plus-times fp32");
+    h->nprof = 0;
     CKS(check_csr(h, A, "A", true));
     CKS(check_csr(h, B, "B", true));
     CKS(check_csr(h, G, "G", true));
     if (A->ncols != B->nrows || G->nrows != A->nrows || G->ncols != B->ncols)
         return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: A %dx%d, B %dx%d, G %dx%d", A->nrows, A->ncols,
                     B->nrows, B->ncols, G->nrows, G->ncols);
+    if (h->validate) CKS(validate_inputs(h, {A, B, G}));
     cudaStream_t st = h->stream;
     // transposes B^T (n x k) and A^T (k x m), values carried, rows unsorted
     struct T { int *rp, *cur, *ci; float *v; long long *tb; };
@@ -528,18 +591,22 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
     };
     T Bt = mk(B), At = mk(A);
     msgemm_status rs = MSGEMM_OK;
-    auto transpose = [&](const msgemm_csr *X, T &t) -> msgemm_status {
+    // sorted: rows of the transpose in ascending column order (needed when it
+    // is the right operand, whose rows the column-tiled MSA walks by cursor)
+    auto transpose = [&](const msgemm_csr *X, T &t, bool sorted) -> msgemm_status {
+        PScope ph(h, "transpose");
         CK(launch_col_counts(X->colidx, X->nnz, X->ncols, t.cur, st, h->nsm));
         CK(launch_excl_scan_int(t.cur, X->ncols, t.rp, t.tb, st, h->nsm));
         CK(cudaMemcpyAsync(t.cur, t.rp, sizeof(int) * ((size_t)X->ncols + 1), cudaMemcpyDeviceToDevice, st));
         CK(launch_transpose_fill(X->rowptr, X->colidx, X->values, 4, X->nrows, t.rp, t.cur, t.ci, t.v, nullptr, st,
                                  h->nsm));
+        if (sorted) CK(launch_segsort(t.rp, t.ci, t.v, 4, X->ncols, st, h->nsm));
         return MSGEMM_OK;
     };
     if (dA_vals) {
         // dA = pattern(A) .* (G B^T): mask A, left G (m x n), right B^T (n x k);
         // the pull kernel reads columns of B^T, which are the rows of B.
-        rs = transpose(B, Bt);
+        rs = transpose(B, Bt, true);
         if (rs == MSGEMM_OK) {
             msgemm_csr Mx = *A, Bx{};
             Mx.values = nullptr;
@@ -550,12 +617,12 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
             in[0].bt_rp = B->rowptr; in[0].bt_ci = B->colidx; in[0].bt_v = B->values;
             in[0].aligned_out = dA_vals;
             if (cudaMemsetAsync(dA_vals, 0, sizeof(float) * (size_t)A->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
-            if (rs == MSGEMM_OK && A->nnz > 0) rs = run_pipeline(h, in, sr, false);
+            if (rs == MSGEMM_OK && A->nnz > 0) rs = run_pipeline(h, in, sr, false, false);
         }
     }
     if (rs == MSGEMM_OK && dB_vals) {
         // dB = pattern(B) .* (A^T G): mask B, left A^T (k x m, rows unsorted), right G
-        rs = transpose(A, At);
+        rs = transpose(A, At, false);
         if (rs == MSGEMM_OK) {
             msgemm_csr Mx = *B, Ax{};
             Mx.values = nullptr;
@@ -566,7 +633,7 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
             in[0].a_sorted = 0;
             in[0].aligned_out = dB_vals;
             if (cudaMemsetAsync(dB_vals, 0, sizeof(float) * (size_t)B->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
-            if (rs == MSGEMM_OK && B->nnz > 0) rs = run_pipeline(h, in, sr, false);
+            if (rs == MSGEMM_OK && B->nnz > 0) rs = run_pipeline(h, in, sr, false, false);
         }
     }
     // the transpose buffer is released in stream order (the callback's free
@@ -580,6 +647,7 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
                                  int use_graph) {
     if (!h || nprod < 0 || (nprod > 0 && (!M || !A || !B || !C))) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
     (void)use_graph;
+    h->nprof = 0;
     if (nprod == 0) return MSGEMM_OK;
     std::vector<ProdIn> in(nprod);
     for (int p = 0; p < nprod; ++p) {
@@ -588,7 +656,7 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
         CKS(alloc_out(h, &M[p], comp, sr, &C[p]));
         in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = comp; in[p].C = &C[p];
     }
-    return run_pipeline(h, in, sr, true);
+    return run_pipeline(h, in, sr, true, h->validate);
 }
 
 msgemm_status msgemm_autotune(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,
@@ -601,7 +669,6 @@ msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_
     if (!h || !At) return MSGEMM_ERR_INVALID;
     CKS(check_csr(h, A, "A", value_bytes > 0));
     if (value_bytes != 0 && value_bytes != 4 && value_bytes != 8) return fail(h, MSGEMM_ERR_INVALID, "value_bytes");
-    if (sorted) return fail(h, MSGEMM_ERR_UNSUPPORTED, "sorted transpose not available in this build");
     cudaStream_t st = h->stream;
     memset(At, 0, sizeof *At);
     At->nrows = A->ncols;
@@ -622,6 +689,7 @@ msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_
     CK(cudaMemcpyAsync(cur, At->rowptr, sizeof(int) * ((size_t)A->ncols + 1), cudaMemcpyDeviceToDevice, st));
     CK(launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At->rowptr, cur, At->colidx,
                              At->values, nullptr, st, h->nsm));
+    if (sorted) CK(launch_segsort(At->rowptr, At->colidx, At->values, value_bytes, A->ncols, st, h->nsm));
     int64_t nnz = A->nnz;
     CK(cudaMemcpyAsync(At->d_nnz, &nnz, sizeof nnz, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));
@@ -630,6 +698,7 @@ msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_
 
 msgemm_status msgemm_reduce_sum(msgemm_handle *h, const msgemm_csr_out *C, msgemm_semiring sr, void *d_sum) {
     if (!h || !C || !d_sum || !C->d_nnz) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
+    PScope ph(h, "reduce");
     CK(launch_reduce_sum(sr, C->values, reinterpret_cast<const long long *>(C->d_nnz), d_sum, h->stream, h->nsm));
     return MSGEMM_OK;
 }
@@ -666,9 +735,36 @@ msgemm_status msgemm_bin_counts(msgemm_handle *h, int64_t *counts, int n) {
     return MSGEMM_OK;
 }
 
+int msgemm_profile_count(msgemm_handle *h) { return h ? h->nprof : 0; }
+
+msgemm_status msgemm_profile_entry(msgemm_handle *h, int idx, char *name, size_t len, float *ms) {
+    if (!h || idx < 0 || idx >= h->nprof) return MSGEMM_ERR_INVALID;
+    if (name && len) snprintf(name, len, "%s", h->prof[idx].name.c_str());
+    if (ms) {
+        CK(cudaEventSynchronize(h->prof[idx].b));
+        CK(cudaEventElapsedTime(ms, h->prof[idx].a, h->prof[idx].b));
+    }
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_last_row_kinds(msgemm_handle *h, uint8_t *kinds, int64_t nrows) {
+    if (!h || (!kinds && nrows > 0)) return MSGEMM_ERR_INVALID;
+    if (nrows != h->last_R) return fail(h, MSGEMM_ERR_INVALID, "last call had %lld rows", h->last_R);
+    if (nrows == 0) return MSGEMM_OK;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(kinds, h->last_kind, (size_t)nrows, cudaMemcpyDeviceToHost));
+    return MSGEMM_OK;
+}
+
+int64_t msgemm_kernel_launches(void) { return g_kernel_launches.load(); }
+
 void msgemm_destroy(msgemm_handle *h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    for (auto &ph : h->prof) {
+        cudaEventDestroy(ph.a);
+        cudaEventDestroy(ph.b);
+    }
     for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods}) dev_free(h, b->p);
     delete h;
 }

@@ -5,7 +5,16 @@
 
 #include "common.cuh"
 
+#include <atomic>
+
 namespace msg {
+
+// Kernels launched by this library (process-wide), for launch accounting.
+extern std::atomic<long long> g_kernel_launches;
+inline cudaError_t counted(cudaError_t e, int n = 1) {
+    g_kernel_launches.fetch_add(n, std::memory_order_relaxed);
+    return e;
+}
 
 struct RowLaunch;
 
@@ -51,6 +60,7 @@ cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, 
 cudaError_t launch_reduce_sum(int semiring, const void *vals, const long long *d_nnz, void *d_sum, cudaStream_t,
                               int nsm);
 cudaError_t launch_sort_heavy(const RowArrays &, int kind, cudaStream_t);
+cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t, int nsm);
 
 constexpr int CTILE = 1024;        // rows per compaction tile
 constexpr int STILE = 2048;        // elements per generic scan tile

@@ -9,6 +9,8 @@
 
 namespace msg {
 
+std::atomic<long long> g_kernel_launches{0};
+
 static int grid_cap(long long work_blocks, int nsm, int per_sm) {
     long long g = std::min<long long>(work_blocks, (long long)nsm * per_sm);
     return (int)std::max<long long>(1, g);
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ Row
 
 cudaError_t launch_bin_scatter(const RowArrays &ra, cudaStream_t st, int nsm) {
     if (ra.R == 0) return cudaSuccess;
-    k_bin_scatter<<<grid_cap((ra.R + 255) / 256, nsm, 8), 256, 0, st>>>(ra);
+    k_bin_scatter<<<grid_cap((ra.R + 255) / 256, nsm, 8), 256, 0, st>>>(ra); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -140,9 +142,9 @@ cudaError_t launch_scan_room(const RowArrays &ra, const long long *room, long lo
     const long long n = ra.R;
     if (n == 0) return cudaMemsetAsync(total, 0, sizeof(long long), st);
     const long long nt = (n + STILE - 1) / STILE;
-    k_tile_sums_ll<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, n, tile_buf, nt);
-    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, total);
-    k_room_apply<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, ra.tmpoff, n, tile_buf, comp_base, nt);
+    k_tile_sums_ll<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, n, tile_buf, nt); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, total); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_room_apply<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(room, ra.tmpoff, n, tile_buf, comp_base, nt); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -212,9 +214,9 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Pro
 
 cudaError_t launch_count_tiles(const ProdSet &ps, const RowArrays &ra, long long ntiles, long long *tile_sums,
                                long long *tile_offs, long long *prod_totals, cudaStream_t st, int nsm) {
-    if (ntiles > 0) k_count_tiles<<<grid_cap(ntiles, nsm, 8), 256, 0, st>>>(ps, ra, ntiles, tile_sums);
+    if (ntiles > 0) { k_count_tiles<<<grid_cap(ntiles, nsm, 8), 256, 0, st>>>(ps, ra, ntiles, tile_sums); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     // prod_totals holds 2 * P entries: [0, P) bases, [P, 2P) totals
-    k_scan_tiles<<<1, 1024, 0, st>>>(ps, ntiles, tile_sums, tile_offs, prod_totals, prod_totals + ps.P);
+    k_scan_tiles<<<1, 1024, 0, st>>>(ps, ntiles, tile_sums, tile_offs, prod_totals, prod_totals + ps.P); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -275,8 +277,8 @@ cudaError_t launch_compact(const ProdSet &ps, const RowArrays &ra, const TmpOut 
                            const long long *tile_offs, int out_bytes, cudaStream_t st, int nsm) {
     if (ntiles == 0) return cudaSuccess;
     const int g = grid_cap(ntiles, nsm, 8);
-    if (out_bytes == 4) k_compact<4><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs);
-    else k_compact<8><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs);
+    if (out_bytes == 4) { k_compact<4><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_compact<8><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     return cudaGetLastError();
 }
 
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(256) k_col_counts(const int *ci, long long nnz
 cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t st, int nsm) {
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * ((size_t)ncols + 1), st);
     if (e != cudaSuccess || nnz == 0) return e;
-    k_col_counts<<<grid_cap((nnz + 255) / 256, nsm, 8), 256, 0, st>>>(ci, nnz, counts);
+    k_col_counts<<<grid_cap((nnz + 255) / 256, nsm, 8), 256, 0, st>>>(ci, nnz, counts); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -332,9 +334,9 @@ __global__ void __launch_bounds__(256) k_scan_apply_int(const int *in, long long
 cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t st, int nsm) {
     if (n == 0) return cudaMemsetAsync(out, 0, sizeof(int), st);
     const long long nt = (n + STILE - 1) / STILE;
-    k_tile_sums_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, tile_buf, nt);
-    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, tile_buf + nt);
-    k_scan_apply_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, out, tile_buf, nt, tile_buf + nt);
+    k_tile_sums_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, tile_buf, nt); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_scan_small_ll<<<1, 1024, 0, st>>>(tile_buf, nt, tile_buf + nt); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_scan_apply_int<<<grid_cap(nt, nsm, 8), 256, 0, st>>>(in, n, out, tile_buf, nt, tile_buf + nt); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -364,9 +366,9 @@ cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, i
     if (nrows == 0) return cudaSuccess;
     (void)trp;
     const int g = grid_cap(((long long)nrows + 7) / 8, nsm, 16);
-    if (vbytes == 4) k_transpose_fill<4><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate);
-    else if (vbytes == 8) k_transpose_fill<8><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate);
-    else k_transpose_fill<0><<<g, 256, 0, st>>>(rp, ci, nullptr, nrows, cursor, tci, nullptr, gate);
+    if (vbytes == 4) { k_transpose_fill<4><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else if (vbytes == 8) { k_transpose_fill<8><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_transpose_fill<0><<<g, 256, 0, st>>>(rp, ci, nullptr, nrows, cursor, tci, nullptr, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     return cudaGetLastError();
 }
 
@@ -398,7 +400,7 @@ __global__ void __launch_bounds__(256) k_validate(const int *rp, const int *ci, 
 
 cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, long long nnz, unsigned *err,
                             cudaStream_t st, int nsm) {
-    k_validate<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, ncols, nnz, err);
+    k_validate<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, ncols, nnz, err); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -428,8 +430,8 @@ cudaError_t launch_reduce_sum(int semiring, const void *vals, const long long *d
                               int nsm) {
     cudaError_t e = cudaMemsetAsync(d_sum, 0, 8, st);
     if (e != cudaSuccess) return e;
-    if (semiring == MSGEMM_PLUS_TIMES_F32) k_reduce_sum<MSGEMM_PLUS_TIMES_F32><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum);
-    else k_reduce_sum<MSGEMM_PLUS_TIMES_I64><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum);
+    if (semiring == MSGEMM_PLUS_TIMES_F32) { k_reduce_sum<MSGEMM_PLUS_TIMES_F32><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_reduce_sum<MSGEMM_PLUS_TIMES_I64><<<nsm * 4, 256, 0, st>>>(vals, d_nnz, d_sum); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     return cudaGetLastError();
 }
 
@@ -472,8 +474,128 @@ __global__ void __launch_bounds__(1024) k_sort_heavy(const __grid_constant__ Row
 }
 
 cudaError_t launch_sort_heavy(const RowArrays &ra, int kind, cudaStream_t st) {
-    k_sort_heavy<<<1, 1024, 0, st>>>(ra, kind);
+    k_sort_heavy<<<1, 1024, 0, st>>>(ra, kind); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
+}
+
+}  // namespace msg
+
+namespace msg {
+
+// ------------------------------------------------------------ segmented sort
+// Sorts every row of a CSR matrix by column, carrying VB-byte values, in
+// place.  Bitonic network written with ascending comparators only (the first
+// step of each merge compares i with i ^ (k - 1)), so positions past the row
+// end act as +infinity without storage.  Rows up to 256 entries: one warp in
+// shared memory; up to SEG_SMEM entries: one CTA in shared memory; longer
+// rows: one CTA on global memory.
+constexpr int SEG_WARP = 256;
+constexpr int SEG_SMEM = 8192;
+
+template <int VB> struct ValT { using T = unsigned char; };
+template <> struct ValT<4> { using T = unsigned; };
+template <> struct ValT<8> { using T = unsigned long long; };
+
+template <int VB, class KeyAt, class Swap>
+__device__ __forceinline__ void bitonic_asc(int len, int tid, int nthreads, KeyAt key, Swap swp, bool cta) {
+    int N = 1;
+    while (N < len) N <<= 1;
+    for (int k = 2; k <= N; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int x = tid; x < N / 2; x += nthreads) {
+                const int i = 2 * j * (x / j) + (x % j);          // lower element of the pair
+                const int p = (j == (k >> 1)) ? (i ^ (k - 1)) : (i + j);
+                if (p < len && key(p) < key(i)) swp(i, p);
+            }
+            if (cta) __syncthreads(); else __syncwarp();
+        }
+    }
+}
+
+template <int VB>
+__global__ void __launch_bounds__(256) k_segsort_warp(const int *rp, int *ci, void *v, int nrows) {
+    using V = typename ValT<VB>::T;
+    __shared__ int sk[8][SEG_WARP];
+    __shared__ V sv[8][VB ? SEG_WARP : 1];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long gw = (long long)blockIdx.x * 8 + w, nw = (long long)gridDim.x * 8;
+    for (long long i = gw; i < nrows; i += nw) {
+        const int s = rp[i], len = rp[i + 1] - s;
+        if (len < 2 || len > SEG_WARP) continue;
+        for (int x = lane; x < len; x += 32) {
+            sk[w][x] = ci[s + x];
+            if (VB) sv[w][x] = static_cast<const V *>(v)[s + x];
+        }
+        __syncwarp();
+        bitonic_asc<VB>(len, lane, 32, [&](int a) { return sk[w][a]; },
+                        [&](int a, int b) {
+                            const int t = sk[w][a]; sk[w][a] = sk[w][b]; sk[w][b] = t;
+                            if (VB) { const V u = sv[w][a]; sv[w][a] = sv[w][b]; sv[w][b] = u; }
+                        }, false);
+        for (int x = lane; x < len; x += 32) {
+            ci[s + x] = sk[w][x];
+            if (VB) static_cast<V *>(v)[s + x] = sv[w][x];
+        }
+        __syncwarp();
+    }
+}
+
+template <int VB>
+__global__ void __launch_bounds__(256) k_segsort_cta(const int *rp, int *ci, void *v, int nrows) {
+    using V = typename ValT<VB>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *sk = reinterpret_cast<int *>(smem);
+    V *sv = reinterpret_cast<V *>(smem + 4 * SEG_SMEM);
+    for (long long i = blockIdx.x; i < nrows; i += gridDim.x) {
+        const int s = rp[i], len = rp[i + 1] - s;
+        if (len <= SEG_WARP) continue;
+        if (len <= SEG_SMEM) {
+            for (int x = threadIdx.x; x < len; x += blockDim.x) {
+                sk[x] = ci[s + x];
+                if (VB) sv[x] = static_cast<const V *>(v)[s + x];
+            }
+            __syncthreads();
+            bitonic_asc<VB>(len, threadIdx.x, blockDim.x, [&](int a) { return sk[a]; },
+                            [&](int a, int b) {
+                                const int t = sk[a]; sk[a] = sk[b]; sk[b] = t;
+                                if (VB) { const V u = sv[a]; sv[a] = sv[b]; sv[b] = u; }
+                            }, true);
+            for (int x = threadIdx.x; x < len; x += blockDim.x) {
+                ci[s + x] = sk[x];
+                if (VB) static_cast<V *>(v)[s + x] = sv[x];
+            }
+        } else {
+            int *gk = ci + s;
+            V *gv = VB ? static_cast<V *>(v) + s : nullptr;
+            bitonic_asc<VB>(len, threadIdx.x, blockDim.x, [&](int a) { return gk[a]; },
+                            [&](int a, int b) {
+                                const int t = gk[a]; gk[a] = gk[b]; gk[b] = t;
+                                if (VB) { const V u = gv[a]; gv[a] = gv[b]; gv[b] = u; }
+                            }, true);
+        }
+        __syncthreads();
+    }
+}
+
+template <int VB>
+static cudaError_t segsort_t(const int *rp, int *ci, void *v, int nrows, cudaStream_t st, int nsm) {
+    const size_t smem = 4 * SEG_SMEM + (VB ? (size_t)VB * SEG_SMEM : 0);
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_segsort_cta<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    k_segsort_warp<VB><<<grid_cap(((long long)nrows + 7) / 8, nsm, 8), 256, 0, st>>>(rp, ci, v, nrows); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_segsort_cta<VB><<<nsm * 2, 256, smem, st>>>(rp, ci, v, nrows); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t st, int nsm) {
+    if (nrows == 0) return cudaSuccess;
+    if (vbytes == 4) return segsort_t<4>(rp, ci, v, nrows, st, nsm);
+    if (vbytes == 8) return segsort_t<8>(rp, ci, v, nrows, st, nsm);
+    return segsort_t<0>(rp, ci, nullptr, nrows, st, nsm);
 }
 
 }  // namespace msg

@@ -548,12 +548,20 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             }
             mq1 = lo;
         }
+        // In-tile guards: sorted rows keep every index inside [0, T); an
+        // unsorted row (invalid input) is flagged and its stray entry skipped
+        // rather than indexing outside the tile.
         for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
             const int jj = __ldg(P.m_ci + q) - c0;
-            atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
+            if ((unsigned)jj < (unsigned)T) atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
+            else atomicOr(L.ra.err, ERR_INTERNAL);
         }
         __syncthreads();
         auto ins = [&](int jj, in_t a, in_t b) {
+            if ((unsigned)jj >= (unsigned)T) {
+                atomicOr(L.ra.err, ERR_INTERNAL);
+                return;
+            }
             const bool m = test_bit(mbits, jj);
             if (m != COMP) {   // plain: allowed iff in mask; complemented: iff not
                 S::add(&vals[jj], S::mul(a, b));
@@ -621,6 +629,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             const int seg = ((cntm + nw - 1) / nw + 31) & ~31;
             const int s0 = mq0 + min(cntm, w * seg), s1 = mq0 + min(cntm, w * seg + seg);
             auto kept = [&](int jj) -> bool {
+                if ((unsigned)jj >= (unsigned)T) return false;
                 if constexpr (S::count_set) return vals[jj] != 0;
                 else return test_bit(setw, jj);
             };
@@ -653,6 +662,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             __syncthreads();
             for (int q = s0 + lane; q < s1; q += 32) {
                 const int jj = __ldg(P.m_ci + q) - c0;
+                if ((unsigned)jj >= (unsigned)T) continue;
                 vals[jj] = 0;
                 mbits[jj >> 5] = 0;
                 setw[jj >> 5] = 0;
@@ -684,7 +694,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             __syncthreads();
             for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
                 const int jj = __ldg(P.m_ci + q) - c0;
-                mbits[jj >> 5] = 0;
+                if ((unsigned)jj < (unsigned)T) mbits[jj >> 5] = 0;
             }
             if (threadIdx.x == 0) { s_out = outbase + total; s_mpos = mq1; }
         }

@@ -32,7 +32,7 @@ cudaError_t go(const ProdSet &ps, const RowLaunch &L, int threads, size_t smem, 
         occ_smem = smem;
     }
     if (occ < 1) return cudaErrorInvalidConfiguration;
-    K<<<occ * nsm, threads, smem, st>>>(ps, L);
+    K<<<occ * nsm, threads, smem, st>>>(ps, L); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -42,7 +42,7 @@ cudaError_t MSG_CAT(launch_bin_score_, MSG_SUFFIX)(const ProdSet &ps, const RowA
                                                    long long *room, cudaStream_t st, int nsm) {
     if (ra.R == 0) return cudaSuccess;
     const long long blocks = std::min<long long>((ra.R + 7) / 8, (long long)nsm * 16);
-    k_bin_score<MSG_SR><<<(int)blocks, 256, 0, st>>>(ps, ra, pol, room);
+    k_bin_score<MSG_SR><<<(int)blocks, 256, 0, st>>>(ps, ra, pol, room); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 

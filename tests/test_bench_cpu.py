@@ -1,0 +1,47 @@
+"""Host-side helpers of bench.py (no GPU): byte models and the CPU-baseline
+sampling loop, and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import bench
+from paper_2111_09947_gb300 import synth
+
+
+def test_q_min_and_kernel_bytes():
+    p = synth.random_problem(50, 40, 60, 4.0, 4.0, 6.0, 3, "f32")
+    M, A, B = p["M"], p["A"], p["B"]
+    q = bench.q_min_bytes(M, A, B, 10, 4, 4)
+    assert q == 4 * 51 + A.nnz * 8 + 4 * 41 + B.nnz * 8 + 4 * 51 + 4 * M.nnz + 4 * 51 + 10 * 8
+    kinds = np.zeros(50, np.uint8)
+    kinds[::2] = 3
+    crp = np.zeros(51, np.int32)
+    kb = bench.kernel_bytes(kinds, 3, M, A, B, crp, 4, 4)
+    rows = np.arange(0, 50, 2)
+    anz = np.diff(A.rowptr)
+    ks = np.unique(np.concatenate([A.row(i) for i in rows]))
+    want = (8 + anz[rows] * 8).sum() + (8 + np.diff(M.rowptr)[rows] * 4).sum() + \
+        (8 + np.diff(B.rowptr)[ks] * 8).sum()
+    assert kb == want
+    assert bench.kernel_bytes(kinds, 5, M, A, B, crp, 4, 4) == 0
+
+
+def test_oracle_sample_rate_runs():
+    p = synth.triangle_counting(scale=10, ef=8, seed=1)
+    L = p["M"]
+    rate, secs, rows = bench.oracle_sample_rate(L, L, L, "plus_pair_i64", False, 0.05,
+                                                kept_fn=lambda r, res: int(res["values"].sum()))
+    assert rate >= 0 and secs > 0 and rows > 0
+
+
+def test_reference_arm_line():
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    out = subprocess.run([sys.executable, bench.__file__, "--impl", "reference", "--scale", "10", "--steps", "2",
+                          "--warmup", "1"], capture_output=True, text=True, env=env, timeout=300)
+    assert out.returncode == 0, out.stderr
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == "masked GFLOP/s"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
