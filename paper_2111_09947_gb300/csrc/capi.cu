@@ -260,7 +260,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
 
     // ---- workspace
     const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 2 + carve_size<unsigned char>(R) +
-                              carve_size<long long>(ntiles) * 2 + carve_size<long long>(2 * (size_t)P) +
+                              carve_size<long long>(ntiles) * 3 + 256 + carve_size<long long>(2 * (size_t)P) +
                               carve_size<long long>((R + STILE - 1) / STILE + 2) + carve_size<DevProd>(P) + 4096;
     CKS(grow(h, h->rows, rows_bytes));
     Carver cv(h->rows.p);
@@ -274,6 +274,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     ra.kind = cv.take<unsigned char>(R);
     long long *tile_sums = cv.take<long long>(ntiles);
     long long *tile_offs = cv.take<long long>(ntiles);
+    long long *chunk_start = cv.take<long long>(ntiles + 1);
     long long *prod_tot = cv.take<long long>(2 * (size_t)P);
     long long *room_tiles = cv.take<long long>((R + STILE - 1) / STILE + 2);
     DevProd *dtab = cv.take<DevProd>(P);
@@ -304,10 +305,21 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     // ---- B^T for the pull kernel: row pointers now, entries if a row picks it
     struct BtPlan { int *rp, *cur, *ci; void *v; long long nnz; int n; const msgemm_csr *B; };
     std::vector<BtPlan> btp;
+    // Building B^T costs a pass over B; it pays only where the pull work
+    // (mask entries x average column length of B) is well below the push work
+    // (entries of A x average row length of B), or when DOT is forced.
+    auto want_bt = [&](const ProdIn &x) {
+        if (x.comp || x.bt_rp || !x.a_sorted) return false;
+        if (h->force == F_DOT) return true;
+        const double bnz = (double)x.B->nnz;
+        const double push = (double)x.A->nnz * bnz / std::max(1, x.B->nrows);
+        const double pull = (double)x.M->nnz * bnz / std::max(1, x.B->ncols);
+        return pull * 4.0 < push;
+    };
     if (build_bt && h->allow_dot && (h->force == F_AUTO || h->force == F_DOT)) {
         size_t bytes = 0;
         for (int p = 0; p < P; ++p) {
-            if (in[p].comp || dp[p].bt_rp || !in[p].a_sorted) continue;
+            if (!want_bt(in[p])) continue;
             const msgemm_csr *B = in[p].B;
             bytes += carve_size<int>((size_t)B->ncols + 1) * 2 + carve_size<int>(B->nnz) +
                      carve_size<char>((size_t)B->nnz * in_bytes(sr)) + carve_size<long long>(B->ncols / STILE + 4);
@@ -317,7 +329,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
             CKS(grow(h, h->bt, bytes));
             Carver cb(h->bt.p);
             for (int p = 0; p < P; ++p) {
-                if (in[p].comp || dp[p].bt_rp || !in[p].a_sorted) continue;
+                if (!want_bt(in[p])) continue;
                 const msgemm_csr *B = in[p].B;
                 BtPlan b{};
                 b.B = B;
@@ -430,7 +442,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     // ---- count, allocate complemented outputs, compact
     {
         PScope ph(h, "count");
-        CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, st, h->nsm));
+        CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, chunk_start, st, h->nsm));
     }
     if (any_comp) {
         std::vector<long long> tot(P);
@@ -452,7 +464,10 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     }
     {
         PScope ph(h, "compact");
-        CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, ob, st, h->nsm));
+        // chunks: at most one per tile plus one per CCH entries of the capacity
+        long long cap = 0;
+        for (int p = 0; p < P; ++p) cap += in[p].C->capacity;
+        CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, chunk_start, ntiles + cap / CCH + 1, ob, st, h->nsm));
     }
     return MSGEMM_OK;
 }

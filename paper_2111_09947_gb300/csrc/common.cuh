@@ -191,13 +191,17 @@ __host__ __device__ __forceinline__ long long pow2_at_least(long long x) {
 __host__ __device__ __forceinline__ long long align8(long long x) { return (x + 7) & ~7LL; }
 __host__ __device__ __forceinline__ long long words32(long long bits) { return (bits + 31) >> 5; }
 
-// Hash (mask-keyed) table size: load factor 0.25 (Sec. 5.3) when it fits,
-// else 0.5.  Returns 0 if even 0.5 does not fit.
+// Hash (mask-keyed) table: 32-bit keys and 16-bit ranks per slot.
+__host__ __device__ __forceinline__ long long hash_table_bytes(long long H) { return align8(6 * H); }
+// Table size: load factor 0.25 (Sec. 5.3) when it fits, else 0.5; ranks are
+// 16-bit, so mask rows longer than 65535 never take this form.  Returns 0 if
+// it does not fit.
 __host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc, bool setbits, long long slab) {
+    if (mnz > 65535) return 0;
     long long extra = align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
     long long h4 = pow2_at_least(4 * mnz), h2 = pow2_at_least(2 * mnz);
-    if (h4 * 8 + extra <= slab) return h4;
-    if (h2 * 8 + extra <= slab) return h2;
+    if (hash_table_bytes(h4) + extra <= slab) return h4;
+    if (hash_table_bytes(h2) + extra <= slab) return h2;
     return 0;
 }
 __host__ __device__ __forceinline__ long long mca_bytes(long long mnz, int acc, bool setbits) {

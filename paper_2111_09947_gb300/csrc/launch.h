@@ -47,9 +47,11 @@ cudaError_t launch_bin_scatter(const RowArrays &, cudaStream_t, int nsm);
 cudaError_t launch_scan_room(const RowArrays &, const long long *room, long long comp_base, long long *tile_buf,
                              long long *total, cudaStream_t, int nsm);
 cudaError_t launch_count_tiles(const ProdSet &, const RowArrays &, long long ntiles, long long *tile_sums,
-                               long long *tile_offs, long long *prod_totals, cudaStream_t, int nsm);
+                               long long *tile_offs, long long *prod_totals, long long *chunk_start, cudaStream_t,
+                               int nsm);
 cudaError_t launch_compact(const ProdSet &, const RowArrays &, const TmpOut &, long long ntiles,
-                           const long long *tile_offs, int out_bytes, cudaStream_t, int nsm);
+                           const long long *tile_offs, const long long *chunk_start, long long max_chunks,
+                           int out_bytes, cudaStream_t, int nsm);
 cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t, int nsm);
 cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t, int nsm);
 cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows,
@@ -63,6 +65,7 @@ cudaError_t launch_sort_heavy(const RowArrays &, int kind, cudaStream_t);
 cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t, int nsm);
 
 constexpr int CTILE = 1024;        // rows per compaction tile
+constexpr int CCH = 8192;          // output entries per compaction chunk
 constexpr int STILE = 2048;        // elements per generic scan tile
 
 }  // namespace msg

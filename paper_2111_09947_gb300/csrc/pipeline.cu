@@ -180,10 +180,10 @@ __global__ void __launch_bounds__(256) k_count_tiles(const __grid_constant__ Pro
 // entry count to *c_nnz, c_rp[m] and prod_totals[p].
 __global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ ProdSet ps, long long ntiles,
                                                      const long long *sums, long long *offs, long long *prod_base,
-                                                     long long *prod_totals) {
+                                                     long long *prod_totals, long long *chunk_start) {
     __shared__ long long sh[33];
-    __shared__ long long carry;
-    if (threadIdx.x == 0) carry = 0;
+    __shared__ long long carry, ccarry;
+    if (threadIdx.x == 0) carry = ccarry = 0;
     __syncthreads();
     for (long long b = 0; b < ntiles; b += blockDim.x) {
         const long long x = b + threadIdx.x;
@@ -191,10 +191,16 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Pro
         long long tot;
         const long long ex = block_excl_scan_ll(val, sh, &tot);
         if (x < ntiles) offs[x] = carry + ex;
+        // copy chunks of a tile: at least one (it also writes the row pointers)
+        const long long nch = x < ntiles ? std::max(1LL, (val + CCH - 1) / CCH) : 0;
+        long long ctot;
+        const long long cex = block_excl_scan_ll(nch, sh, &ctot);
+        if (x < ntiles) chunk_start[x] = ccarry + cex;
         __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
+        if (threadIdx.x == 0) { carry += tot; ccarry += ctot; }
         __syncthreads();
     }
+    if (threadIdx.x == 0) chunk_start[ntiles] = ccarry;
     for (int p = threadIdx.x; p < ps.P; p += blockDim.x) {
         const DevProd &P = prod_at(ps, p);
         const long long nt = (P.m + CTILE - 1) / CTILE;
@@ -213,25 +219,43 @@ __global__ void __launch_bounds__(1024) k_scan_tiles(const __grid_constant__ Pro
 }
 
 cudaError_t launch_count_tiles(const ProdSet &ps, const RowArrays &ra, long long ntiles, long long *tile_sums,
-                               long long *tile_offs, long long *prod_totals, cudaStream_t st, int nsm) {
+                               long long *tile_offs, long long *prod_totals, long long *chunk_start, cudaStream_t st,
+                               int nsm) {
     if (ntiles > 0) { k_count_tiles<<<grid_cap(ntiles, nsm, 8), 256, 0, st>>>(ps, ra, ntiles, tile_sums); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     // prod_totals holds 2 * P entries: [0, P) bases, [P, 2P) totals
-    k_scan_tiles<<<1, 1024, 0, st>>>(ps, ntiles, tile_sums, tile_offs, prod_totals, prod_totals + ps.P); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_scan_tiles<<<1, 1024, 0, st>>>(ps, ntiles, tile_sums, tile_offs, prod_totals, prod_totals + ps.P, chunk_start); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
-// Row pointers of C from the tile offsets and a block scan of the counts;
-// then each warp copies the kept entries of its rows out of the temporary room.
+// Compaction: the output of a tile (CTILE rows of one product) is cut into
+// chunks of CCH entries, one CTA per chunk.  The CTA rebuilds its tile's
+// row offsets by a block scan of the kept counts (and the first chunk of the
+// tile writes them into C's row pointers), then copies its output range:
+// each output position finds its row by binary search over the offsets, so
+// reads and writes stay coalesced whatever the row lengths.
 template <int OUTB>
 __global__ void __launch_bounds__(256) k_compact(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
                                                  const __grid_constant__ TmpOut tmp, long long ntiles,
-                                                 const long long *offs) {
+                                                 const long long *offs, const long long *chunk_start) {
     using V = typename std::conditional<OUTB == 4, unsigned, unsigned long long>::type;
     __shared__ long long sh[33];
-    __shared__ int rowoff[CTILE];
+    __shared__ int rowoff[CTILE + 1];
+    __shared__ long long src0[CTILE];
+    __shared__ long long s_tile;
     constexpr int PER = CTILE / 256;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const long long nch = chunk_start[ntiles];
+    for (long long ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        if (threadIdx.x == 0) {
+            long long lo = 0, hi = ntiles - 1;
+            while (lo < hi) {
+                const long long mid = (lo + hi + 1) >> 1;
+                if (chunk_start[mid] <= ch) lo = mid; else hi = mid - 1;
+            }
+            s_tile = lo;
+        }
+        __syncthreads();
+        const long long t = s_tile;
+        const long long sub = ch - chunk_start[t];
         const DevProd &P = prod_at(ps, prod_of_tile(ps, t));
         const long long lt = t - P.tile0;
         const int i0 = (int)(lt * CTILE);
@@ -245,40 +269,44 @@ __global__ void __launch_bounds__(256) k_compact(const __grid_constant__ ProdSet
             s += c[u];
         }
         long long tot;
-        long long ex = block_excl_scan_ll(s, sh, &tot) + offs[t];
+        long long ex = block_excl_scan_ll(s, sh, &tot);
 #pragma unroll
         for (int u = 0; u < PER; ++u) {
             const int il = threadIdx.x * PER + u;
             if (i0 + il < i1) {
                 rowoff[il] = (int)ex;
-                P.c_rp[i0 + il] = (int)ex;
+                src0[il] = ra.tmpoff[P.row0 + i0 + il];
+                if (sub == 0) P.c_rp[i0 + il] = (int)(offs[t] + ex);
             }
             ex += c[u];
         }
         __syncthreads();
+        const int nrow = i1 - i0;
+        const long long base = offs[t];
+        const long long o1 = std::min(tot, (sub + 1) * (long long)CCH);
         const V *src = static_cast<const V *>(tmp.v);
         V *dst = static_cast<V *>(P.c_v);
-        for (int il = w; il < i1 - i0; il += blockDim.x >> 5) {
-            const long long r = P.row0 + i0 + il;
-            const int cnt = ra.cnt[r];
-            if (cnt == 0) continue;
-            const long long so = ra.tmpoff[r];
-            const int d0 = rowoff[il];
-            for (int x = lane; x < cnt; x += 32) {
-                P.c_ci[d0 + x] = tmp.ci[so + x];
-                dst[d0 + x] = src[so + x];
+        for (long long o = sub * (long long)CCH + threadIdx.x; o < o1; o += blockDim.x) {
+            int lo = 0, hi = nrow - 1;   // last row whose offset is <= o (it holds o)
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (rowoff[mid] <= o) lo = mid; else hi = mid - 1;
             }
+            const long long so = src0[lo] + (o - rowoff[lo]);
+            P.c_ci[base + o] = tmp.ci[so];
+            dst[base + o] = src[so];
         }
         __syncthreads();
     }
 }
 
 cudaError_t launch_compact(const ProdSet &ps, const RowArrays &ra, const TmpOut &tmp, long long ntiles,
-                           const long long *tile_offs, int out_bytes, cudaStream_t st, int nsm) {
+                           const long long *tile_offs, const long long *chunk_start, long long max_chunks,
+                           int out_bytes, cudaStream_t st, int nsm) {
     if (ntiles == 0) return cudaSuccess;
-    const int g = grid_cap(ntiles, nsm, 8);
-    if (out_bytes == 4) { k_compact<4><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
-    else { k_compact<8><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    const int g = grid_cap(max_chunks, nsm, 8);
+    if (out_bytes == 4) { k_compact<4><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs, chunk_start); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_compact<8><<<g, 256, 0, st>>>(ps, ra, tmp, ntiles, tile_offs, chunk_start); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     return cudaGetLastError();
 }
 

@@ -56,8 +56,13 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
     using in_t = typename Sr<SR>::in_t;
     Team<CTA> team;
     const int lane = lane_id();
-    for (int w0 = o0 + team.warp() * 32; w0 < o1; w0 += team.nwarps() * 32) {
-        const int t = w0 + lane;
+    // Outer entries are dealt to the team's warps round-robin (entry x goes to
+    // warp x mod nw), so every warp of a CTA-row gets work even for short
+    // outer lists; a warp's window holds its next 32 entries.
+    const int nw = team.nwarps(), wq = team.warp();
+    const int cnt = o1 - o0;
+    for (int b0 = 0; wq + nw * b0 < cnt; b0 += 32) {
+        const int t = o0 + wq + nw * (b0 + lane);
         int s = 0, e = 0;
         in_t av{};
         if (t < o1) {
@@ -66,8 +71,9 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             e = __ldg(irp + c + 1);
             if constexpr (OUTV) av = load_val<SR>(ov, t);
         }
+        const int tbase = o0 + wq + nw * b0;   // outer position of lane 0's entry
         if (!flat) {
-            const int nu = min(32, o1 - w0);
+            const int nu = min(32, (cnt - wq - nw * b0 + nw - 1) / nw);
             for (int u = 0; u < nu; ++u) {
                 const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
                 const in_t au = shfl_val<SR>(av, u);
@@ -85,7 +91,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
                     }
 #pragma unroll
                     for (int x = 0; x < 4; ++x)
-                        if (col[x] >= 0) f(w0 + u, au, col[x], bv[x]);
+                        if (col[x] >= 0) f(tbase + nw * u, au, col[x], bv[x]);
                 }
             }
         } else {
@@ -105,7 +111,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
                 const in_t ak = shfl_val<SR>(av, k & 31);
                 if (p < total) {
                     const int q = sk + p - xk;
-                    f(w0 + k, ak, __ldg(ici + q), load_val<SR>(iv, q));
+                    f(tbase + nw * k, ak, __ldg(ici + q), load_val<SR>(iv, q));
                 }
             }
         }
@@ -215,10 +221,12 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
     const long long H = hash_slots(mnz, (int)sizeof(acc_t), SrSizes<SR>::setbits, L.slab);
     const int logH = ilog2(H);
     const unsigned hmask = (unsigned)H - 1u;
-    unsigned long long *tab = reinterpret_cast<unsigned long long *>(slab);
-    acc_t *acc = reinterpret_cast<acc_t *>(slab + H * 8);
-    unsigned *sb = reinterpret_cast<unsigned *>(slab + H * 8 + align8((long long)mnz * sizeof(acc_t)));
-    for (long long h = team.tid(); h < H; h += team.size()) tab[h] = EMPTY64;
+    // slot h: key[h] (mask column or EMPTY) and rank[h] (its position in the mask row)
+    unsigned *key = reinterpret_cast<unsigned *>(slab);
+    unsigned short *rank = reinterpret_cast<unsigned short *>(slab + 4 * H);
+    acc_t *acc = reinterpret_cast<acc_t *>(slab + hash_table_bytes(H));
+    unsigned *sb = reinterpret_cast<unsigned *>(slab + hash_table_bytes(H) + align8((long long)mnz * sizeof(acc_t)));
+    for (long long h = team.tid(); h < H; h += team.size()) key[h] = EMPTY32;
     for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
     if constexpr (SrSizes<SR>::setbits)
         for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
@@ -226,22 +234,21 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
     for (int q = team.tid(); q < mnz; q += team.size()) {   // setAllowed for every mask column
         const unsigned j = (unsigned)__ldg(P.m_ci + c.m0 + q);
         unsigned h = hash32(j, logH);
-        const unsigned long long ent = ((unsigned long long)q << 32) | j;
-        while (atomicCAS(&tab[h], EMPTY64, ent) != EMPTY64) h = (h + 1) & hmask;
+        while (atomicCAS(&key[h], EMPTY32, j) != EMPTY32) h = (h + 1) & hmask;
+        rank[h] = (unsigned short)q;
     }
     team.sync();
     auto ins = [&](int, in_t a, int j, in_t b) {
         unsigned h = hash32((unsigned)j, logH);
         for (;;) {   // terminates: at least half of the slots are empty
-            const unsigned long long e = tab[h];
-            const unsigned key = (unsigned)e;
-            if (key == (unsigned)j) {
-                const int rk = (int)(e >> 32);
+            const unsigned kk = key[h];
+            if (kk == (unsigned)j) {
+                const int rk = rank[h];
                 S::add(&acc[rk], S::mul(a, b));
                 if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
                 return;
             }
-            if (key == EMPTY32) return;   // NOTALLOWED: product never evaluated
+            if (kk == EMPTY32) return;   // NOTALLOWED: product never evaluated
             h = (h + 1) & hmask;
         }
     };
@@ -572,8 +579,9 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
             enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), f);
         } else {
-            for (int w0 = c.a0 + team.warp() * 32; w0 < c.a1; w0 += team.nwarps() * 32) {
-                const int t = w0 + lane;
+            const int nwq = team.nwarps(), wq = team.warp();
+            for (int b0 = 0; wq + nwq * b0 < c.a1 - c.a0; b0 += 32) {
+                const int t = c.a0 + wq + nwq * (b0 + lane);
                 int4 cu = make_int4(0, 0, INT_MAX, 0);
                 in_t av{};
                 if (t < c.a1) {
