@@ -1,17 +1,18 @@
 #!/usr/bin/env python
 """Masked SpGEMM benchmark on GB300.
 
-Default workload: triangle counting on an R-MAT graph of scale 20 (edge
-factor 16, Graph500 quadrant probabilities), symmetrised, loops and
-duplicates removed, degree-relabelled; C = L .* (L L) on plus-pair int64 and
-the count sum(C) (Sec. 8.2).  One step = the whole path on resident inputs:
-binning, accumulators, compaction and the count reduction.  The metric is
-masked GFLOP/s = 2 x (products kept by the mask) / time.
+Default workload (--workload tc): triangle counting on an R-MAT graph of
+scale 20 (edge factor 16, Graph500 quadrant probabilities), symmetrised,
+loops and duplicates removed, degree-relabelled; C = L .* (L L) on plus-pair
+int64 and the count sum(C) (Sec. 8.2).  One step = the whole path on resident
+inputs: binning, accumulators, compaction and the count reduction.  The
+metric is masked GFLOP/s = 2 x (products kept by the mask) / time.
 
-Also reported (key "forms"): the plain fp32 product on Erdos-Renyi n = 4096,
-the complemented BFS step of multi-source betweenness centrality (512
-sources, scale 20), 256 batched products against per-product calls, and the
-forward + backward pass of the differentiable form (R-MAT scale 18).
+Other workloads (also reported under "forms" of the default run):
+  er        plain fp32 product, Erdos-Renyi n = 4096, 8 entries per row
+  bfs       complemented step of multi-source BFS (512 sources, scale 20)
+  batched   256 independent fp32 products in one call (vs 256 calls)
+  autograd  forward + backward of the differentiable form (R-MAT scale 18)
 
 --impl reference times the CPU oracle (the plain C program under oracle/)
 on bounded row samples of the same workload.
@@ -21,7 +22,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -35,26 +35,28 @@ sys.path.insert(0, REPO)
 import numpy as np  # noqa: E402
 
 L2_FLUSH_BYTES = 256 << 20     # > 129 MB L2
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0}
+WORKLOADS = ("tc", "er", "bfs", "batched", "autograd")
 _T0 = time.perf_counter()
 
 
 def log(msg: str) -> None:
     """Progress on stderr (the JSON line alone goes to stdout)."""
     print(f"[bench {time.perf_counter() - _T0:7.1f}s] {msg}", file=sys.stderr, flush=True)
-PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
 
 
-def parse_args():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--scale", type=int, default=20, help="R-MAT scale of the triangle-count workload")
+    ap.add_argument("--workload", choices=WORKLOADS, default="tc")
+    ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (tc: 20, bfs: 20, autograd: 18)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def peaks():
@@ -62,9 +64,9 @@ def peaks():
     try:
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     except Exception:
-        return {"hbm_gbs": PEAKS_FALLBACK["hbm_gbs"], "source": "fallback"}
+        return {"hbm_gbs": PEAKS_FALLBACK["hbm_gbs"], "source": "fallback 6.8 TB/s"}
 
 
 # ----------------------------------------------------------------- clocks
@@ -105,33 +107,30 @@ class ClockSampler:
             self.proc.kill()
         if self.thread:
             self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
-            return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return summarize_clocks(self.lines)
 
 
-# ----------------------------------------------------------------- workload math
-def masked_products_from_pp(res_pp) -> int:
-    """Products kept by the mask = sum of the plus-pair result."""
-    v = res_pp.values[: res_pp.nnz()]
-    return int(v.sum().item())
+def summarize_clocks(lines):
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower().startswith("active"):
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ----------------------------------------------------------------- byte / flop models
 def push_products(A, B) -> int:
     bl = np.diff(B.rowptr).astype(np.int64)
     return int(bl[A.colidx].sum())
@@ -191,8 +190,139 @@ def traffic_for(kernel: str, workload: str):
     return e.get("dram_bytes_per_launch")
 
 
-# ----------------------------------------------------------------- timing
-def timed_steps(torch, step, steps, flush_buf, stream):
+VB = {"plus_times_f32": (4, 4), "plus_times_i64": (8, 8), "plus_pair_i64": (0, 8)}
+
+
+# ----------------------------------------------------------------- workloads
+class Workload:
+    """A benchmark workload: host inputs and its counts.
+
+    mats: list of (M, A, B, complement) host products one step runs;
+    kept: products kept by the masks per step; masked flops = 2 * kept."""
+
+    def __init__(self, name, semiring, config, mats, dtype):
+        self.name = name
+        self.semiring = semiring
+        self.config = config
+        self.mats = mats
+        self.dtype = dtype
+        self.kept = None
+        self.nnz_c = None
+
+
+def build_workload(name, scale, seed):
+    from paper_2111_09947_gb300 import synth
+    if name == "tc":
+        scale = scale or 20
+        tc = synth.triangle_counting(scale=scale, ef=16, seed=seed)
+        L = tc["M"]
+        cfg = {"workload": f"triangle counting: R-MAT scale {scale}, edge factor 16, (a,b,c)=(0.57,0.19,0.19), "
+                           "symmetrised, loops/duplicates removed, degree-relabelled, L strict lower; "
+                           "C = L .* (L L) plus-pair int64 + count", "n": L.nrows, "nnz_L": L.nnz}
+        return Workload(name, "plus_pair_i64", cfg, [(L, L, L, False)], "int64")
+    if name == "er":
+        p = synth.er_plain_f32(seed=seed)
+        cfg = {"workload": "plain masked product, fp32: A, B, M independent Erdos-Renyi n=4096, 8 entries per row, "
+                           "values uniform[-1,1)", "n": 4096, "nnz_A": p["A"].nnz, "nnz_M": p["M"].nnz}
+        return Workload(name, "plus_times_f32", cfg, [(p["M"], p["A"], p["B"], False)], "f32")
+    if name == "bfs":
+        scale = scale or 20
+        b = synth.bfs_step(scale=scale, ef=16, nsrc=512, seed=seed)
+        cfg = {"workload": f"multi-source BFS step, complemented mask: C = !Visited .* (F A), plus-times int64; "
+                           f"A = R-MAT scale {scale} ef 16 symmetrised (values 1), F = level-2 frontier of 512 "
+                           "random sources with path counts", "n": b["B"].nrows, "nnz_F": b["A"].nnz,
+               "nnz_visited": b["M"].nnz, "nnz_A": b["B"].nnz}
+        return Workload(name, "plus_times_i64", cfg, [(b["M"], b["A"], b["B"], True)], "int64")
+    if name == "batched":
+        ps = synth.batched_problems(nprod=256, seed=seed)
+        cfg = {"workload": "256 independent fp32 products in one call: n log-uniform in [2^10, 2^16], A/B R-MAT "
+                           "ef 8, M Erdos-Renyi with {1,16,256} entries per row",
+               "rows": int(sum(p["n"] for p in ps)), "nnz_M": int(sum(p["M"].nnz for p in ps))}
+        return Workload(name, "plus_times_f32", cfg, [(p["M"], p["A"], p["B"], False) for p in ps], "f32")
+    if name == "autograd":
+        scale = scale or 18
+        a = synth.autograd_problem(scale=scale, ef=16, seed=seed)
+        cfg = {"workload": f"differentiable masked product, fp32, forward + backward: A R-MAT scale {scale} ef 16 "
+                           "N(0,1), B = pattern(A^T) N(0,1), M = pattern(A), G N(0,1) on C",
+               "n": a["A"].nrows, "nnz_A": a["A"].nnz}
+        return Workload(name, "plus_times_f32", cfg, [(a["M"], a["A"], a["B"], False)], "f32")
+    raise ValueError(name)
+
+
+class DeviceRun:
+    """Device copies of a workload's inputs and its step callable."""
+
+    def __init__(self, torch, _lib, synth, h, wl, dev):
+        self.torch, self._lib, self.h, self.wl, self.dev = torch, _lib, h, wl, dev
+        sr = wl.semiring
+        vd = {"plus_times_f32": torch.float32, "plus_times_i64": torch.int64, "plus_pair_i64": None}[sr]
+        keep = sr != "plus_pair_i64"
+        cache = {}
+
+        def dv(m, values):
+            key = (id(m), values)
+            if key not in cache:
+                d = _lib.DeviceCsr.from_host(m, device=dev, values_dtype=vd if values else None)
+                if not values:
+                    d.values = None
+                cache[key] = d
+            return cache[key]
+        self.prods = [(dv(M, False), dv(A, keep), dv(B, keep), c) for (M, A, B, c) in wl.mats]
+        self.G = None
+        if wl.name == "autograd":
+            M, A, B, _ = self.prods[0]
+            res = _lib.msgemm_run(h, M, A, B, sr).trimmed()
+            self.G = _lib.DeviceCsr(res.nrows, res.ncols, res.rowptr, res.colidx,
+                                    torch.from_numpy(synth.upstream_grad(res.nnz)).to(dev))
+
+    def step(self):
+        """One step; returns (result object, a device scalar to read back)."""
+        _lib, h, sr = self._lib, self.h, self.wl.semiring
+        name = self.wl.name
+        if name == "tc":
+            L = self.prods[0][0]
+            r = _lib.msgemm_run(h, L, L, L, sr)
+            return r, _lib.msgemm_reduce_sum(h, r, sr)
+        if name == "batched":
+            Ms, As, Bs = [p[0] for p in self.prods], [p[1] for p in self.prods], [p[2] for p in self.prods]
+            outs = _lib.msgemm_run_batched(h, Ms, As, Bs, sr)
+            return outs[0], outs[-1].d_nnz
+        M, A, B, comp = self.prods[0]
+        if name == "autograd":
+            r = _lib.msgemm_run(h, M, A, B, sr)
+            _lib.msgemm_backward(h, A, B, self.G)
+            return r, r.d_nnz
+        r = _lib.msgemm_run(h, M, A, B, sr, comp)
+        return r, r.d_nnz
+
+    def per_product_step(self):
+        """The batched workload as separate calls (the plain path)."""
+        for (M, A, B, c) in self.prods:
+            self._lib.msgemm_run(self.h, M, A, B, self.wl.semiring, c)
+
+    def count_kept(self):
+        """Products kept by the masks: the sum of the plus-pair result."""
+        _lib, h = self._lib, self.h
+
+        def pat(d):
+            return _lib.DeviceCsr(d.nrows, d.ncols, d.rowptr, d.colidx, None)
+        kept, nnz_c = 0, 0
+        for (M, A, B, c) in self.prods:
+            r = _lib.msgemm_run(h, pat(M), pat(A), pat(B), "plus_pair_i64", c)
+            kept += int(_lib.msgemm_reduce_sum(h, r, "plus_pair_i64").item())
+            nnz_c += r.nnz()
+        if self.wl.name == "autograd":
+            # backward: dA = pattern(A) .* (G B^T), dB = pattern(B) .* (A^T G)
+            M, A, B, _ = self.prods[0]
+            Bt = _lib.msgemm_transpose(h, pat(B), 0, True)
+            At = _lib.msgemm_transpose(h, pat(A), 0, True)
+            for (mm, aa, bb) in ((pat(A), pat(self.G), pat(Bt)), (pat(B), pat(At), pat(self.G))):
+                r = _lib.msgemm_run(h, mm, aa, bb, "plus_pair_i64")
+                kept += int(_lib.msgemm_reduce_sum(h, r, "plus_pair_i64").item())
+        return kept, nnz_c
+
+
+def timed_steps(torch, step, steps, flush_buf, stream, after=None):
     """Per-step device times (ms) with CUDA events on the launching stream;
     L2 flushed (a write larger than L2) before each step, outside the timing."""
     times = []
@@ -205,12 +335,14 @@ def timed_steps(torch, step, steps, flush_buf, stream):
         b.record(stream)
         b.synchronize()
         times.append(a.elapsed_time(b))
+        if after:
+            after()
     return times
 
 
 def oracle_sample_rate(M, A, B, semiring, complement, target_s, rng_seed=7, kept_fn=None):
     """Times the CPU oracle on random row samples until about target_s of
-    work; returns (masked GFLOP/s, seconds, rows, sample description)."""
+    work; returns (masked GFLOP/s, seconds, rows)."""
     from oracle import oracle as O
     rng = np.random.default_rng(rng_seed)
     m = M.nrows
@@ -235,7 +367,125 @@ def oracle_sample_rate(M, A, B, semiring, complement, target_s, rng_seed=7, kept
     return total_f / total_t / 1e9, total_t, total_rows
 
 
-# ----------------------------------------------------------------- main arm
+def kept_from_oracle(M, A, B, complement):
+    """kept_fn for oracle samples: products kept in the sampled rows, counted
+    by the oracle in plus-pair (not part of the timed oracle call)."""
+    from oracle import oracle as O
+
+    def fn(rows, res):
+        pp = O.masked_spgemm(M, A, B, "plus_pair_i64", complement=complement,
+                             method=O.ESC if complement else O.MERGE, rows=rows)
+        return int(pp["values"].sum())
+    return fn
+
+
+# ----------------------------------------------------------------- measurement
+def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks_gpu=None):
+    """Times `steps` steps of a workload; returns a dict of measurements."""
+    run = DeviceRun(torch, _lib, synth, h, wl, dev)
+    wl.kept, wl.nnz_c = run.count_kept()
+    h.set_option(_lib.OPT_PROFILE, 1)
+    for _ in range(warmup):
+        run.step()
+    torch.cuda.synchronize()
+    kinds = h.row_kinds(wl.mats[0][0].nrows) if len(wl.mats) == 1 and wl.name != "autograd" else None
+    clocks = ClockSampler(clocks_gpu) if clocks_gpu is not None else None
+    if clocks:
+        clocks.start()
+    per_phase = {}
+    l0 = _lib.load().msgemm_kernel_launches()
+
+    def collect():
+        for name, ms in h.profile():
+            per_phase.setdefault(name, []).append(ms)
+    times = timed_steps(torch, run.step, steps, flush, stream, after=collect)
+    launches = _lib.load().msgemm_kernel_launches() - l0
+    clk = clocks.stop() if clocks else None
+    out = {"times": times, "launches": launches, "clocks": clk, "per_phase": per_phase, "kinds": kinds, "run": run}
+    if wl.name == "batched":
+        run.per_product_step()
+        torch.cuda.synchronize()
+        out["per_product_ms"] = statistics.median(timed_steps(torch, run.per_product_step, 3, flush, stream))
+    if wl.name == "autograd":
+        M, A, B, _ = run.prods[0]
+        fwd = lambda: _lib.msgemm_run(h, M, A, B, wl.semiring)  # noqa: E731
+        bwd = lambda: _lib.msgemm_backward(h, A, B, run.G)  # noqa: E731
+        out["fwd_ms"] = statistics.median(timed_steps(torch, fwd, 5, flush, stream))
+        out["bwd_ms"] = statistics.median(timed_steps(torch, bwd, 5, flush, stream))
+    return out
+
+
+def roofline_of(_lib, wl, meas):
+    """Roofline of the dominant accumulator kernel (single-product workloads):
+    its compulsory bytes (rows of A and M it processes, distinct rows of B
+    they touch, their output) over its mean launch time."""
+    pk = peaks()
+    kind_ids = {n: i for i, n in enumerate(_lib.KIND_NAMES)}
+    cand = {n: statistics.mean(v) for n, v in meas["per_phase"].items() if n in kind_ids and n != "empty"}
+    if not cand or meas["kinds"] is None:
+        return None
+    dom = max(cand, key=cand.get)
+    dom_ms = cand[dom]
+    M, A, B, comp = wl.mats[0]
+    vb_in, vb_out = VB[wl.semiring]
+    r, _ = meas["run"].step()
+    C_rp = r.rowptr.cpu().numpy()
+    kb = kernel_bytes(meas["kinds"], kind_ids[dom], M, A, B, C_rp, vb_in, vb_out)
+    achieved = kb / (dom_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
+            "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": traffic_for(dom, wl.name),
+            "peak_source": pk["source"], "algorithmic_bytes_per_launch": kb, "kernel_ms": round(dom_ms, 4)}
+
+
+def e2e_measure(torch, run, flush, stream, steps):
+    """Same workload through the C ABI from pinned host buffers: every step
+    copies its inputs host->device, runs, and reads a result scalar back."""
+    wl = run.wl
+    seen, uniq, h2d = set(), [], 0
+    for (Md, Ad, Bd, _c) in run.prods:
+        for d in (Md, Ad, Bd):
+            for t in (d.rowptr, d.colidx, d.values):
+                if t is None or t.numel() == 0 or t.data_ptr() in seen:
+                    continue
+                seen.add(t.data_ptr())
+                uniq.append((t.cpu().pin_memory(), t))
+                h2d += t.numel() * t.element_size()
+    out_h = torch.empty(1, dtype=torch.int64).pin_memory()
+
+    def step():
+        for hsrc, dst in uniq:
+            dst.copy_(hsrc, non_blocking=True)
+        _, scalar = run.step()
+        out_h.copy_(scalar.view(-1)[:1].view(torch.int64), non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    t = timed_steps(torch, step, steps, flush, stream)
+    ms = statistics.mean(t)
+    return {"value": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 8, "ms_per_step": round(ms, 4)}
+
+
+def form_summary(wl, meas):
+    ms = statistics.mean(meas["times"])
+    d = {"ms_per_step": round(ms, 4), "masked_products": wl.kept,
+         "masked_gflops": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3)}
+    if len(wl.mats) == 1:
+        M, A, B, comp = wl.mats[0]
+        vb_in, vb_out = VB[wl.semiring]
+        d["hbm_min_gbs"] = round(q_min_bytes(M, A, B, wl.nnz_c, vb_in, vb_out) / (ms * 1e-3) / 1e9, 2)
+        d["push_products"] = push_products(A, B)
+    if meas["per_phase"]:
+        d["phase_ms"] = {n: round(statistics.mean(v), 4) for n, v in meas["per_phase"].items()}
+    for k in ("per_product_ms", "fwd_ms", "bwd_ms"):
+        if k in meas:
+            d[k] = round(meas[k], 3)
+    if "per_product_ms" in meas:
+        d["batched_speedup"] = round(meas["per_product_ms"] / ms, 2)
+    return d
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -251,154 +501,78 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     seed = synth.BASE_SEED + 7919 * rank      # weak scaling: one instance per rank
-
-    # ---- workload (host), then resident on the device
-    log('generating triangle-count workload')
-    t_gen = time.perf_counter()
-    tc = synth.triangle_counting(scale=args.scale, ef=16, seed=seed)
-    L = tc["M"]
-    gen_s = time.perf_counter() - t_gen
-    Ld = _lib.DeviceCsr.from_host(L, device=dev)
-    Ld.values = None
     h = _lib.Handle(dev)
-    h.set_option(_lib.OPT_PROFILE, 1)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
-    def step():
-        r = _lib.msgemm_run(h, Ld, Ld, Ld, "plus_pair_i64")
-        s = _lib.msgemm_reduce_sum(h, r, "plus_pair_i64")
-        return r, s
-
-    log('warm-up')
-    for _ in range(args.warmup):
-        r, s = step()
-    torch.cuda.synchronize()
-    triangles = int(s.item())
-    nnz_c = r.nnz()
-    kept = triangles                       # plus-pair: each kept product counts 1
-    masked_flops = 2 * kept
-    kinds = h.row_kinds(L.nrows)
-    C_rp = r.rowptr.cpu().numpy()
-
-    # ---- timed region
-    log('timed steps')
+    log(f"generating {args.workload} workload")
+    t_gen = time.perf_counter()
+    wl = build_workload(args.workload, args.scale, seed)
+    gen_s = time.perf_counter() - t_gen
+    log("measuring")
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    clocks = ClockSampler(local)
-    clocks.start()
-    l0 = _lib.load().msgemm_kernel_launches()
-    per_kernel = {}
-    times = []
-    for i in range(args.steps):
-        flush.fill_(i & 0xFF)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        r, s = step()
-        b.record(stream)
-        b.synchronize()
-        times.append(a.elapsed_time(b))
-        for name, ms in h.profile():
-            per_kernel.setdefault(name, []).append(ms)
-    launches = _lib.load().msgemm_kernel_launches() - l0
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    total_ms = sum(times)
+    meas = measure(torch, _lib, synth, h, wl, dev, stream, flush, args.steps, args.warmup, local)
+    total_ms = sum(meas["times"])
+    flops = 2.0 * wl.kept
     if world > 1:
         t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-        f = torch.tensor([masked_flops], dtype=torch.float64, device=dev)
+        f = torch.tensor([flops], dtype=torch.float64, device=dev)
         dist.all_reduce(f, op=dist.ReduceOp.SUM)
-        flops_all = float(f.item())
-    else:
-        flops_all = float(masked_flops)
+        flops = float(f.item())
     ms_per_step = total_ms / args.steps
-    value = flops_all * args.steps / (total_ms * 1e-3) / 1e9
-    assert int(s.item()) == triangles
-
-    # ---- roofline of the dominant accumulator kernel
-    pk = peaks()
-    kind_ids = {n: i for i, n in enumerate(_lib.KIND_NAMES)}
-    cand = {n: statistics.mean(v) for n, v in per_kernel.items() if n in kind_ids and n != "empty"}
-    dom = max(cand, key=cand.get)
-    dom_ms = cand[dom]
-    kb = kernel_bytes(kinds, kind_ids[dom], L, L, L, C_rp, 0, 8)
-    achieved = kb / (dom_ms * 1e-3) / 1e9
-    traffic = traffic_for(dom, f"tc_scale{args.scale}")
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 5), "traffic": traffic,
-                "peak_source": pk["source"] + " (MEASURED_PEAKS.json hbm_gbs)" if pk["source"] == "measured"
-                else "fallback 6.8 TB/s", "algorithmic_bytes_per_launch": kb, "kernel_ms": round(dom_ms, 4)}
-    qmin = q_min_bytes(L, L, L, nnz_c, 0, 8)
-    pushp = push_products(L, L)
-    phase_ms = {n: round(statistics.mean(v), 4) for n, v in per_kernel.items()}
-
-    # ---- end to end through the C ABI from pinned host buffers
-    log('end-to-end steps')
-    rp_h = torch.from_numpy(L.rowptr).pin_memory()
-    ci_h = torch.from_numpy(L.colidx).pin_memory()
-    rp_d = torch.empty_like(rp_h, device=dev)
-    ci_d = torch.empty_like(ci_h, device=dev)
-    out_h = torch.empty(1, dtype=torch.int64).pin_memory()
-    Le = _lib.DeviceCsr(L.nrows, L.ncols, rp_d, ci_d, None)
-
-    def e2e_step():
-        rp_d.copy_(rp_h, non_blocking=True)
-        ci_d.copy_(ci_h, non_blocking=True)
-        rr = _lib.msgemm_run(h, Le, Le, Le, "plus_pair_i64")
-        ss = _lib.msgemm_reduce_sum(h, rr, "plus_pair_i64")
-        out_h.copy_(ss, non_blocking=True)
-
-    for _ in range(2):
-        e2e_step()
-    torch.cuda.synchronize()
-    et = timed_steps(torch, e2e_step, max(3, args.steps // 2), flush, stream)
-    assert int(out_h.item()) == triangles
-    e2e_ms = statistics.mean(et)
-    h2d = rp_h.numel() * 4 + ci_h.numel() * 4
-
+    value = flops * args.steps / (total_ms * 1e-3) / 1e9
+    summary = form_summary(wl, meas)
+    log("roofline and end-to-end")
+    roof = roofline_of(_lib, wl, meas)
+    if roof is None:
+        pk = peaks()
+        q = summary.get("hbm_min_gbs")
+        roof = {"bound": "hbm", "kernel": "whole step", "achieved": q, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": round(q / pk["hbm_gbs"], 5) if q else None, "traffic": None, "peak_source": pk["source"]}
+    e2e = e2e_measure(torch, meas["run"], flush, stream, max(3, args.steps // 2))
+    cfg = dict(wl.config)
+    cfg.update({"masked_products": wl.kept, "nnz_C": wl.nnz_c, "l2": "flushed before every timed step (256 MiB write)",
+                "seed_per_rank": True})
     line = {
         "metric": "masked GFLOP/s", "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
-        "data": "synthetic (seeded R-MAT; the paper's SuiteSparse graphs are not used)",
-        "config": {"workload": f"triangle counting: R-MAT scale {args.scale}, edge factor 16, (a,b,c)=(0.57,0.19,0.19), "
-                               "symmetrised, loops/duplicates removed, degree-relabelled, L strict lower; "
-                               "C = L .* (L L) plus-pair int64 + count",
-                   "n": L.nrows, "nnz_L": L.nnz, "triangles": triangles, "nnz_C": nnz_c,
-                   "masked_products": kept, "push_products": pushp,
-                   "l2": "flushed before every timed step (256 MiB write)", "seed_per_rank": True},
-        "gpu_launches": int(launches),
-        "roofline": roofline,
-        "hbm_min_gbs": round(qmin / (ms_per_step * 1e-3) / 1e9, 2),
-        "push_effective_gbs": round(pushp * 4 / (ms_per_step * 1e-3) / 1e9, 2),
-        "push_gflops": round(2 * pushp / (ms_per_step * 1e-3) / 1e9, 2),
-        "phase_ms": phase_ms,
-        "clocks": clk,
-        "e2e": {"value": round(2 * kept / (e2e_ms * 1e-3) / 1e9, 3), "unit": "GFLOP/s",
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": 8, "ms_per_step": round(e2e_ms, 4)},
-        "gen_seconds": round(gen_s, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype,
+        "data": "synthetic (seeded R-MAT / Erdos-Renyi; the paper's SuiteSparse graphs are not used)",
+        "config": cfg, "gpu_launches": int(meas["launches"]), "roofline": roof,
+        "hbm_min_gbs": summary.get("hbm_min_gbs"), "phase_ms": summary.get("phase_ms"),
+        "clocks": meas["clocks"], "e2e": e2e, "gen_seconds": round(gen_s, 2),
     }
+    if "push_products" in summary:
+        line["push_gflops"] = round(2 * summary["push_products"] / (ms_per_step * 1e-3) / 1e9, 2)
+    for k in ("per_product_ms", "batched_speedup", "fwd_ms", "bwd_ms"):
+        if k in summary:
+            line[k] = summary[k]
 
-    # ---- CPU baseline: the oracle on a bounded row sample (rank 0, N = 1)
-    log('cpu baseline')
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rp_pp = C_rp
-        cvals = r.values[:nnz_c].cpu().numpy()
-
-        def kept_fn(rows, res):
-            return int(res["values"].sum())
-        cores = os.cpu_count()
-        rate, secs, nrows = oracle_sample_rate(L, L, L, "plus_pair_i64", False, args.cpu_seconds, kept_fn=kept_fn)
-        what = ("the whole C" if nrows >= L.nrows else f"{nrows} uniformly drawn rows of the same C")
-        line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{what} (oracle merge per mask entry, all cores), {secs:.1f} s"}
-        del rp_pp, cvals
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and len(wl.mats) == 1:
+        log("cpu baseline")
+        M, A, B, comp = wl.mats[0]
+        kfn = (lambda rows, res: int(res["values"].sum())) if wl.semiring == "plus_pair_i64" \
+            else kept_from_oracle(M, A, B, comp)
+        rate, secs, nrows = oracle_sample_rate(M, A, B, wl.semiring, comp, args.cpu_seconds, kept_fn=kfn)
+        what = "the whole C" if nrows >= M.nrows else f"{nrows} uniformly drawn rows of the same C"
+        line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{what} ({'expand-sort-compress' if comp else 'merge per mask entry'}, "
+                                          f"all cores), {secs:.1f} s"}
 
     if rank == 0 and not args.no_forms:
-        line["forms"] = other_forms(torch, h, dev, stream, flush, synth, _lib)
+        forms = {}
+        for name in WORKLOADS:
+            if name == args.workload:
+                continue
+            log(f"form: {name}")
+            fw = build_workload(name, None, synth.BASE_SEED)
+            fm = measure(torch, _lib, synth, h, fw, dev, stream, flush, 5, 2, None)
+            forms[name] = dict(config=fw.config["workload"], **form_summary(fw, fm))
+            del fm
+            torch.cuda.empty_cache()
+        line["forms"] = forms
 
     h.close()
     if rank == 0:
@@ -406,102 +580,6 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
-
-
-def other_forms(torch, h, dev, stream, flush, synth, _lib):
-    forms = {}
-    h.set_option(_lib.OPT_PROFILE, 0)
-    K = 10
-
-    # plain fp32, Erdos-Renyi n = 4096, 8 per row
-    log('form: er plain fp32')
-    p = synth.er_plain_f32()
-    d = {k: _lib.DeviceCsr.from_host(v, device=dev) for k, v in p.items()}
-    d["M"].values = None
-    pp = {k: _lib.DeviceCsr(v.nrows, v.ncols, v.rowptr, v.colidx, None) for k, v in d.items()}
-    kept = masked_products_from_pp(_lib.msgemm_run(h, pp["M"], pp["A"], pp["B"], "plus_pair_i64"))
-    step = lambda: _lib.msgemm_run(h, d["M"], d["A"], d["B"], "plus_times_f32")  # noqa: E731
-    for _ in range(5):
-        step()
-    t = timed_steps(torch, step, K, flush, stream)
-    ms = statistics.median(t)
-    forms["er_plain_f32"] = {"n": 4096, "avg_per_row": 8, "us_per_call": round(ms * 1e3, 2),
-                             "masked_products": kept, "masked_gflops": round(2 * kept / (ms * 1e-3) / 1e9, 4)}
-
-    # complemented BFS step, 512 sources
-    log('form: bfs step')
-    b = synth.bfs_step(scale=20, ef=16, nsrc=512)
-    db = {k: _lib.DeviceCsr.from_host(v, device=dev) for k, v in (("M", b["M"]), ("A", b["A"]), ("B", b["B"]))}
-    db["M"].values = None
-    dpp = {k: _lib.DeviceCsr(v.nrows, v.ncols, v.rowptr, v.colidx, None) for k, v in db.items()}
-    rpp = _lib.msgemm_run(h, dpp["M"], dpp["A"], dpp["B"], "plus_pair_i64", complement=True)
-    kept = masked_products_from_pp(rpp)
-    nnz_c = rpp.nnz()
-    del rpp
-    step = lambda: _lib.msgemm_run(h, db["M"], db["A"], db["B"], "plus_times_i64", complement=True)  # noqa: E731
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize()
-    t = timed_steps(torch, step, 5, flush, stream)
-    ms = statistics.median(t)
-    q = q_min_bytes(b["M"], b["A"], b["B"], nnz_c, 8, 8, True)
-    forms["bfs_complement_i64"] = {"sources": int(b["A"].nrows), "ms_per_step": round(ms, 3),
-                                   "masked_products": kept, "nnz_C": nnz_c,
-                                   "masked_gflops": round(2 * kept / (ms * 1e-3) / 1e9, 3),
-                                   "hbm_min_gbs": round(q / (ms * 1e-3) / 1e9, 2),
-                                   "push_products": push_products(b["A"], b["B"])}
-    del db, dpp, b
-    torch.cuda.empty_cache()
-
-    # batched: 256 products in one call vs 256 calls
-    log('form: batched')
-    ps = synth.batched_problems(nprod=256)
-    devs = []
-    for q in ps:
-        x = {k: _lib.DeviceCsr.from_host(v, device=dev) for k, v in (("M", q["M"]), ("A", q["A"]), ("B", q["B"]))}
-        x["M"].values = None
-        devs.append(x)
-    Ms, As, Bs = [x["M"] for x in devs], [x["A"] for x in devs], [x["B"] for x in devs]
-
-    def per_product():
-        for x in devs:
-            _lib.msgemm_run(h, x["M"], x["A"], x["B"], "plus_times_f32")
-
-    def batched():
-        _lib.msgemm_run_batched(h, Ms, As, Bs, "plus_times_f32")
-
-    for _ in range(2):
-        per_product()
-        batched()
-    tp = statistics.median(timed_steps(torch, per_product, 3, flush, stream))
-    tb = statistics.median(timed_steps(torch, batched, 5, flush, stream))
-    forms["batched_256_f32"] = {"products": len(ps), "per_product_ms": round(tp, 3), "batched_ms": round(tb, 3),
-                                "speedup": round(tp / tb, 2)}
-    del devs, Ms, As, Bs
-    torch.cuda.empty_cache()
-
-    # differentiable form: forward, backward, forward + backward
-    log('form: autograd')
-    a = synth.autograd_problem(scale=18, ef=16)
-    da = {k: _lib.DeviceCsr.from_host(v, device=dev) for k, v in a.items()}
-    da["M"].values = None
-    res = _lib.msgemm_run(h, da["M"], da["A"], da["B"], "plus_times_f32").trimmed()
-    G = _lib.DeviceCsr(res.nrows, res.ncols, res.rowptr, res.colidx,
-                       torch.from_numpy(synth.upstream_grad(res.nnz)).to(dev))
-    fwd = lambda: _lib.msgemm_run(h, da["M"], da["A"], da["B"], "plus_times_f32")  # noqa: E731
-    bwd = lambda: _lib.msgemm_backward(h, da["A"], da["B"], G)  # noqa: E731
-
-    def fwdbwd():
-        fwd()
-        bwd()
-    for _ in range(2):
-        fwdbwd()
-    tf = statistics.median(timed_steps(torch, fwd, 5, flush, stream))
-    tbw = statistics.median(timed_steps(torch, bwd, 5, flush, stream))
-    tfb = statistics.median(timed_steps(torch, fwdbwd, 5, flush, stream))
-    forms["autograd_f32_scale18"] = {"nnz_A": int(a["A"].nnz), "fwd_ms": round(tf, 3), "bwd_ms": round(tbw, 3),
-                                     "fwd_bwd_ms": round(tfb, 3), "bwd_over_fwd": round(tbw / tf, 2)}
-    return forms
 
 
 # ----------------------------------------------------------------- reference arm
@@ -515,42 +593,47 @@ def run_reference(args):
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     from oracle import oracle as O
     from paper_2111_09947_gb300 import synth
-    tc = synth.triangle_counting(scale=args.scale, ef=16, seed=synth.BASE_SEED)
-    L = tc["M"]
+    name = args.workload if args.workload in ("tc", "er", "bfs", "autograd") else "tc"
+    wl = build_workload(name, args.scale, synth.BASE_SEED)
+    M, A, B, comp = wl.mats[0]
+    method = O.ESC if comp else O.MERGE
     rng = np.random.default_rng(11)
-    # size one step's sample to ~ a few seconds
     frac = 0.002
     t0 = time.perf_counter()
-    rows = np.sort(rng.choice(L.nrows, size=max(1, int(L.nrows * frac)), replace=False)).astype(np.int32)
-    O.masked_spgemm(L, L, L, "plus_pair_i64", rows=rows)
+    rows = np.sort(rng.choice(M.nrows, size=max(1, int(M.nrows * frac)), replace=False)).astype(np.int32)
+    O.masked_spgemm(M, A, B, wl.semiring, complement=comp, method=method, rows=rows)
     dt = time.perf_counter() - t0
     frac = min(1.0, frac * max(1.0, 4.0 / max(dt, 1e-3)))
-    nrow = max(1, int(L.nrows * frac))
+    nrow = max(1, int(M.nrows * frac))
     times, flops = [], []
     for s in range(args.warmup + args.steps):
-        rows = np.sort(rng.choice(L.nrows, size=nrow, replace=False)).astype(np.int32)
+        rows = np.sort(rng.choice(M.nrows, size=nrow, replace=False)).astype(np.int32)
         t0 = time.perf_counter()
-        res = O.masked_spgemm(L, L, L, "plus_pair_i64", rows=rows)
+        res = O.masked_spgemm(M, A, B, wl.semiring, complement=comp, method=method, rows=rows)
         dt = time.perf_counter() - t0
         if s >= args.warmup:
             times.append(dt)
-            flops.append(2 * int(res["values"].sum()))
+            if wl.semiring == "plus_pair_i64":
+                kept = int(res["values"].sum())
+            else:
+                kept = kept_from_oracle(M, A, B, comp)(rows, res)
+            flops.append(2 * kept)
     value = sum(flops) / sum(times) / 1e9
-    sample = f"{nrow} uniformly drawn rows per step (of {L.nrows}), oracle merge per mask entry"
+    sample = f"{nrow} uniformly drawn rows per step (of {M.nrows}), oracle " + \
+             ("expand-sort-compress" if comp else "merge per mask entry")
     line = {"impl": "reference", "metric": "masked GFLOP/s", "value": round(value, 4), "unit": "GFLOP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1e3 * sum(times) / len(times), 2), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "int64", "data": "synthetic (seeded R-MAT)",
-            "config": {"workload": f"triangle counting: R-MAT scale {args.scale}, edge factor 16, relabelled, "
-                                   "C = L .* (L L) plus-pair int64", "n": L.nrows, "nnz_L": L.nnz},
+            "vs_baseline": None, "dtype": wl.dtype, "data": "synthetic (seeded R-MAT / Erdos-Renyi)",
+            "config": wl.config,
             "cpu_baseline": {"value": round(value, 4), "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(value, 4), "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
-def main():
-    args = parse_args()
+def main(argv=None):
+    args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
         return

@@ -37,7 +37,7 @@ struct msgemm_handle {
     int force = 0, validate = 0, allow_dot = 1;
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
-    int warp_flops_max = 4096;
+    int warp_flops_max = 65536;
     int *last_kind_count = nullptr;
     unsigned char *last_kind = nullptr;
     long long last_R = 0;

@@ -579,14 +579,35 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
             enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), f);
         } else {
-            const int nwq = team.nwarps(), wq = team.warp();
-            for (int b0 = 0; wq + nwq * b0 < c.a1 - c.a0; b0 += 32) {
-                const int t = c.a0 + wq + nwq * (b0 + lane);
+            // Contiguous windows of 32 entries per warp (coalesced cursor
+            // loads).  Pass 1: every lane advances its own entry's segment
+            // inside the tile, up to LS entries, so the many short segments
+            // (low-degree k) proceed 32 at a time.  Pass 2: segments still
+            // open (long rows of B) are walked by the whole warp; the next
+            // column after the tile comes from the loaded chunk by shuffle.
+            constexpr int LS = 3;
+            for (int w0 = c.a0 + team.warp() * 32; w0 < c.a1; w0 += team.nwarps() * 32) {
+                const int t = w0 + lane;
                 int4 cu = make_int4(0, 0, INT_MAX, 0);
                 in_t av{};
-                if (t < c.a1) {
-                    cu = cur[t];
-                    if constexpr (Sr<SR>::vals) av = load_val<SR>(P.a_v, t);
+                if (t < c.a1) cu = cur[t];
+                if (!__any_sync(FULL, cu.z < c1)) continue;
+                if constexpr (Sr<SR>::vals) {
+                    if (t < c.a1) av = load_val<SR>(P.a_v, t);
+                }
+                const int x0 = cu.x;
+#pragma unroll 1
+                for (int rep = 0; rep < LS; ++rep) {
+                    const bool go = cu.z < c1;
+                    if (!__any_sync(FULL, go)) break;
+                    if (go) {
+                        const in_t b = load_val<SR>(P.b_v, cu.x);
+                        const int nx = cu.x + 1;
+                        const int ncol = nx < cu.y ? __ldg(P.b_ci + nx) : INT_MAX;
+                        ins(cu.z - c0, av, b);
+                        cu.x = nx;
+                        cu.z = ncol;
+                    }
                 }
                 unsigned act = __ballot_sync(FULL, cu.z < c1);
                 while (act) {
@@ -594,7 +615,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                     act &= act - 1;
                     const int pos = __shfl_sync(FULL, cu.x, u), end = __shfl_sync(FULL, cu.y, u);
                     const in_t au = shfl_val<SR>(av, u);
-                    int stop = end;
+                    int stop = end, nextc = INT_MAX;
                     for (int q0 = pos; q0 < end; q0 += 128) {
                         int col[4];
                         in_t bv[4];
@@ -612,7 +633,11 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                                 if (ok) ins(col[x] - c0, au, bv[x]);
                                 const unsigned okm = __ballot_sync(FULL, ok);
                                 if (okm != FULL) {
-                                    stop = q0 + x * 32 + __popc(okm);
+                                    // sorted row: the ok lanes are a prefix; the
+                                    // first other lane holds the next column
+                                    const int first = __popc(okm);
+                                    stop = q0 + x * 32 + first;
+                                    nextc = __shfl_sync(FULL, col[x], first);
                                     done = true;
                                 }
                             }
@@ -621,10 +646,10 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                     }
                     if (lane == u) {
                         cu.x = stop;
-                        cu.z = stop < end ? __ldg(P.b_ci + stop) : INT_MAX;
-                        cur[t] = cu;
+                        cu.z = stop < end ? nextc : INT_MAX;
                     }
                 }
+                if (t < c.a1 && cu.x != x0) cur[t] = cu;
             }
         }
         __syncthreads();
