@@ -24,7 +24,9 @@ __device__ __forceinline__ int pick_family(const Policy &pol, int fam, bool warp
     switch (fam) {
     case F_MSA:
         if (warp && pol.slab[K_MSA_W] > 0 && msa_bytes(n, acc) <= pol.slab[K_MSA_W]) return K_MSA_W;
-        if (forced || n <= pol.tileT[0]) return K_MSA_T;
+        // the one-CTA form pays a CTA per row: unforced, only for CTA-sized
+        // rows whose columns fit one shared-memory tile
+        if (forced || (!warp && n <= pol.tileT[0])) return K_MSA_T;
         return -1;
     case F_HASH:
         if (warp && pol.slab[K_HASH_W] > 0 && hash_slots(mnz, acc, sb, pol.slab[K_HASH_W])) return K_HASH_W;

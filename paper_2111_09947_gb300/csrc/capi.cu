@@ -167,7 +167,7 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.dot_ratio = h->dot_ratio;
     p.warp_flops_max = h->warp_flops_max;
     const int acc = acc_bytes(sr);
-    const int wslab = 4096;
+    const int wslab = 4608;   // per warp: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
     const int bslab = 64 * 1024;
     const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
     p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
@@ -303,8 +303,6 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     }
 
     // ---- B^T for the pull kernel: row pointers now, entries if a row picks it
-    struct BtPlan { int *rp, *cur, *ci; void *v; long long nnz; int n; const msgemm_csr *B; };
-    std::vector<BtPlan> btp;
     // Building B^T costs a pass over B; it pays only where the pull work
     // (mask entries x average column length of B) is well below the push work
     // (entries of A x average row length of B), or when DOT is forced.
@@ -316,37 +314,46 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         const double pull = (double)x.M->nnz * bnz / std::max(1, x.B->ncols);
         return pull * 4.0 < push;
     };
+    std::vector<BtDesc> bd;
+    long long bt_counts = 0, bt_nnz = 0, bt_rows = 0;
     if (build_bt && h->allow_dot && (h->force == F_AUTO || h->force == F_DOT)) {
-        size_t bytes = 0;
         for (int p = 0; p < P; ++p) {
             if (!want_bt(in[p])) continue;
             const msgemm_csr *B = in[p].B;
-            bytes += carve_size<int>((size_t)B->ncols + 1) * 2 + carve_size<int>(B->nnz) +
-                     carve_size<char>((size_t)B->nnz * in_bytes(sr)) + carve_size<long long>(B->ncols / STILE + 4);
+            bd.push_back(BtDesc{B->rowptr, B->colidx, B->values, B->nrows, B->ncols, B->nnz, bt_counts, bt_nnz,
+                                bt_rows});
+            bt_counts += (long long)B->ncols + 1;
+            bt_nnz += B->nnz;
+            bt_rows += B->nrows;
         }
-        if (bytes) {
-            PScope ph(h, "bt_counts");
-            CKS(grow(h, h->bt, bytes));
-            Carver cb(h->bt.p);
-            for (int p = 0; p < P; ++p) {
-                if (!want_bt(in[p])) continue;
-                const msgemm_csr *B = in[p].B;
-                BtPlan b{};
-                b.B = B;
-                b.n = B->ncols;
-                b.nnz = B->nnz;
-                b.rp = cb.take<int>((size_t)B->ncols + 1);
-                b.cur = cb.take<int>((size_t)B->ncols + 1);
-                b.ci = cb.take<int>(B->nnz);
-                b.v = cb.take<char>((size_t)B->nnz * in_bytes(sr));
-                long long *tb = cb.take<long long>(B->ncols / STILE + 4);
-                CK(launch_col_counts(B->colidx, B->nnz, B->ncols, b.cur, st, h->nsm));
-                CK(launch_excl_scan_int(b.cur, B->ncols, b.rp, tb, st, h->nsm));
-                dp[p].bt_rp = b.rp;
-                dp[p].bt_ci = b.ci;
-                dp[p].bt_v = in_bytes(sr) ? b.v : nullptr;
-                btp.push_back(b);
-            }
+    }
+    int *bt_rp_all = nullptr, *bt_cur = nullptr, *bt_ci = nullptr;
+    void *bt_v = nullptr;
+    BtDesc *bt_tab = nullptr;
+    if (!bd.empty()) {
+        PScope ph(h, "bt_counts");
+        const int Q = (int)bd.size();
+        const size_t bytes = carve_size<int>(bt_counts + 1) * 2 + carve_size<int>(bt_nnz) +
+                             carve_size<char>((size_t)bt_nnz * in_bytes(sr)) +
+                             carve_size<long long>(bt_counts / STILE + 4) + carve_size<BtDesc>(Q);
+        CKS(grow(h, h->bt, bytes));
+        Carver cb(h->bt.p);
+        bt_rp_all = cb.take<int>(bt_counts + 1);
+        bt_cur = cb.take<int>(bt_counts + 1);
+        bt_ci = cb.take<int>(bt_nnz);
+        bt_v = cb.take<char>((size_t)bt_nnz * in_bytes(sr));
+        long long *tb = cb.take<long long>(bt_counts / STILE + 4);
+        bt_tab = cb.take<BtDesc>(Q);
+        CK(cudaMemcpyAsync(bt_tab, bd.data(), sizeof(BtDesc) * Q, cudaMemcpyHostToDevice, st));
+        CK(launch_bt_counts_multi(bt_tab, Q, bt_nnz, bt_cur, bt_counts, st, h->nsm));
+        CK(launch_excl_scan_int(bt_cur, bt_counts, bt_rp_all, tb, st, h->nsm));
+        int q = 0;
+        for (int p = 0; p < P; ++p) {
+            if (!want_bt(in[p])) continue;
+            dp[p].bt_rp = bt_rp_all + bd[q].co;
+            dp[p].bt_ci = bt_ci;
+            dp[p].bt_v = in_bytes(sr) ? bt_v : nullptr;
+            ++q;
         }
     }
 
@@ -396,11 +403,11 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     }
 
     // ---- B^T entries, only when some row picked the pull kernel
-    for (const BtPlan &b : btp) {
+    if (!bd.empty()) {
         PScope ph(h, "bt_fill");
-        CK(cudaMemcpyAsync(b.cur, b.rp, sizeof(int) * ((size_t)b.n + 1), cudaMemcpyDeviceToDevice, st));
-        CK(launch_transpose_fill(b.B->rowptr, b.B->colidx, b.B->values, in_bytes(sr), b.B->nrows, b.rp, b.cur, b.ci,
-                                 b.v, ra.any_dot, st, h->nsm));
+        CK(cudaMemcpyAsync(bt_cur, bt_rp_all, sizeof(int) * (size_t)(bt_counts + 1), cudaMemcpyDeviceToDevice, st));
+        CK(launch_bt_fill_multi(bt_tab, (int)bd.size(), bt_rows, in_bytes(sr), bt_cur, bt_ci, bt_v, ra.any_dot, st,
+                                h->nsm));
     }
 
     // ---- accumulation, one persistent kernel per kind
@@ -418,7 +425,7 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (any_plain) {
         if (pol.slab[K_MSA_W]) kinds.push_back(K_MSA_W);
         kinds.insert(kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
-        if (!btp.empty() || std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
+        if (!bd.empty() || std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
             kinds.insert(kinds.end(), {K_DOT_W, K_DOT_B});
         kinds.push_back(K_MSA_T);
     }

@@ -62,6 +62,20 @@ cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, 
 cudaError_t launch_reduce_sum(int semiring, const void *vals, const long long *d_nnz, void *d_sum, cudaStream_t,
                               int nsm);
 cudaError_t launch_sort_heavy(const RowArrays &, int kind, cudaStream_t);
+// One product's B for the multi-product transpose (pull kernel).
+struct BtDesc {
+    const int *rp, *ci;
+    const void *v;
+    int nrows, ncols;
+    long long nnz;
+    long long co;   // first count slot (ncols + 1 slots per product)
+    long long eo;   // first entry in the concatenation of all entries
+    long long ro;   // first row in the concatenation of all rows
+};
+cudaError_t launch_bt_counts_multi(const BtDesc *d, int Q, long long total_nnz, int *counts, long long ncounts,
+                                   cudaStream_t, int nsm);
+cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, int vbytes, int *cursor, int *tci,
+                                 void *tv, const int *gate, cudaStream_t, int nsm);
 cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t, int nsm);
 
 constexpr int CTILE = 1024;        // rows per compaction tile

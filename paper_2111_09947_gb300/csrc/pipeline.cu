@@ -627,3 +627,67 @@ cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrow
 }
 
 }  // namespace msg
+
+namespace msg {
+
+// ------------------------------------------------------------ multi-product transpose
+// B^T for the pull kernel, for every product of a call at once: column
+// counts of all B's go to one concatenated array (product q owns slots
+// [co, co + ncols]), one exclusive scan turns it into row pointers that index
+// a shared entry array, and one fill kernel scatters the entries.
+__device__ __forceinline__ int bt_of(const BtDesc *d, int Q, long long x, bool by_rows) {
+    int lo = 0, hi = Q - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((by_rows ? d[mid].ro : d[mid].eo) <= x) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(256) k_col_counts_multi(const BtDesc *d, int Q, long long total, int *counts) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        const int q = bt_of(d, Q, e, false);
+        atomicAdd(&counts[d[q].co + d[q].ci[e - d[q].eo]], 1);
+    }
+}
+
+template <int VB>
+__global__ void __launch_bounds__(256) k_transpose_fill_multi(const BtDesc *d, int Q, long long rows, int *cursor,
+                                                              int *tci, void *tv, const int *gate) {
+    if (gate && *gate == 0) return;
+    using V = typename std::conditional<VB == 4, unsigned, unsigned long long>::type;
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long r = gw; r < rows; r += nw) {
+        const int q = bt_of(d, Q, r, true);
+        const BtDesc &b = d[q];
+        const int i = (int)(r - b.ro);
+        const int s = b.rp[i], e = b.rp[i + 1];
+        for (int t = s + lane; t < e; t += 32) {
+            const int pos = atomicAdd(&cursor[b.co + b.ci[t]], 1);
+            tci[pos] = i;
+            if (VB) static_cast<V *>(tv)[pos] = static_cast<const V *>(b.v)[t];
+        }
+    }
+}
+
+cudaError_t launch_bt_counts_multi(const BtDesc *d, int Q, long long total_nnz, int *counts, long long ncounts,
+                                   cudaStream_t st, int nsm) {
+    cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (size_t)ncounts, st);
+    if (e != cudaSuccess || total_nnz == 0) return e;
+    k_col_counts_multi<<<grid_cap((total_nnz + 255) / 256, nsm, 8), 256, 0, st>>>(d, Q, total_nnz, counts); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, int vbytes, int *cursor, int *tci,
+                                 void *tv, const int *gate, cudaStream_t st, int nsm) {
+    if (total_rows == 0) return cudaSuccess;
+    const int g = grid_cap((total_rows + 7) / 8, nsm, 16);
+    if (vbytes == 4) { k_transpose_fill_multi<4><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else if (vbytes == 8) { k_transpose_fill_multi<8><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_transpose_fill_multi<0><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, nullptr, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    return cudaGetLastError();
+}
+
+}  // namespace msg
