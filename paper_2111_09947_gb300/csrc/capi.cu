@@ -168,7 +168,7 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.warp_flops_max = h->warp_flops_max;
     const int acc = acc_bytes(sr);
     const int wslab = 4608;   // per warp: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
-    const int bslab = 64 * 1024;
+    const int bslab = 32 * 1024;  // per CTA-row: 7 CTAs per SM
     const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
     p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
     p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;

@@ -149,7 +149,18 @@ template <> struct Sr<MSGEMM_PLUS_TIMES_I64> {
     __device__ static __forceinline__ acc_t mul(in_t a, in_t b) {
         return (unsigned long long)a * (unsigned long long)b;  // wraps mod 2^64
     }
-    __device__ static __forceinline__ void add(acc_t *p, acc_t v) { atomicAdd(p, v); }
+    // Shared-memory add mod 2^64 as two 32-bit atomics (64-bit shared atomics
+    // are about 9x slower): the low word is added and its old value returned;
+    // if that add wrapped, one carry goes to the high word with the addend's
+    // high half.  Every wrap is counted by exactly the add that caused it, so
+    // the final 64-bit value is the exact sum mod 2^64 in any order.
+    __device__ static __forceinline__ void add(acc_t *p, acc_t v) {
+        unsigned *w = reinterpret_cast<unsigned *>(p);   // little-endian: w[0] low, w[1] high
+        const unsigned lo = (unsigned)v;
+        const unsigned old = atomicAdd(w, lo);
+        const unsigned hi = (unsigned)(v >> 32) + (old + lo < old ? 1u : 0u);
+        if (hi) atomicAdd(w + 1, hi);
+    }
     __device__ static __forceinline__ out_t out(acc_t v) { return (long long)v; }
 };
 

@@ -94,6 +94,24 @@ def test_random_complement(handle, semiring, force):
         assert_parity(res, ref, semiring, ctx=f"shape {s} force {force}")
 
 
+@pytest.mark.parametrize("complement", [False, True])
+@pytest.mark.parametrize("force", ["auto", "msa", "hash", "mca", "dot"])
+def test_int64_wide_values_wrap(handle, complement, force):
+    """int64 values spread over +-2^50: products and sums wrap mod 2^64;
+    the 64-bit shared-memory accumulation (two 32-bit words with carry) must
+    match the oracle bit for bit."""
+    if complement and force in ("mca", "dot"):
+        pytest.skip("no complemented form")
+    rng = np.random.default_rng(77)
+    p = synth.random_problem(300, 200, 70000 if force == "msa" else 400, 12.0, 30.0, 40.0, 606, "pair")
+    p = {k: (v if k == "M" else v.with_values(rng.integers(-2 ** 50, 2 ** 50, v.nnz, dtype=np.int64)))
+         for k, v in p.items()}
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64", complement=complement,
+                          method=O.ESC if complement else O.MERGE)
+    res = run(handle, p, "plus_times_i64", complement, force)
+    assert_parity(res, ref, "plus_times_i64", ctx=force)
+
+
 def test_empty_matrices(handle):
     for m, k, n in [(0, 5, 7), (5, 7, 0), (0, 0, 0), (3, 4, 5)]:
         p = synth.random_problem(m, k, n, 0.0, 0.0, 0.0, 5, "f32")
