@@ -79,9 +79,13 @@ typedef enum {
                                      the product.  Without validation, out-of-range indices
                                      are undefined behaviour. */
     MSGEMM_OPT_DOT = 3,           /* value 0/1 (default 1): allow the pull (DOT) kernel in AUTO */
-    MSGEMM_OPT_PROFILE = 4        /* value 0/1 (default 0): record CUDA events around every
+    MSGEMM_OPT_PROFILE = 4,       /* value 0/1 (default 0): record CUDA events around every
                                      phase and kernel launch of a call, on the handle's stream
                                      (read back with msgemm_profile_entry) */
+    MSGEMM_OPT_TILE_INDEX = 5     /* value 0/1 (default 1): heavy rows of wide products walk
+                                     their column tiles through a per-row tile index of B
+                                     (rows(B) x (tiles + 1) ints, built per call, 4 GiB cap);
+                                     0, or a product over the cap, uses per-entry cursors */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

@@ -32,9 +32,10 @@ struct msgemm_handle {
     msgemm_free_fn free_fn = nullptr;
     void *ctx = nullptr;
     // workspace, reused across calls
-    Buf rows, small, tmp, bt, cur, prods;
+    Buf rows, small, tmp, bt, cur, prods, tix;
     unsigned *d_err = nullptr;   // in `small`, persistent
-    int force = 0, validate = 0, allow_dot = 1;
+    int force = 0, validate = 0, allow_dot = 1, tile_index = 1;
+    long long tile_index_budget = 4LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
@@ -416,8 +417,37 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     L.tmp = tmp;
     L.aligned = aligned ? 1 : 0;
     if (any_tiled) {
-        CKS(grow(h, h->cur, carve_size<int4>(std::max<long long>(nnzA, 1))));
-        L.cursors = static_cast<int4 *>(h->cur.p);
+        // tile index of B for every tiled product, within the memory budget;
+        // products left without one walk their tiles with per-entry cursors
+        const int T = pol.tileT[0];
+        long long need = 0;
+        std::vector<int> nts(P, 0);
+        for (int p = 0; p < P; ++p) {
+            if (dp[p].n <= T) continue;
+            nts[p] = (dp[p].n + T - 1) / T;
+            need += (long long)carve_size<int>((size_t)in[p].B->nrows * (nts[p] + 1));
+        }
+        bool cursors = false;
+        if (h->tile_index && need <= h->tile_index_budget) {
+            PScope ph(h, "tile_index");
+            CKS(grow(h, h->tix, (size_t)need + 256));
+            Carver ct(h->tix.p);
+            for (int p = 0; p < P; ++p) {
+                if (!nts[p]) continue;
+                int *tp = ct.take<int>((size_t)in[p].B->nrows * (nts[p] + 1));
+                CK(launch_tile_bounds(in[p].B->rowptr, in[p].B->colidx, in[p].B->nrows, T, nts[p], tp, st, h->nsm));
+                dp[p].tpos = tp;
+                dp[p].tstride = nts[p] + 1;
+            }
+            if (P == 1) ps.p0 = dp[0];
+            CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
+        } else {
+            cursors = true;
+        }
+        if (cursors) {
+            CKS(grow(h, h->cur, carve_size<int4>(std::max<long long>(nnzA, 1))));
+            L.cursors = static_cast<int4 *>(h->cur.p);
+        }
     }
     std::vector<int> kinds;
     bool any_plain = false;
@@ -563,6 +593,7 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_VALIDATE: h->validate = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_DOT: h->allow_dot = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_PROFILE: h->profile = value != 0; return MSGEMM_OK;
+    case MSGEMM_OPT_TILE_INDEX: h->tile_index = value != 0; return MSGEMM_OK;
     default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
     }
 }
@@ -787,7 +818,7 @@ void msgemm_destroy(msgemm_handle *h) {
         cudaEventDestroy(ph.a);
         cudaEventDestroy(ph.b);
     }
-    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods}) dev_free(h, b->p);
+    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix}) dev_free(h, b->p);
     delete h;
 }
 

@@ -50,6 +50,8 @@ struct DevProd {
     long long tile0;                          // first compaction tile of this product
     long long abase;                          // first cursor slot (stored entries of A before this product)
     long long tmp0;                           // first temporary-output slot of this product (plain mask)
+    const int *tpos;                          // tile index of B (rows x tstride) or null
+    int tstride;                              // column tiles + 1
     int *c_rp, *c_ci; void *c_v; long long *c_nnz;  // outputs
 };
 

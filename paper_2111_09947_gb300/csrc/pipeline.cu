@@ -691,3 +691,39 @@ cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, i
 }
 
 }  // namespace msg
+
+namespace msg {
+
+// ------------------------------------------------------------ tile index
+// For every row k of B and column tile t (width T): tpos[k * (nt + 1) + t] =
+// first position of row k whose column is >= t * T (the row end if none), so
+// the part of row k inside tile t is [tpos[.. + t], tpos[.. + t + 1]).  One
+// warp per row; every slot is first set to the row end, then each entry that
+// starts a tile writes the slots of the tiles it opens (rows are sorted).
+__global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt,
+                                                     int *tpos) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long k = gw; k < nrows; k += nw) {
+        const int s = rp[k], e = rp[k + 1];
+        int *base = tpos + k * (long long)(nt + 1);
+        for (int t = lane; t <= nt; t += 32) base[t] = e;
+        __syncwarp();
+        for (int q = s + lane; q < e; q += 32) {
+            const int tq = min(nt - 1, ci[q] / T);
+            const int tp = (q == s) ? -1 : min(nt - 1, ci[q - 1] / T);
+            for (int t = tp + 1; t <= tq; ++t) base[t] = q;
+        }
+        __syncwarp();
+    }
+}
+
+cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, cudaStream_t st,
+                               int nsm) {
+    if (nrows == 0) return cudaSuccess;
+    k_tile_bounds<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, T, nt, tpos); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
+}  // namespace msg

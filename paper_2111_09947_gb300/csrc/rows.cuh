@@ -42,23 +42,45 @@ __device__ __forceinline__ void set_bit_once(unsigned *w, int b) {
 }
 
 // --------------------------------------------------------------- enumerators
+// Inner range of outer entry t with inner row c: the whole row of the inner
+// CSR (RowSeg) or the part of it inside one column tile (TileSeg, from the
+// per-row tile index).
+struct RowSeg {
+    const int *irp;
+    __device__ __forceinline__ void operator()(int c, int &s, int &e) const {
+        s = __ldg(irp + c);
+        e = __ldg(irp + c + 1);
+    }
+};
+struct TileSeg {
+    const int *tpos;   // row c, tile t: [tpos[c * stride + t], tpos[c * stride + t + 1])
+    int stride, tile;
+    __device__ __forceinline__ void operator()(int c, int &s, int &e) const {
+        const int *p = tpos + (long long)c * stride + tile;
+        s = __ldg(p);
+        e = __ldg(p + 1);
+    }
+};
+
+enum : int { ENUM_STRIDED = 0, ENUM_FLAT = 1, ENUM_AUTO = 2 };
+
 // Calls f(t, a_t, col, val) for every (outer position t in [o0, o1), inner
-// entry q of row oci[t]) pair, with col = ici[q], val = iv[q].  Warps of the
-// team take 32-entry windows of the outer list.  Strided mode: the warp walks
-// the inner rows of a window one by one, lanes striding each row (4 loads in
-// flight per lane).  Flat mode (short inner rows): the products of a window
-// are numbered 0..total-1 and each lane finds its inner row by a binary search
-// over the window's inclusive prefix of row lengths.
-template <int SR, bool CTA, bool OUTV, class F>
+// entry q of the range seg gives for row oci[t]) pair, with col = ici[q],
+// val = iv[q].  Outer entries are dealt to the team's warps round-robin
+// (entry x goes to warp x mod nw), so every warp of a CTA-row gets work even
+// for short outer lists; a warp's window holds its next 32 entries.
+// Strided mode: the warp walks the window's inner ranges one by one, lanes
+// striding each (4 loads in flight per lane).  Flat mode (short ranges): the
+// products of a window are numbered 0..total-1 and each lane finds its range
+// by a binary search over the window's inclusive prefix of lengths.  Auto
+// picks per window: flat when the ranges average fewer than 16 entries.
+template <int SR, bool CTA, bool OUTV, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
-                                              const int *__restrict__ irp, const int *__restrict__ ici,
-                                              const void *iv, bool flat, F &f) {
+                                              const Seg &seg, const int *__restrict__ ici, const void *iv,
+                                              int mode, F &f) {
     using in_t = typename Sr<SR>::in_t;
     Team<CTA> team;
     const int lane = lane_id();
-    // Outer entries are dealt to the team's warps round-robin (entry x goes to
-    // warp x mod nw), so every warp of a CTA-row gets work even for short
-    // outer lists; a warp's window holds its next 32 entries.
     const int nw = team.nwarps(), wq = team.warp();
     const int cnt = o1 - o0;
     for (int b0 = 0; wq + nw * b0 < cnt; b0 += 32) {
@@ -66,12 +88,16 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
         int s = 0, e = 0;
         in_t av{};
         if (t < o1) {
-            const int c = __ldg(oci + t);
-            s = __ldg(irp + c);
-            e = __ldg(irp + c + 1);
+            seg(__ldg(oci + t), s, e);
             if constexpr (OUTV) av = load_val<SR>(ov, t);
         }
         const int tbase = o0 + wq + nw * b0;   // outer position of lane 0's entry
+        const int len = max(0, e - s);   // an unsorted row can give e < s in a tile index
+        const int incl = warp_incl_scan(len);
+        const int total = __shfl_sync(FULL, incl, 31);
+        if (total == 0) continue;
+        bool flat = mode == ENUM_FLAT;
+        if (mode == ENUM_AUTO) flat = total < 16 * __popc(__ballot_sync(FULL, len > 0));
         if (!flat) {
             const int nu = min(32, (cnt - wq - nw * b0 + nw - 1) / nw);
             for (int u = 0; u < nu; ++u) {
@@ -95,17 +121,14 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
                 }
             }
         } else {
-            const int len = e - s;
-            const int incl = warp_incl_scan(len);
-            const int total = __shfl_sync(FULL, incl, 31);
             const int excl = incl - len;
             for (int base = 0; base < total; base += 32) {
                 const int p = base + lane;
                 int k = 0;
 #pragma unroll
                 for (int st = 16; st > 0; st >>= 1) {
-                    const int c = __shfl_sync(FULL, incl, k + st - 1);
-                    if (c <= p) k += st;
+                    const int cc = __shfl_sync(FULL, incl, k + st - 1);
+                    if (cc <= p) k += st;
                 }
                 const int sk = __shfl_sync(FULL, s, k & 31), xk = __shfl_sync(FULL, excl, k & 31);
                 const in_t ak = shfl_val<SR>(av, k & 31);
@@ -202,9 +225,9 @@ __device__ __forceinline__ RowCtx row_ctx(const DevProd &P, long long r, const R
     return c;
 }
 
-__device__ __forceinline__ bool flat_mode(const RowCtx &c) {
+__device__ __forceinline__ int enum_mode(const RowCtx &c) {
     // average inner row shorter than 12: load-balanced flat enumeration
-    return c.flops < 12LL * (long long)(c.a1 - c.a0);
+    return c.flops < 12LL * (long long)(c.a1 - c.a0) ? ENUM_FLAT : ENUM_STRIDED;
 }
 
 // --------------------------------------------------------------- HASH rows
@@ -252,7 +275,7 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
             h = (h + 1) & hmask;
         }
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
     team.sync();
     gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -289,7 +312,7 @@ __device__ __forceinline__ void row_mca(const DevProd &P, const RowCtx &c, const
             if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, lo);
         }
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
     team.sync();
     gather_ranked<SR, CTA>(mcol, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -334,8 +357,7 @@ __device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const
             if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
         }
     };
-    const bool flat = true;   // pull pairs: columns of B are short in this regime
-    enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, P.bt_rp, P.bt_ci, P.bt_v, flat, ins);
+    enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, RowSeg{P.bt_rp}, P.bt_ci, P.bt_v, ENUM_AUTO, ins);
     team.sync();
     gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -367,7 +389,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
             if constexpr (SrSizes<SR>::setbits) set_bit_once(setw, j);
         }
     };
-    enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
     __syncwarp();
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     int base = 0;
@@ -455,7 +477,7 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
         }
         S::add(&vals[h], S::mul(a, b));
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
     team.sync();
     // bitonic sort of (key, value) over H slots, ascending; EMPTY sorts last
     for (long long kk = 2; kk <= H; kk <<= 1) {
@@ -528,13 +550,16 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
     unsigned *setw = mbits + words32(T);
     const int n = c.n;
     const int ntiles = (n + T - 1) / T;
-    // cursor of stored entry t of A (product-local index) is cursors[abase + t]
+    // Column tiles come from the product's tile index when it has one (exact
+    // range of every (row of B, tile)); otherwise from per-entry cursors:
+    // cursor of stored entry t of A (product-local index) is cursors[abase + t].
+    const bool use_index = P.tpos != nullptr;
     int4 *cur = L.cursors + P.abase;
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     __shared__ int s_out;    // entries written so far in this row
     __shared__ int s_mpos;   // mask cursor
     if (threadIdx.x == 0) { s_out = 0; s_mpos = c.m0; }
-    if (ntiles > 1) {
+    if (ntiles > 1 && !use_index) {
         for (int t = c.a0 + team.tid(); t < c.a1; t += team.size()) {
             const int k = __ldg(P.a_ci + t);
             const int s = __ldg(P.b_rp + k), e = __ldg(P.b_rp + k + 1);
@@ -577,7 +602,11 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
         };
         if (ntiles == 1) {
             auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
-            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, P.b_rp, P.b_ci, P.b_v, flat_mode(c), f);
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), f);
+        } else if (use_index) {
+            auto f = [&](int, in_t a, int j, in_t b) { ins(j - c0, a, b); };
+            const TileSeg seg{P.tpos, P.tstride, tile};
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, ENUM_AUTO, f);
         } else {
             // Contiguous windows of 32 entries per warp (coalesced cursor
             // loads).  Pass 1: every lane advances its own entry's segment

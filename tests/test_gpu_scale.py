@@ -132,3 +132,28 @@ def test_batched_full_size_sampled_products(handle):
         q = ps[pidx]
         ref = O.masked_spgemm(q["M"], q["A"], q["B"], "plus_times_f32")
         assert_parity(outs[pidx].trimmed(), ref, "plus_times_f32", ctx=f"product {pidx}")
+
+
+@pytest.mark.parametrize("tile_index", [0, 1])
+def test_tiled_rows_index_and_cursor_paths(handle, tile_index):
+    """Rows wider than one shared-memory tile, walked through the per-row tile
+    index of B (default) and through per-entry cursors (fallback)."""
+    handle.set_option(_lib.OPT_TILE_INDEX, tile_index)
+    try:
+        p = synth.bfs_step(scale=16, ef=16, nsrc=256, seed=29)        # 65536 columns: 3 int64 tiles
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64", complement=True, method=O.ESC)
+        handle.force("msa")
+        d = to_dev(p, "plus_times_i64")
+        res = _lib.msgemm_run(handle, d["M"], d["A"], d["B"], "plus_times_i64", complement=True).trimmed()
+        handle.sync_status()
+        assert_parity(res, ref, "plus_times_i64", ctx=f"bfs tile_index={tile_index}")
+        for sr, gen in (("plus_times_f32", "f32"), ("plus_pair_i64", "pair")):
+            q = synth.random_problem(900, 400, 120000, 20.0, 500.0, 60.0, 55, gen)
+            ref = O.masked_spgemm(q["M"], q["A"], q["B"], sr)
+            dq = to_dev(q, sr)
+            res = _lib.msgemm_run(handle, dq["M"], dq["A"], dq["B"], sr).trimmed()
+            handle.sync_status()
+            assert_parity(res, ref, sr, ctx=f"{sr} tile_index={tile_index}")
+    finally:
+        handle.force("auto")
+        handle.set_option(_lib.OPT_TILE_INDEX, 1)
