@@ -435,7 +435,9 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
             for (int p = 0; p < P; ++p) {
                 if (!nts[p]) continue;
                 int *tp = ct.take<int>((size_t)in[p].B->nrows * (nts[p] + 1));
-                CK(launch_tile_bounds(in[p].B->rowptr, in[p].B->colidx, in[p].B->nrows, T, nts[p], tp, st, h->nsm));
+                // skipped on the device unless binning put rows in a tiled kind
+                CK(launch_tile_bounds(in[p].B->rowptr, in[p].B->colidx, in[p].B->nrows, T, nts[p], tp,
+                                      ra.kind_count, st, h->nsm));
                 dp[p].tpos = tp;
                 dp[p].tstride = nts[p] + 1;
             }

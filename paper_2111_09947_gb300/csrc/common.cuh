@@ -21,7 +21,7 @@ constexpr unsigned FULL = 0xffffffffu;
 enum Kind : int {
     K_EMPTY = 0,   // no output possible (no product, or nothing allowed)
     K_MSA_W,       // Sec. 5.2 MSA, dense states + values over all n columns
-    K_MSA_T,       // Sec. 5.2 MSA over column tiles, per-k cursors
+    K_MSA_T,       // Sec. 5.2 MSA over column tiles (tile index of B, or cursors)
     K_HASH_W,      // Sec. 5.3 hash keyed by mask columns (load factor <= 0.5)
     K_HASH_B,
     K_MCA_W,       // Sec. 5.4 MCA: rank of j in the mask row by binary search

@@ -76,8 +76,8 @@ cudaError_t launch_bt_counts_multi(const BtDesc *d, int Q, long long total_nnz, 
                                    cudaStream_t, int nsm);
 cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, int vbytes, int *cursor, int *tci,
                                  void *tv, const int *gate, cudaStream_t, int nsm);
-cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, cudaStream_t,
-                               int nsm);
+cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, const int *gate,
+                               cudaStream_t, int nsm);
 cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t, int nsm);
 
 constexpr int CTILE = 1024;        // rows per compaction tile

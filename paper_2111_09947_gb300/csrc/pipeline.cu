@@ -701,7 +701,8 @@ namespace msg {
 // warp per row; every slot is first set to the row end, then each entry that
 // starts a tile writes the slots of the tiles it opens (rows are sorted).
 __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt,
-                                                     int *tpos) {
+                                                     int *tpos, const int *gate) {
+    if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0) return;   // gate = per-kind row counts
     const int lane = threadIdx.x & 31;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -719,10 +720,10 @@ __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *c
     }
 }
 
-cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, cudaStream_t st,
-                               int nsm) {
+cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, const int *gate,
+                               cudaStream_t st, int nsm) {
     if (nrows == 0) return cudaSuccess;
-    k_tile_bounds<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, T, nt, tpos); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_tile_bounds<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, T, nt, tpos, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 

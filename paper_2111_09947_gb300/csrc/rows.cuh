@@ -62,22 +62,21 @@ struct TileSeg {
     }
 };
 
-enum : int { ENUM_STRIDED = 0, ENUM_FLAT = 1, ENUM_AUTO = 2 };
-
 // Calls f(t, a_t, col, val) for every (outer position t in [o0, o1), inner
 // entry q of the range seg gives for row oci[t]) pair, with col = ici[q],
 // val = iv[q].  Outer entries are dealt to the team's warps round-robin
 // (entry x goes to warp x mod nw), so every warp of a CTA-row gets work even
-// for short outer lists; a warp's window holds its next 32 entries.
-// Strided mode: the warp walks the window's inner ranges one by one, lanes
-// striding each (4 loads in flight per lane).  Flat mode (short ranges): the
-// products of a window are numbered 0..total-1 and each lane finds its range
-// by a binary search over the window's inclusive prefix of lengths.  Auto
-// picks per window: flat when the ranges average fewer than 16 entries.
+// for short outer lists; a warp's window holds its next 32 entries.  Within a
+// window, ranges of LONG_SEG or more entries are walked one at a time by the
+// whole warp (lanes stride the range, 4 loads in flight per lane); all
+// shorter ranges are enumerated together: their products are numbered and
+// each lane finds its range by a binary search over the window's prefix of
+// lengths, so lanes stay busy whatever the mix of lengths.
+constexpr int LONG_SEG = 64;
+
 template <int SR, bool CTA, bool OUTV, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
-                                              const Seg &seg, const int *__restrict__ ici, const void *iv,
-                                              int mode, F &f) {
+                                              const Seg &seg, const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
     Team<CTA> team;
     const int lane = lane_id();
@@ -92,50 +91,49 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             if constexpr (OUTV) av = load_val<SR>(ov, t);
         }
         const int tbase = o0 + wq + nw * b0;   // outer position of lane 0's entry
-        const int len = max(0, e - s);   // an unsorted row can give e < s in a tile index
-        const int incl = warp_incl_scan(len);
-        const int total = __shfl_sync(FULL, incl, 31);
-        if (total == 0) continue;
-        bool flat = mode == ENUM_FLAT;
-        if (mode == ENUM_AUTO) flat = total < 16 * __popc(__ballot_sync(FULL, len > 0));
-        if (!flat) {
-            const int nu = min(32, (cnt - wq - nw * b0 + nw - 1) / nw);
-            for (int u = 0; u < nu; ++u) {
-                const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
-                const in_t au = shfl_val<SR>(av, u);
-                for (int q0 = su; q0 < eu; q0 += 128) {
-                    int col[4];
-                    in_t bv[4];
+        const int len = max(0, e - s);         // an unsorted row can give e < s in a tile index
+        // long ranges: cooperative walk
+        unsigned lmask = __ballot_sync(FULL, len >= LONG_SEG);
+        while (lmask) {
+            const int u = __ffs(lmask) - 1;
+            lmask &= lmask - 1;
+            const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
+            const in_t au = shfl_val<SR>(av, u);
+            for (int q0 = su; q0 < eu; q0 += 128) {
+                int col[4];
+                in_t bv[4];
 #pragma unroll
-                    for (int x = 0; x < 4; ++x) {
-                        const int q = q0 + x * 32 + lane;
-                        col[x] = -1;
-                        if (q < eu) {
-                            col[x] = __ldg(ici + q);
-                            bv[x] = load_val<SR>(iv, q);
-                        }
+                for (int x = 0; x < 4; ++x) {
+                    const int q = q0 + x * 32 + lane;
+                    col[x] = -1;
+                    if (q < eu) {
+                        col[x] = __ldg(ici + q);
+                        bv[x] = load_val<SR>(iv, q);
                     }
-#pragma unroll
-                    for (int x = 0; x < 4; ++x)
-                        if (col[x] >= 0) f(tbase + nw * u, au, col[x], bv[x]);
                 }
+#pragma unroll
+                for (int x = 0; x < 4; ++x)
+                    if (col[x] >= 0) f(tbase + nw * u, au, col[x], bv[x]);
             }
-        } else {
-            const int excl = incl - len;
-            for (int base = 0; base < total; base += 32) {
-                const int p = base + lane;
-                int k = 0;
+        }
+        // short ranges: load-balanced flat enumeration
+        const int sl = len < LONG_SEG ? len : 0;
+        const int incl = warp_incl_scan(sl);
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - sl;
+        for (int base = 0; base < total; base += 32) {
+            const int p = base + lane;
+            int k = 0;
 #pragma unroll
-                for (int st = 16; st > 0; st >>= 1) {
-                    const int cc = __shfl_sync(FULL, incl, k + st - 1);
-                    if (cc <= p) k += st;
-                }
-                const int sk = __shfl_sync(FULL, s, k & 31), xk = __shfl_sync(FULL, excl, k & 31);
-                const in_t ak = shfl_val<SR>(av, k & 31);
-                if (p < total) {
-                    const int q = sk + p - xk;
-                    f(tbase + nw * k, ak, __ldg(ici + q), load_val<SR>(iv, q));
-                }
+            for (int st = 16; st > 0; st >>= 1) {
+                const int cc = __shfl_sync(FULL, incl, k + st - 1);
+                if (cc <= p) k += st;
+            }
+            const int sk = __shfl_sync(FULL, s, k & 31), xk = __shfl_sync(FULL, excl, k & 31);
+            const in_t ak = shfl_val<SR>(av, k & 31);
+            if (p < total) {
+                const int q = sk + p - xk;
+                f(tbase + nw * k, ak, __ldg(ici + q), load_val<SR>(iv, q));
             }
         }
     }
@@ -225,10 +223,7 @@ __device__ __forceinline__ RowCtx row_ctx(const DevProd &P, long long r, const R
     return c;
 }
 
-__device__ __forceinline__ int enum_mode(const RowCtx &c) {
-    // average inner row shorter than 12: load-balanced flat enumeration
-    return c.flops < 12LL * (long long)(c.a1 - c.a0) ? ENUM_FLAT : ENUM_STRIDED;
-}
+
 
 // --------------------------------------------------------------- HASH rows
 // Sec. 5.3: open addressing, linear probing, no resizing, keyed by the mask's
@@ -275,7 +270,7 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
             h = (h + 1) & hmask;
         }
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     team.sync();
     gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -312,7 +307,7 @@ __device__ __forceinline__ void row_mca(const DevProd &P, const RowCtx &c, const
             if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, lo);
         }
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     team.sync();
     gather_ranked<SR, CTA>(mcol, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -357,7 +352,7 @@ __device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const
             if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
         }
     };
-    enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, RowSeg{P.bt_rp}, P.bt_ci, P.bt_v, ENUM_AUTO, ins);
+    enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, RowSeg{P.bt_rp}, P.bt_ci, P.bt_v, ins);
     team.sync();
     gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
     team.sync();
@@ -389,7 +384,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
             if constexpr (SrSizes<SR>::setbits) set_bit_once(setw, j);
         }
     };
-    enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
+    enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     __syncwarp();
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     int base = 0;
@@ -477,7 +472,7 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
         }
         S::add(&vals[h], S::mul(a, b));
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), ins);
+    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     team.sync();
     // bitonic sort of (key, value) over H slots, ascending; EMPTY sorts last
     for (long long kk = 2; kk <= H; kk <<= 1) {
@@ -602,11 +597,11 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
         };
         if (ntiles == 1) {
             auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
-            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, enum_mode(c), f);
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, f);
         } else if (use_index) {
             auto f = [&](int, in_t a, int j, in_t b) { ins(j - c0, a, b); };
             const TileSeg seg{P.tpos, P.tstride, tile};
-            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, ENUM_AUTO, f);
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, f);
         } else {
             // Contiguous windows of 32 entries per warp (coalesced cursor
             // loads).  Pass 1: every lane advances its own entry's segment
