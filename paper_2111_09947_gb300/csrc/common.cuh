@@ -247,10 +247,21 @@ template <bool CTA> struct Team {
     __device__ __forceinline__ int size() const { return CTA ? (int)blockDim.x : 32; }
     __device__ __forceinline__ int warp() const { return CTA ? (int)(threadIdx.x >> 5) : 0; }
     __device__ __forceinline__ int nwarps() const { return CTA ? (int)(blockDim.x >> 5) : 1; }
+    // Barrier that also publishes the team's shared-memory atomics (hash
+    // keys, bitmaps, accumulators) to the plain loads that follow it.  An
+    // explicit block-scope fence before the barrier is required: without it a
+    // lookup after the barrier was seen to miss a key another warp had just
+    // inserted with atomicCAS.
     __device__ __forceinline__ void sync() const {
+        __threadfence_block();
         if (CTA) __syncthreads(); else __syncwarp();
     }
 };
+
+__device__ __forceinline__ void cta_sync() {
+    __threadfence_block();
+    __syncthreads();
+}
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 __device__ __forceinline__ unsigned lanemask_lt() { return (1u << lane_id()) - 1u; }

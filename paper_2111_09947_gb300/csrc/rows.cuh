@@ -72,7 +72,10 @@ struct TileSeg {
 // shorter ranges are enumerated together: their products are numbered and
 // each lane finds its range by a binary search over the window's prefix of
 // lengths, so lanes stay busy whatever the mix of lengths.
-constexpr int LONG_SEG = 64;
+#ifndef MSG_LONG_SEG
+#define MSG_LONG_SEG 64
+#endif
+constexpr int LONG_SEG = MSG_LONG_SEG;
 
 template <int SR, bool CTA, bool OUTV, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
@@ -377,6 +380,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
         const int j = __ldg(P.m_ci + q);
         atomicOr(&allowed[j >> 5], 1u << (j & 31));
     }
+    __threadfence_block();
     __syncwarp();
     auto ins = [&](int, in_t a, int j, in_t b) {
         if (test_bit(allowed, j)) {
@@ -385,6 +389,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
         }
     };
     enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+    __threadfence_block();
     __syncwarp();
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     int base = 0;
@@ -415,6 +420,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
         base += __popc(bal);
     }
     if (lane == 0) L.ra.cnt[c.r] = base;
+    __threadfence_block();
     __syncwarp();
     for (int q = c.m0 + lane; q < c.m1; q += 32) {
         const int j = __ldg(P.m_ci + q);
@@ -422,6 +428,7 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
         allowed[j >> 5] = 0;
         setw[j >> 5] = 0;
     }
+    __threadfence_block();
     __syncwarp();
 }
 
@@ -561,7 +568,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             cur[t] = make_int4(s, e, s < e ? __ldg(P.b_ci + s) : INT_MAX, 0);
         }
     }
-    __syncthreads();
+    cta_sync();
     for (int tile = 0; tile < ntiles; ++tile) {
         const int c0 = tile * T, c1 = min(n, c0 + T);
         const int mq0 = s_mpos;
@@ -583,7 +590,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             if ((unsigned)jj < (unsigned)T) atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
             else atomicOr(L.ra.err, ERR_INTERNAL);
         }
-        __syncthreads();
+        cta_sync();
         auto ins = [&](int jj, in_t a, in_t b) {
             if ((unsigned)jj >= (unsigned)T) {
                 atomicOr(L.ra.err, ERR_INTERNAL);
@@ -676,7 +683,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                 if (t < c.a1 && cu.x != x0) cur[t] = cu;
             }
         }
-        __syncthreads();
+        cta_sync();
         // gather this tile in ascending column order
         int outbase = s_out;
         if (!COMP) {
@@ -716,7 +723,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                 }
                 base += __popc(bal);
             }
-            __syncthreads();
+            cta_sync();
             for (int q = s0 + lane; q < s1; q += 32) {
                 const int jj = __ldg(P.m_ci + q) - c0;
                 if ((unsigned)jj >= (unsigned)T) continue;
@@ -748,17 +755,17 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                 }
                 setw[w] = 0;
             }
-            __syncthreads();
+            cta_sync();
             for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
                 const int jj = __ldg(P.m_ci + q) - c0;
                 if ((unsigned)jj < (unsigned)T) mbits[jj >> 5] = 0;
             }
             if (threadIdx.x == 0) { s_out = outbase + total; s_mpos = mq1; }
         }
-        __syncthreads();
+        cta_sync();
     }
     if (threadIdx.x == 0) L.ra.cnt[c.r] = s_out;
-    __syncthreads();
+    cta_sync();
 }
 
 // ------------------------------------------------------------------ kernels
@@ -816,9 +823,9 @@ __global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet 
         for (int x = threadIdx.x; x < L.slab / 4; x += blockDim.x) w[x] = 0;
     }
     for (;;) {
-        __syncthreads();
+        cta_sync();
         if (threadIdx.x == 0) s_row = atomicAdd(&L.ra.kind_next[KIND], 1);
-        __syncthreads();
+        cta_sync();
         const int x = s_row;
         if (x >= count) break;
         const long long r = L.ra.perm[off + x];
