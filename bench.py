@@ -515,12 +515,8 @@ def run_ours(args):
     total_ms = sum(meas["times"])
     flops = 2.0 * wl.kept
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        f = torch.tensor([flops], dtype=torch.float64, device=dev)
-        dist.all_reduce(f, op=dist.ReduceOp.SUM)
-        flops = float(f.item())
+        from paper_2111_09947_gb300.shard import reduce_timing
+        total_ms, flops = reduce_timing(total_ms, flops, device=dev)
     ms_per_step = total_ms / args.steps
     value = flops * args.steps / (total_ms * 1e-3) / 1e9
     summary = form_summary(wl, meas)

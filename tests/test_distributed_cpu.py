@@ -1,0 +1,68 @@
+"""Multi-rank host logic on CPU (gloo, world size 2): the timing reduction the
+benchmark uses under torchrun, the global row offsets that stitch row blocks
+into one CSR, and the partition helpers."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from paper_2111_09947_gb300 import shard
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms, work = shard.reduce_timing(10.0 + 5 * rank, 100.0 * (rank + 1))
+        offs = shard.gather_row_offsets(7 + 3 * rank)
+        q.put((rank, ms, work, offs))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_reduction_and_offsets():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, work, offs in res:
+        assert ms == 15.0 and work == 300.0
+        assert offs == [0, 7]
+
+
+def test_partition_rows_balances_work():
+    rng = np.random.default_rng(0)
+    work = rng.pareto(1.5, 10000) * 100
+    b = shard.partition_rows(work, 4)
+    assert b[0] == 0 and b[-1] == len(work) and np.all(np.diff(b) >= 0)
+    sums = [work[b[i]:b[i + 1]].sum() for i in range(4)]
+    assert max(sums) <= work.sum() / 4 + work.max() + 1e-9
+    assert list(shard.partition_rows(np.zeros(10), 3)) == [0, 3, 7, 10]
+    with pytest.raises(ValueError):
+        shard.partition_rows(work, 0)
+
+
+def test_partition_products_covers_all():
+    costs = [5, 1, 1, 1, 9, 3, 2]
+    parts = shard.partition_products(costs, 3)
+    assert sorted(sum(parts, [])) == list(range(len(costs)))
+    loads = [sum(costs[p] for p in part) for part in parts]
+    assert max(loads) - min(loads) <= max(costs)
