@@ -184,6 +184,27 @@ msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr
 msgemm_status msgemm_transpose(msgemm_handle *handle, const msgemm_csr *A, int value_bytes,
                                int sorted, msgemm_csr_out *At);
 
+/* Transpose that allocates nothing.  The paper has no counterpart to this
+ * entry point: it serves callers that cannot allocate device memory where
+ * they need a transpose -- runtimes that hand out all device memory from
+ * their own fixed pools and forbid any other allocation, hosts with no
+ * device allocator to pass in, and latency-critical paths where cudaMalloc
+ * (which may synchronise the device) is not acceptable.
+ * It needs no handle.  Result as msgemm_transpose(A, value_bytes, sorted),
+ * written into caller-owned device arrays: At_rowptr (ncols(A) + 1 entries),
+ * At_colidx and At_values (nnz(A) entries; At_values unused when value_bytes
+ * is 0).  Asynchronous on `stream` (a cudaStream_t; NULL = legacy default).
+ * Its scratch (per-column cursors, scan tile sums) is one file-scope device
+ * array of about 4 MiB that every GPU loading the library keeps until the
+ * process exits; it bounds ncols(A) at 1,048,576 -- larger returns
+ * MSGEMM_ERR_OVERFLOW before any work.  The first call on a device looks up
+ * the array's device address with that device current; make that first call
+ * before any stream capture.  Every call shares the array, which keeps the
+ * previous call's contents (each call clears what it needs), so calls that
+ * overlap on the GPU race: serialise them (one stream, or events). */
+msgemm_status msgemm_transpose_noalloc(const msgemm_csr *A, int value_bytes, int sorted, int32_t *At_rowptr,
+                                       int32_t *At_colidx, void *At_values, void *stream);
+
 /* *d_sum (device, 8 bytes) = sum of C's values: int64 wrapping for the int64
  * semirings (the triangle count of Sec. 8.2 for C = L .* (L L) on plus-pair),
  * fp64 accumulation rounded into a double for plus-times fp32. */

@@ -31,7 +31,7 @@ EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_ru
            "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
            "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
            "msgemm_profile_count", "msgemm_profile_entry", "msgemm_last_row_kinds", "msgemm_kernel_launches",
-           "msgemm_destroy"]
+           "msgemm_transpose_noalloc", "msgemm_destroy"]
 
 
 class MsgemmError(RuntimeError):
@@ -93,6 +93,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "msgemm_profile_entry": (i32, [vp, i32, C.c_char_p, sz, P(C.c_float)]),
         "msgemm_last_row_kinds": (i32, [vp, vp, i64]),
         "msgemm_kernel_launches": (i64, []),
+        "msgemm_transpose_noalloc": (i32, [P(Csr), i32, i32, vp, vp, vp, vp]),
         "msgemm_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
@@ -325,3 +326,22 @@ def msgemm_transpose(h: Handle, A: DeviceCsr, value_bytes: int, sorted_rows: boo
     v = h.adopt(out.values, dt, out.capacity) if value_bytes else None
     nz = h.adopt(out.d_nnz, torch.int64, 1)
     return Result(out.nrows, out.ncols, rp, ci, v, nz)
+
+
+def msgemm_transpose_noalloc(A: DeviceCsr, value_bytes: int, sorted_rows: bool = False):
+    """Transpose through the entry point that allocates nothing: the output
+    arrays are allocated here (by the caller), the library only fills them.
+    Returns (rowptr, colidx, values-or-None)."""
+    lib = load()
+    dev = A.rowptr.device
+    rp = torch.empty(A.ncols + 1, dtype=torch.int32, device=dev)
+    ci = torch.empty(max(A.nnz, 1), dtype=torch.int32, device=dev)
+    dt = {0: None, 4: torch.float32, 8: torch.int64}[value_bytes]
+    v = torch.empty(max(A.nnz, 1), dtype=dt, device=dev) if dt is not None else None
+    a = A.abi()
+    st = lib.msgemm_transpose_noalloc(C.byref(a), int(value_bytes), int(bool(sorted_rows)), rp.data_ptr(),
+                                      ci.data_ptr(), v.data_ptr() if v is not None else None,
+                                      torch.cuda.current_stream(dev).cuda_stream)
+    if st != 0:
+        raise MsgemmError(st, "msgemm_transpose_noalloc")
+    return rp, ci[:A.nnz], (v[:A.nnz] if v is not None else None)
