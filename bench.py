@@ -406,6 +406,18 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
         run.per_product_step()
         torch.cuda.synchronize()
         out["per_product_ms"] = statistics.median(timed_steps(torch, run.per_product_step, 3, flush, stream))
+    if wl.name in ("batched", "er"):
+        # the same products replayed from a captured CUDA graph (plain masks)
+        h.set_option(_lib.OPT_PROFILE, 0)
+        Ms, As, Bs = [p[0] for p in run.prods], [p[1] for p in run.prods], [p[2] for p in run.prods]
+
+        def graph_step():
+            return _lib.msgemm_run_batched(h, Ms, As, Bs, wl.semiring, use_graph=True)
+        for _ in range(3):
+            graph_step()
+        torch.cuda.synchronize()
+        out["graph_ms"] = statistics.median(timed_steps(torch, graph_step, 5, flush, stream))
+        h.set_option(_lib.OPT_PROFILE, 1)
     if wl.name == "autograd":
         M, A, B, _ = run.prods[0]
         fwd = lambda: _lib.msgemm_run(h, M, A, B, wl.semiring)  # noqa: E731
@@ -478,11 +490,13 @@ def form_summary(wl, meas):
         d["push_products"] = push_products(A, B)
     if meas["per_phase"]:
         d["phase_ms"] = {n: round(statistics.mean(v), 4) for n, v in meas["per_phase"].items()}
-    for k in ("per_product_ms", "fwd_ms", "bwd_ms"):
+    for k in ("per_product_ms", "graph_ms", "fwd_ms", "bwd_ms"):
         if k in meas:
             d[k] = round(meas[k], 3)
     if "per_product_ms" in meas:
         d["batched_speedup"] = round(meas["per_product_ms"] / ms, 2)
+        if "graph_ms" in meas:
+            d["graph_vs_per_product"] = round(meas["per_product_ms"] / meas["graph_ms"], 2)
     return d
 
 
@@ -542,7 +556,7 @@ def run_ours(args):
     }
     if "push_products" in summary:
         line["push_gflops"] = round(2 * summary["push_products"] / (ms_per_step * 1e-3) / 1e9, 2)
-    for k in ("per_product_ms", "batched_speedup", "fwd_ms", "bwd_ms"):
+    for k in ("per_product_ms", "batched_speedup", "graph_ms", "graph_vs_per_product", "fwd_ms", "bwd_ms"):
         if k in summary:
             line[k] = summary[k]
 

@@ -158,21 +158,32 @@ msgemm_status msgemm_backward(msgemm_handle *handle, const msgemm_csr *A, const 
                               float *dA_vals, float *dB_vals);
 
 /* nprod independent products C[p] = M[p] .* (A[p] B[p]) (or complemented per
- * complement[p], which may be NULL for all-plain), one semiring.  All binning,
- * accumulation and compaction for all products run in one pipeline whose
- * accumulation phase is ONE persistent kernel that pulls (product, row) work
- * items from a device queue.  With use_graph != 0 the pipeline is captured once
- * into a CUDA graph and replayed when called again with identical arguments
- * (same pointers and sizes).  Each C[p] is allocated as in msgemm_run; a
- * complemented product synchronises the host as msgemm_run does. */
+ * complement[p], which may be NULL for all-plain), one semiring.  Binning,
+ * accumulation and compaction for all products run as one pipeline: rows of
+ * every product are binned together, and each accumulator kind is ONE
+ * persistent kernel over the rows of that kind in all products (grid =
+ * resident CTAs x SMs), so the launch count does not grow with nprod.
+ * With use_graph != 0 and every mask plain (and neither validation nor
+ * profiling on), the device part of the pipeline is captured into a CUDA
+ * graph on first use and replayed while the arguments stay the same (the
+ * same input pointers and sizes, the same handle options and workspace);
+ * outputs may differ between replays: they are passed through a device table
+ * uploaded before each replay.  Anything else runs eagerly.  Each C[p] is
+ * allocated as in msgemm_run; a complemented product synchronises the host as
+ * msgemm_run does. */
 msgemm_status msgemm_run_batched(msgemm_handle *handle, int nprod, const msgemm_csr *M,
                                  const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                                  msgemm_semiring semiring, msgemm_csr_out *C, int use_graph);
 
-/* Times each accumulator family on the given batch (synchronises), keeps the
- * fastest per row class in the handle's policy, and, when cache_path is not
- * NULL, writes the table as JSON keyed by device name and semiring (and
- * reads it back instead of timing when the file already holds that key). */
+/* Tunes the handle's binning policy on the given batch by timing it
+ * (synchronises; every candidate computes the same result): for each row
+ * class carrying work (4 push-flop bands x 4 mask-row bands), the
+ * accumulator family tried first (MSA, hash or MCA), then the flop bound
+ * between warp and CTA rows, then the pull/push ratio above which rows take
+ * the pull kernel.  With cache_path != NULL the tuned policy is stored there
+ * as JSON keyed by device name and semiring, and read back instead of
+ * timing when the file already holds that key (a malformed entry is
+ * ignored).  nprod == 0 only loads the cache. */
 msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr *M,
                               const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                               msgemm_semiring semiring, const char *cache_path);

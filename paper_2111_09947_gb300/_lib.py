@@ -304,6 +304,22 @@ def msgemm_run_batched(h: Handle, Ms, As, Bs, semiring="plus_times_f32", complem
     return [h.result(outs[p], out_dtype(sr)) for p in range(n)]
 
 
+def msgemm_autotune(h: Handle, Ms, As, Bs, semiring="plus_times_f32", complement=None, cache_path=None):
+    """Tune the handle's binning policy on this batch (or load it from the
+    JSON cache at cache_path when it holds this device and semiring)."""
+    sr = _sr(semiring)
+    h.bind_stream()
+    n = len(Ms)
+    marr = (Csr * max(n, 1))(*[x.abi() for x in Ms])
+    aarr = (Csr * max(n, 1))(*[x.abi() for x in As])
+    barr = (Csr * max(n, 1))(*[x.abi() for x in Bs])
+    comp = None
+    if complement is not None:
+        comp = (C.c_int * max(n, 1))(*[int(bool(c)) for c in complement])
+    path = None if cache_path is None else str(cache_path).encode()
+    h.check(h.lib.msgemm_autotune(h.h, n, marr, comp, aarr, barr, sr, path))
+
+
 def msgemm_reduce_sum(h: Handle, res: Result, semiring) -> torch.Tensor:
     """Device scalar: int64 (wrapping) sum for the int64 semirings, float64 for fp32."""
     sr = _sr(semiring)

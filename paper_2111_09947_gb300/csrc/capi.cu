@@ -5,7 +5,9 @@
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -50,6 +52,11 @@ struct msgemm_handle {
     int nprof = 0;
     // host staging
     std::vector<DevProd> hprods;
+    // CUDA graph of the last graph-mode plan (msgemm_run_batched, use_graph)
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    std::string gkey;
+    long long gkernels = 0, gcaptures = 0;
 };
 
 namespace {
@@ -219,15 +226,44 @@ msgemm_status validate_inputs(msgemm_handle *h, const std::vector<const msgemm_c
     return MSGEMM_OK;
 }
 
-// The whole one-phase pipeline for a set of products (Sec. 4-6).
-msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
-                           bool validate) {
+// Host view of one pipeline run: workspace carved, tables built and every
+// pointer the device sequence needs fixed before its first kernel.  With
+// plain masks nothing in the device sequence depends on device results, so
+// it can be captured once into a CUDA graph and replayed.
+struct Plan {
+    int P = 0;
+    bool aligned = false, any_comp = false;
+    msgemm_semiring sr{};
+    Policy pol{};
+    ProdSet ps{};
+    long long R = 0, nnzA = 0, tmpn = 0, ntiles = 0, cap = 0;
+    long long *room = nullptr, *tile_sums = nullptr, *tile_offs = nullptr, *chunk_start = nullptr,
+              *prod_tot = nullptr, *room_tiles = nullptr;
+    DevProd *dtab = nullptr;
+    char *zero_begin = nullptr;
+    size_t zero_bytes = 0;
+    // B^T of the products whose rows may take the pull kernel
+    std::vector<BtDesc> bd;
+    long long bt_counts = 0, bt_nnz = 0, bt_rows = 0;
+    int *bt_rp_all = nullptr, *bt_cur = nullptr, *bt_ci = nullptr;
+    void *bt_v = nullptr;
+    BtDesc *bt_tab = nullptr;
+    long long *bt_tb = nullptr;
+    // tile index of B for column-tiled products (nts[p] tiles, 0 = untiled)
+    std::vector<int> nts;
+    std::vector<int *> tpos;
+    RowLaunch L{};
+    std::vector<int> kinds;
+};
+
+msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
+                           bool by_value, Plan &pl) {
     const int P = (int)in.size();
-    const bool aligned = P > 0 && in[0].aligned_out != nullptr;
-    cudaStream_t st = h->stream;
-    long long R = 0, nnzA = 0, tmpn = 0, ntiles = 0;
+    pl.P = P;
+    pl.sr = sr;
+    pl.aligned = P > 0 && in[0].aligned_out != nullptr;
     int max_n = 0;
-    bool any_comp = false, any_tiled = false;
+    bool any_tiled = false;
     const Policy pol0 = make_policy(h, sr, 0);
     std::vector<DevProd> &dp = h->hprods;
     dp.assign(P, DevProd{});
@@ -241,72 +277,66 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         d.m = x.M->nrows; d.n = x.M->ncols; d.k = x.A->ncols;
         d.complement = x.comp;
         d.a_sorted = x.a_sorted;
-        d.row0 = R;
-        d.tile0 = ntiles;
-        d.abase = nnzA;
-        d.tmp0 = tmpn;
-        R += d.m;
-        nnzA += x.A->nnz;
-        ntiles += (d.m + CTILE - 1) / CTILE;
-        if (!x.comp) tmpn += x.M->nnz;
-        any_comp |= x.comp != 0;
+        d.row0 = pl.R;
+        d.tile0 = pl.ntiles;
+        d.abase = pl.nnzA;
+        d.tmp0 = pl.tmpn;
+        pl.R += d.m;
+        pl.nnzA += x.A->nnz;
+        pl.ntiles += (d.m + CTILE - 1) / CTILE;
+        if (!x.comp) pl.tmpn += x.M->nnz;
+        pl.any_comp |= x.comp != 0;
         max_n = std::max(max_n, d.n);
         if (d.n > pol0.tileT[x.comp ? 1 : 0]) any_tiled = true;
         if (x.C) {
             d.c_rp = x.C->rowptr; d.c_ci = x.C->colidx; d.c_v = x.C->values; d.c_nnz = reinterpret_cast<long long *>(x.C->d_nnz);
+            if (!x.comp) pl.cap += x.C->capacity;
         }
     }
+    const long long R = pl.R, ntiles = pl.ntiles;
     if (R >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "total rows >= 2^31");
-    const Policy pol = make_policy(h, sr, max_n);
+    pl.pol = make_policy(h, sr, max_n);
 
-    // ---- workspace
+    // ---- per-row workspace
     const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 2 + carve_size<unsigned char>(R) +
                               carve_size<long long>(ntiles) * 3 + 256 + carve_size<long long>(2 * (size_t)P) +
                               carve_size<long long>((R + STILE - 1) / STILE + 2) + carve_size<DevProd>(P) + 4096;
     CKS(grow(h, h->rows, rows_bytes));
     Carver cv(h->rows.p);
-    RowArrays ra{};
+    RowArrays &ra = pl.L.ra;
     ra.R = R;
     ra.flops = cv.take<long long>(R);
     ra.tmpoff = cv.take<long long>(R);
-    long long *room = cv.take<long long>(R);
+    pl.room = cv.take<long long>(R);
     ra.cnt = cv.take<int>(R);
     ra.perm = cv.take<int>(R);
     ra.kind = cv.take<unsigned char>(R);
-    long long *tile_sums = cv.take<long long>(ntiles);
-    long long *tile_offs = cv.take<long long>(ntiles);
-    long long *chunk_start = cv.take<long long>(ntiles + 1);
-    long long *prod_tot = cv.take<long long>(2 * (size_t)P);
-    long long *room_tiles = cv.take<long long>((R + STILE - 1) / STILE + 2);
-    DevProd *dtab = cv.take<DevProd>(P);
+    pl.tile_sums = cv.take<long long>(ntiles);
+    pl.tile_offs = cv.take<long long>(ntiles);
+    pl.chunk_start = cv.take<long long>(ntiles + 1);
+    pl.prod_tot = cv.take<long long>(2 * (size_t)P);
+    pl.room_tiles = cv.take<long long>((R + STILE - 1) / STILE + 2);
+    pl.dtab = cv.take<DevProd>(P);
     // small counters: zeroed per run (err is persistent, kept first)
     Carver cs(h->small.p);
-    unsigned *err = cs.take<unsigned>(1);
-    ra.err = err;
-    char *zero_begin = cs.base + ((cs.off + 255) & ~size_t(255));
+    ra.err = cs.take<unsigned>(1);
+    pl.zero_begin = cs.base + ((cs.off + 255) & ~size_t(255));
     ra.kind_count = cs.take<int>(NKIND);
     ra.kind_fill = cs.take<int>(NKIND);
     ra.kind_next = cs.take<int>(NKIND);
     ra.kind_off = cs.take<int>(NKIND + 1);
     ra.any_dot = cs.take<int>(1);
     ra.bound_total = cs.take<long long>(1);
-    const size_t zero_bytes = (size_t)(cs.base + cs.off - zero_begin);
+    pl.zero_bytes = (size_t)(cs.base + cs.off - pl.zero_begin);
     h->last_kind_count = ra.kind_count;
-    CK(cudaMemsetAsync(zero_begin, 0, zero_bytes, st));
+    h->last_kind = ra.kind;
+    h->last_R = R;
 
-    // ---- optional input validation: synchronises, and rejects invalid input
-    // before any kernel that would index through it runs
-    if (validate) {
-        PScope ph(h, "validate");
-        std::vector<const msgemm_csr *> mats;
-        for (int p = 0; p < P; ++p) mats.insert(mats.end(), {in[p].M, in[p].A, in[p].B});
-        CKS(validate_inputs(h, mats));
-    }
-
-    // ---- B^T for the pull kernel: row pointers now, entries if a row picks it
-    // Building B^T costs a pass over B; it pays only where the pull work
-    // (mask entries x average column length of B) is well below the push work
-    // (entries of A x average row length of B), or when DOT is forced.
+    // ---- B^T for the pull kernel: row pointers in the front of the sequence,
+    // entries only if some row picked it.  Building B^T costs a pass over B;
+    // it pays only where the pull work (mask entries x average column length
+    // of B) is well below the push work (entries of A x average row length of
+    // B), or when DOT is forced.
     auto want_bt = [&](const ProdIn &x) {
         if (x.comp || x.bt_rp || !x.a_sorted) return false;
         if (h->force == F_DOT) return true;
@@ -315,200 +345,351 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         const double pull = (double)x.M->nnz * bnz / std::max(1, x.B->ncols);
         return pull * 4.0 < push;
     };
-    std::vector<BtDesc> bd;
-    long long bt_counts = 0, bt_nnz = 0, bt_rows = 0;
     if (build_bt && h->allow_dot && (h->force == F_AUTO || h->force == F_DOT)) {
         for (int p = 0; p < P; ++p) {
             if (!want_bt(in[p])) continue;
             const msgemm_csr *B = in[p].B;
-            bd.push_back(BtDesc{B->rowptr, B->colidx, B->values, B->nrows, B->ncols, B->nnz, bt_counts, bt_nnz,
-                                bt_rows});
-            bt_counts += (long long)B->ncols + 1;
-            bt_nnz += B->nnz;
-            bt_rows += B->nrows;
+            pl.bd.push_back(BtDesc{B->rowptr, B->colidx, B->values, B->nrows, B->ncols, B->nnz, pl.bt_counts,
+                                   pl.bt_nnz, pl.bt_rows});
+            pl.bt_counts += (long long)B->ncols + 1;
+            pl.bt_nnz += B->nnz;
+            pl.bt_rows += B->nrows;
         }
     }
-    int *bt_rp_all = nullptr, *bt_cur = nullptr, *bt_ci = nullptr;
-    void *bt_v = nullptr;
-    BtDesc *bt_tab = nullptr;
-    if (!bd.empty()) {
-        PScope ph(h, "bt_counts");
-        const int Q = (int)bd.size();
-        const size_t bytes = carve_size<int>(bt_counts + 1) * 2 + carve_size<int>(bt_nnz) +
-                             carve_size<char>((size_t)bt_nnz * in_bytes(sr)) +
-                             carve_size<long long>(bt_counts / STILE + 4) + carve_size<BtDesc>(Q);
+    if (!pl.bd.empty()) {
+        const int Q = (int)pl.bd.size();
+        const size_t bytes = carve_size<int>(pl.bt_counts + 1) * 2 + carve_size<int>(pl.bt_nnz) +
+                             carve_size<char>((size_t)pl.bt_nnz * in_bytes(sr)) +
+                             carve_size<long long>(pl.bt_counts / STILE + 4) + carve_size<BtDesc>(Q);
         CKS(grow(h, h->bt, bytes));
         Carver cb(h->bt.p);
-        bt_rp_all = cb.take<int>(bt_counts + 1);
-        bt_cur = cb.take<int>(bt_counts + 1);
-        bt_ci = cb.take<int>(bt_nnz);
-        bt_v = cb.take<char>((size_t)bt_nnz * in_bytes(sr));
-        long long *tb = cb.take<long long>(bt_counts / STILE + 4);
-        bt_tab = cb.take<BtDesc>(Q);
-        CK(cudaMemcpyAsync(bt_tab, bd.data(), sizeof(BtDesc) * Q, cudaMemcpyHostToDevice, st));
-        CK(launch_bt_counts_multi(bt_tab, Q, bt_nnz, bt_cur, bt_counts, st, h->nsm));
-        CK(launch_excl_scan_int(bt_cur, bt_counts, bt_rp_all, tb, st, h->nsm));
+        pl.bt_rp_all = cb.take<int>(pl.bt_counts + 1);
+        pl.bt_cur = cb.take<int>(pl.bt_counts + 1);
+        pl.bt_ci = cb.take<int>(pl.bt_nnz);
+        pl.bt_v = cb.take<char>((size_t)pl.bt_nnz * in_bytes(sr));
+        pl.bt_tb = cb.take<long long>(pl.bt_counts / STILE + 4);
+        pl.bt_tab = cb.take<BtDesc>(Q);
         int q = 0;
         for (int p = 0; p < P; ++p) {
             if (!want_bt(in[p])) continue;
-            dp[p].bt_rp = bt_rp_all + bd[q].co;
-            dp[p].bt_ci = bt_ci;
-            dp[p].bt_v = in_bytes(sr) ? bt_v : nullptr;
+            dp[p].bt_rp = pl.bt_rp_all + pl.bd[q].co;
+            dp[p].bt_ci = pl.bt_ci;
+            dp[p].bt_v = in_bytes(sr) ? pl.bt_v : nullptr;
             ++q;
         }
     }
 
-    // ---- products table
-    ProdSet ps{};
-    ps.P = P;
-    if (P == 1) {
-        ps.p0 = dp[0];
-        ps.tab = dtab;
-    } else {
-        ps.tab = dtab;
-    }
-    CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
-
-    // ---- binning
-    {
-    PScope ph(h, "bin");
-    switch (sr) {
-    case MSGEMM_PLUS_TIMES_F32: CK(launch_bin_score_f32(ps, ra, pol, room, st, h->nsm)); break;
-    case MSGEMM_PLUS_TIMES_I64: CK(launch_bin_score_i64(ps, ra, pol, room, st, h->nsm)); break;
-    default: CK(launch_bin_score_pp(ps, ra, pol, room, st, h->nsm)); break;
-    }
-    CK(launch_bin_scatter(ra, st, h->nsm));
-    }
-    h->last_kind = ra.kind;
-    h->last_R = R;
-
-    // ---- temporary room: mask-sized for plain masks, bound-sized when complemented
-    long long comp_total = 0;
-    if (any_comp) {
-        PScope ph(h, "room");
-        CK(launch_scan_room(ra, room, tmpn, room_tiles, ra.bound_total, st, h->nsm));
-        CK(cudaMemcpyAsync(&comp_total, ra.bound_total, sizeof comp_total, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-    }
-    const long long tmp_entries = tmpn + comp_total;
-    TmpOut tmp{};
-    const int ob = out_bytes(sr);
-    if (!aligned) {
-        CKS(grow(h, h->tmp, carve_size<int>(tmp_entries) + carve_size<char>((size_t)tmp_entries * ob)));
+    // ---- temporary output: mask-sized for plain masks (complemented room is
+    // known only after the bound scan); the gradient form writes in place
+    if (pl.aligned) {
+        pl.L.tmp.ci = nullptr;
+        pl.L.tmp.v = in[0].aligned_out;   // one product in gradient form
+    } else if (!pl.any_comp) {
+        const int ob = out_bytes(sr);
+        CKS(grow(h, h->tmp, carve_size<int>(pl.tmpn) + carve_size<char>((size_t)pl.tmpn * ob)));
         Carver ct(h->tmp.p);
-        tmp.ci = ct.take<int>(tmp_entries);
-        tmp.v = ct.take<char>((size_t)tmp_entries * ob);
-    } else {
-        tmp.ci = nullptr;
-        tmp.v = in[0].aligned_out;   // one product in gradient form
+        pl.L.tmp.ci = ct.take<int>(pl.tmpn);
+        pl.L.tmp.v = ct.take<char>((size_t)pl.tmpn * ob);
     }
 
-    // ---- B^T entries, only when some row picked the pull kernel
-    if (!bd.empty()) {
-        PScope ph(h, "bt_fill");
-        CK(cudaMemcpyAsync(bt_cur, bt_rp_all, sizeof(int) * (size_t)(bt_counts + 1), cudaMemcpyDeviceToDevice, st));
-        CK(launch_bt_fill_multi(bt_tab, (int)bd.size(), bt_rows, in_bytes(sr), bt_cur, bt_ci, bt_v, ra.any_dot, st,
-                                h->nsm));
-    }
-
-    // ---- accumulation, one persistent kernel per kind
-    RowLaunch L{};
-    L.ra = ra;
-    L.tmp = tmp;
-    L.aligned = aligned ? 1 : 0;
+    // ---- tile index of B for every tiled product, within the memory budget;
+    // products left without one walk their tiles with per-entry cursors
+    pl.L.aligned = pl.aligned ? 1 : 0;
+    pl.nts.assign(P, 0);
+    pl.tpos.assign(P, nullptr);
     if (any_tiled) {
-        // tile index of B for every tiled product, within the memory budget;
-        // products left without one walk their tiles with per-entry cursors
-        const int T = pol.tileT[0];
+        const int T = pl.pol.tileT[0];
         long long need = 0;
-        std::vector<int> nts(P, 0);
         for (int p = 0; p < P; ++p) {
             if (dp[p].n <= T) continue;
-            nts[p] = (dp[p].n + T - 1) / T;
-            need += (long long)carve_size<int>((size_t)in[p].B->nrows * (nts[p] + 1));
+            pl.nts[p] = (dp[p].n + T - 1) / T;
+            need += (long long)carve_size<int>((size_t)in[p].B->nrows * (pl.nts[p] + 1));
         }
-        bool cursors = false;
         if (h->tile_index && need <= h->tile_index_budget) {
-            PScope ph(h, "tile_index");
             CKS(grow(h, h->tix, (size_t)need + 256));
             Carver ct(h->tix.p);
             for (int p = 0; p < P; ++p) {
-                if (!nts[p]) continue;
-                int *tp = ct.take<int>((size_t)in[p].B->nrows * (nts[p] + 1));
-                // skipped on the device unless binning put rows in a tiled kind
-                CK(launch_tile_bounds(in[p].B->rowptr, in[p].B->colidx, in[p].B->nrows, T, nts[p], tp,
-                                      ra.kind_count, st, h->nsm));
-                dp[p].tpos = tp;
-                dp[p].tstride = nts[p] + 1;
+                if (!pl.nts[p]) continue;
+                pl.tpos[p] = ct.take<int>((size_t)in[p].B->nrows * (pl.nts[p] + 1));
+                dp[p].tpos = pl.tpos[p];
+                dp[p].tstride = pl.nts[p] + 1;
             }
-            if (P == 1) ps.p0 = dp[0];
-            CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
         } else {
-            cursors = true;
-        }
-        if (cursors) {
-            CKS(grow(h, h->cur, carve_size<int4>(std::max<long long>(nnzA, 1))));
-            L.cursors = static_cast<int4 *>(h->cur.p);
+            pl.nts.assign(P, 0);
+            CKS(grow(h, h->cur, carve_size<int4>(std::max<long long>(pl.nnzA, 1))));
+            pl.L.cursors = static_cast<int4 *>(h->cur.p);
         }
     }
-    std::vector<int> kinds;
+
+    // ---- accumulator kinds to launch
     bool any_plain = false;
     for (int p = 0; p < P; ++p) any_plain |= !in[p].comp;
     if (any_plain) {
-        if (pol.slab[K_MSA_W]) kinds.push_back(K_MSA_W);
-        kinds.insert(kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
-        if (!bd.empty() || std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
-            kinds.insert(kinds.end(), {K_DOT_W, K_DOT_B});
-        kinds.push_back(K_MSA_T);
+        if (pl.pol.slab[K_MSA_W]) pl.kinds.push_back(K_MSA_W);
+        pl.kinds.insert(pl.kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
+        if (!pl.bd.empty() ||
+            std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
+            pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
+        pl.kinds.push_back(K_MSA_T);
     }
-    if (any_comp) kinds.insert(kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
-    for (int kd : kinds) {
+    if (pl.any_comp) pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
+
+    // ---- products table
+    pl.ps.P = P;
+    pl.ps.by_value = (P == 1 && by_value) ? 1 : 0;
+    pl.ps.tab = pl.dtab;
+    if (pl.ps.by_value) pl.ps.p0 = dp[0];
+    return MSGEMM_OK;
+}
+
+// Host -> device tables (pageable sources: never inside a capture).
+msgemm_status plan_upload(msgemm_handle *h, Plan &pl) {
+    cudaStream_t st = h->stream;
+    if (pl.P) CK(cudaMemcpyAsync(pl.dtab, h->hprods.data(), sizeof(DevProd) * pl.P, cudaMemcpyHostToDevice, st));
+    if (!pl.bd.empty())
+        CK(cudaMemcpyAsync(pl.bt_tab, pl.bd.data(), sizeof(BtDesc) * pl.bd.size(), cudaMemcpyHostToDevice, st));
+    return MSGEMM_OK;
+}
+
+// Device sequence, front: counters, B^T row pointers, binning.
+msgemm_status seq_front(msgemm_handle *h, Plan &pl) {
+    cudaStream_t st = h->stream;
+    CK(cudaMemsetAsync(pl.zero_begin, 0, pl.zero_bytes, st));
+    if (!pl.bd.empty()) {
+        PScope ph(h, "bt_counts");
+        CK(launch_bt_counts_multi(pl.bt_tab, (int)pl.bd.size(), pl.bt_nnz, pl.bt_cur, pl.bt_counts, st, h->nsm));
+        CK(launch_excl_scan_int(pl.bt_cur, pl.bt_counts, pl.bt_rp_all, pl.bt_tb, st, h->nsm));
+    }
+    PScope ph(h, "bin");
+    switch (pl.sr) {
+    case MSGEMM_PLUS_TIMES_F32: CK(launch_bin_score_f32(pl.ps, pl.L.ra, pl.pol, pl.room, st, h->nsm)); break;
+    case MSGEMM_PLUS_TIMES_I64: CK(launch_bin_score_i64(pl.ps, pl.L.ra, pl.pol, pl.room, st, h->nsm)); break;
+    default: CK(launch_bin_score_pp(pl.ps, pl.L.ra, pl.pol, pl.room, st, h->nsm)); break;
+    }
+    CK(launch_bin_scatter(pl.L.ra, st, h->nsm));
+    return MSGEMM_OK;
+}
+
+// Complemented products: temporary room from the per-row bounds (synchronises).
+msgemm_status comp_room(msgemm_handle *h, Plan &pl) {
+    cudaStream_t st = h->stream;
+    long long comp_total = 0;
+    {
+        PScope ph(h, "room");
+        CK(launch_scan_room(pl.L.ra, pl.room, pl.tmpn, pl.room_tiles, pl.L.ra.bound_total, st, h->nsm));
+        CK(cudaMemcpyAsync(&comp_total, pl.L.ra.bound_total, sizeof comp_total, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    const long long tmp_entries = pl.tmpn + comp_total;
+    const int ob = out_bytes(pl.sr);
+    CKS(grow(h, h->tmp, carve_size<int>(tmp_entries) + carve_size<char>((size_t)tmp_entries * ob)));
+    Carver ct(h->tmp.p);
+    pl.L.tmp.ci = ct.take<int>(tmp_entries);
+    pl.L.tmp.v = ct.take<char>((size_t)tmp_entries * ob);
+    return MSGEMM_OK;
+}
+
+// Device sequence, middle: B^T entries, tile index, one persistent kernel per
+// kind, per-tile output counts.
+msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
+    cudaStream_t st = h->stream;
+    const RowArrays &ra = pl.L.ra;
+    if (!pl.bd.empty()) {
+        PScope ph(h, "bt_fill");
+        CK(cudaMemcpyAsync(pl.bt_cur, pl.bt_rp_all, sizeof(int) * (size_t)(pl.bt_counts + 1), cudaMemcpyDeviceToDevice,
+                           st));
+        CK(launch_bt_fill_multi(pl.bt_tab, (int)pl.bd.size(), pl.bt_rows, in_bytes(pl.sr), pl.bt_cur, pl.bt_ci,
+                                pl.bt_v, ra.any_dot, st, h->nsm));
+    }
+    if (std::any_of(pl.nts.begin(), pl.nts.end(), [](int x) { return x > 0; })) {
+        PScope ph(h, "tile_index");
+        const std::vector<DevProd> &dp = h->hprods;
+        for (int p = 0; p < pl.P; ++p) {
+            if (!pl.nts[p]) continue;
+            // skipped on the device unless binning put rows in a tiled kind
+            CK(launch_tile_bounds(dp[p].b_rp, dp[p].b_ci, dp[p].k, pl.pol.tileT[0], pl.nts[p], pl.tpos[p],
+                                  ra.kind_count, st, h->nsm));
+        }
+    }
+    RowLaunch L = pl.L;
+    for (int kd : pl.kinds) {
         if (kd == K_MSA_T || kd == K_CMSA_T) {
             PScope ph(h, "sort_heavy");
             CK(launch_sort_heavy(ra, kd, st));
         }
         PScope ph(h, kind_name(kd));
-        L.slab = pol.slab[kd];
-        L.tileT = pol.tileT[kd == K_CMSA_T ? 1 : 0];
-        switch (sr) {
-        case MSGEMM_PLUS_TIMES_F32: CK(launch_kind_f32(kd, ps, L, st, h->nsm)); break;
-        case MSGEMM_PLUS_TIMES_I64: CK(launch_kind_i64(kd, ps, L, st, h->nsm)); break;
-        default: CK(launch_kind_pp(kd, ps, L, st, h->nsm)); break;
+        L.slab = pl.pol.slab[kd];
+        L.tileT = pl.pol.tileT[kd == K_CMSA_T ? 1 : 0];
+        switch (pl.sr) {
+        case MSGEMM_PLUS_TIMES_F32: CK(launch_kind_f32(kd, pl.ps, L, st, h->nsm)); break;
+        case MSGEMM_PLUS_TIMES_I64: CK(launch_kind_i64(kd, pl.ps, L, st, h->nsm)); break;
+        default: CK(launch_kind_pp(kd, pl.ps, L, st, h->nsm)); break;
         }
     }
-    if (aligned) return MSGEMM_OK;
-
-    // ---- count, allocate complemented outputs, compact
-    {
-        PScope ph(h, "count");
-        CK(launch_count_tiles(ps, ra, ntiles, tile_sums, tile_offs, prod_tot, chunk_start, st, h->nsm));
-    }
-    if (any_comp) {
-        std::vector<long long> tot(P);
-        CK(cudaMemcpyAsync(tot.data(), prod_tot + P, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        for (int p = 0; p < P; ++p) {
-            if (!in[p].comp) continue;
-            msgemm_csr_out *C = in[p].C;
-            if (tot[p] >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "product %d has >= 2^31 entries", p);
-            C->capacity = tot[p];
-            C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(tot[p], 1)));
-            C->values = dev_alloc(h, (size_t)ob * (size_t)std::max<long long>(tot[p], 1));
-            if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
-            dp[p].c_ci = C->colidx;
-            dp[p].c_v = C->values;
-        }
-        if (P == 1) ps.p0 = dp[0];
-        CK(cudaMemcpyAsync(dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
-    }
-    {
-        PScope ph(h, "compact");
-        // chunks: at most one per tile plus one per CCH entries of the capacity
-        long long cap = 0;
-        for (int p = 0; p < P; ++p) cap += in[p].C->capacity;
-        CK(launch_compact(ps, ra, tmp, ntiles, tile_offs, chunk_start, ntiles + cap / CCH + 1, ob, st, h->nsm));
-    }
+    if (pl.aligned) return MSGEMM_OK;
+    PScope ph(h, "count");
+    CK(launch_count_tiles(pl.ps, ra, pl.ntiles, pl.tile_sums, pl.tile_offs, pl.prod_tot, pl.chunk_start, st, h->nsm));
     return MSGEMM_OK;
+}
+
+// Complemented products: exact output sizes (synchronises), outputs allocated.
+msgemm_status comp_outputs(msgemm_handle *h, std::vector<ProdIn> &in, Plan &pl) {
+    cudaStream_t st = h->stream;
+    const int P = pl.P;
+    std::vector<DevProd> &dp = h->hprods;
+    std::vector<long long> tot(P);
+    CK(cudaMemcpyAsync(tot.data(), pl.prod_tot + P, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const int ob = out_bytes(pl.sr);
+    for (int p = 0; p < P; ++p) {
+        if (!in[p].comp) continue;
+        msgemm_csr_out *C = in[p].C;
+        if (tot[p] >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "product %d has >= 2^31 entries", p);
+        C->capacity = tot[p];
+        C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(tot[p], 1)));
+        C->values = dev_alloc(h, (size_t)ob * (size_t)std::max<long long>(tot[p], 1));
+        if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+        dp[p].c_ci = C->colidx;
+        dp[p].c_v = C->values;
+        pl.cap += tot[p];
+    }
+    if (pl.ps.by_value) pl.ps.p0 = dp[0];
+    CK(cudaMemcpyAsync(pl.dtab, dp.data(), sizeof(DevProd) * P, cudaMemcpyHostToDevice, st));
+    return MSGEMM_OK;
+}
+
+// Device sequence, back: chunked compaction into C.
+msgemm_status seq_compact(msgemm_handle *h, Plan &pl) {
+    PScope ph(h, "compact");
+    // chunks: at most one per tile plus one per CCH entries of the capacity
+    CK(launch_compact(pl.ps, pl.L.ra, pl.L.tmp, pl.ntiles, pl.tile_offs, pl.chunk_start,
+                      pl.ntiles + pl.cap / CCH + 1, out_bytes(pl.sr), h->stream, h->nsm));
+    return MSGEMM_OK;
+}
+
+template <class T> void key_put(std::string &k, const T &x) {
+    k.append(reinterpret_cast<const char *>(&x), sizeof x);
+}
+
+// Everything a captured sequence bakes in: policy, launch arguments,
+// workspace and input pointers and sizes (not the outputs, which the device
+// table carries and which are uploaded before every replay).
+std::string graph_key(const msgemm_handle *h, const Plan &pl) {
+    std::string k;
+    key_put(k, pl.sr);
+    key_put(k, pl.P);
+    key_put(k, pl.pol);
+    key_put(k, pl.L);
+    key_put(k, pl.ps.tab);
+    key_put(k, pl.R);
+    key_put(k, pl.ntiles);
+    key_put(k, pl.cap);
+    key_put(k, pl.zero_begin);
+    key_put(k, pl.zero_bytes);
+    key_put(k, h->nsm);
+    for (int kd : pl.kinds) key_put(k, kd);
+    for (const BtDesc &b : pl.bd) key_put(k, b);
+    key_put(k, pl.bt_rp_all);
+    key_put(k, pl.bt_tab);
+    for (int p = 0; p < pl.P; ++p) {
+        const DevProd &d = h->hprods[p];
+        for (const void *ptr : {(const void *)d.m_rp, (const void *)d.m_ci, (const void *)d.a_rp, (const void *)d.a_ci,
+                                d.a_v, (const void *)d.b_rp, (const void *)d.b_ci, d.b_v, (const void *)d.bt_rp,
+                                (const void *)d.bt_ci, d.bt_v, (const void *)d.tpos})
+            key_put(k, ptr);
+        for (long long x : {(long long)d.m, (long long)d.n, (long long)d.k, (long long)d.complement,
+                            (long long)d.a_sorted, d.row0, d.tile0, d.abase, d.tmp0, (long long)d.tstride,
+                            (long long)pl.nts[p]})
+            key_put(k, x);
+    }
+    return k;
+}
+
+// Replays the cached graph of this plan, or captures a new one (on the
+// handle's private capture stream: nothing runs during the capture) and
+// launches it on the handle's stream.
+msgemm_status run_graph(msgemm_handle *h, Plan &pl) {
+    std::string key = graph_key(h, pl);
+    if (h->gexec && key == h->gkey) {
+        CK(cudaGraphLaunch(h->gexec, h->stream));
+        g_kernel_launches.fetch_add(h->gkernels, std::memory_order_relaxed);
+        return MSGEMM_OK;
+    }
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+        h->gkey.clear();
+    }
+    if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+    const long long before = g_kernel_launches.load();
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    msgemm_status rs = MSGEMM_OK;
+    if (e == cudaSuccess) {
+        rs = seq_front(h, pl);
+        if (rs == MSGEMM_OK) rs = seq_middle(h, pl);
+        if (rs == MSGEMM_OK) rs = seq_compact(h, pl);
+    }
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) e = cudaStreamEndCapture(h->cap_stream, &g);
+    h->stream = user;
+    // launches counted during the capture were recorded, not run
+    g_kernel_launches.fetch_sub(g_kernel_launches.load() - before, std::memory_order_relaxed);
+    if (rs != MSGEMM_OK || e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return rs != MSGEMM_OK ? rs : fail(h, MSGEMM_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+    }
+    size_t nn = 0;
+    long long nk = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType t;
+                if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++nk;
+            }
+    }
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->gexec = nullptr;
+        return fail(h, MSGEMM_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+    }
+    h->gkey = std::move(key);
+    h->gkernels = nk;
+    ++h->gcaptures;
+    CK(cudaGraphLaunch(h->gexec, h->stream));
+    g_kernel_launches.fetch_add(nk, std::memory_order_relaxed);
+    return MSGEMM_OK;
+}
+
+// The whole one-phase pipeline for a set of products (Sec. 4-6).  With
+// use_graph, plain masks, no validation and no profiling, the device
+// sequence runs as a replayed CUDA graph; otherwise eagerly.
+msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
+                           bool validate, bool use_graph = false) {
+    bool graph = use_graph && !validate && !h->profile;
+    for (const ProdIn &x : in) graph = graph && !x.comp && !x.aligned_out;
+    Plan pl;
+    CKS(plan_prepare(h, in, sr, build_bt, !graph, pl));
+    CKS(plan_upload(h, pl));
+    // optional input validation: synchronises, and rejects invalid input
+    // before any kernel that would index through it runs
+    if (validate) {
+        PScope ph(h, "validate");
+        std::vector<const msgemm_csr *> mats;
+        for (const ProdIn &x : in) mats.insert(mats.end(), {x.M, x.A, x.B});
+        CKS(validate_inputs(h, mats));
+    }
+    if (graph) return run_graph(h, pl);
+    CKS(seq_front(h, pl));
+    if (pl.any_comp) CKS(comp_room(h, pl));
+    CKS(seq_middle(h, pl));
+    if (pl.aligned) return MSGEMM_OK;
+    if (pl.any_comp) CKS(comp_outputs(h, in, pl));
+    return seq_compact(h, pl);
 }
 
 msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_semiring sr, msgemm_csr_out *C) {
@@ -539,6 +720,215 @@ msgemm_status check_product(msgemm_handle *h, const msgemm_csr *M, const msgemm_
                     A->ncols, B->nrows, B->ncols);
     return MSGEMM_OK;
 }
+
+// ---- autotuning (msgemm_autotune): the policy knobs the binning pass reads
+struct Tuned {
+    int warp_flops_max = 65536;
+    float dot_ratio = 2.0f;
+    unsigned char pref[NCLASS][4];
+};
+
+Tuned current_tuned(const msgemm_handle *h) {
+    Tuned t;
+    t.warp_flops_max = h->warp_flops_max;
+    t.dot_ratio = h->dot_ratio;
+    memcpy(t.pref, h->pref, sizeof t.pref);
+    return t;
+}
+
+void apply_tuned(msgemm_handle *h, const Tuned &t) {
+    h->warp_flops_max = t.warp_flops_max;
+    h->dot_ratio = t.dot_ratio;
+    memcpy(h->pref, t.pref, sizeof t.pref);
+}
+
+// Cache file: a JSON object, one entry per line,
+//   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "pref": [[f,f,f,f], ...]}
+// with NCLASS preference rows of accumulator families (msgemm_accumulator).
+void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
+    FILE *f = fopen(path, "r");
+    if (!f) return;
+    char line[4096];
+    while (fgets(line, sizeof line, f)) {
+        const char *q0 = strchr(line, '"');
+        if (!q0) continue;
+        const char *q1 = strstr(q0 + 1, "\":");
+        if (!q1) continue;
+        std::string key(q0 + 1, q1);
+        std::vector<double> num;
+        for (const char *c = q1 + 2; *c;) {
+            if ((*c >= '0' && *c <= '9') || *c == '-' || *c == '.') {
+                char *e = nullptr;
+                num.push_back(strtod(c, &e));
+                c = e;
+            } else {
+                ++c;
+            }
+        }
+        if (num.size() != 2 + NCLASS * 4) continue;
+        Tuned t;
+        if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
+        t.warp_flops_max = (int)num[0];
+        t.dot_ratio = (float)num[1];
+        bool ok = true;
+        for (int c = 0; c < NCLASS; ++c)
+            for (int x = 0; x < 4; ++x) {
+                const double v = num[2 + c * 4 + x];
+                ok &= v >= F_AUTO && v <= F_DOT && v == (int)v;
+                t.pref[c][x] = (unsigned char)v;
+            }
+        if (ok) out[key] = t;
+    }
+    fclose(f);
+}
+
+bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : m) {
+        const Tuned &t = kv.second;
+        fprintf(f, "\"%s\": {\"warp_flops_max\": %d, \"dot_ratio\": %g, \"pref\": [", kv.first.c_str(),
+                t.warp_flops_max, (double)t.dot_ratio);
+        for (int c = 0; c < NCLASS; ++c)
+            fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
+        fprintf(f, "]}%s\n", ++i < m.size() ? "," : "");
+    }
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+// Coordinate search over the policy, timing the whole given batch: first the
+// accumulator family tried first for each row class that carries work (the
+// classes by descending work), then the warp/CTA split and the pull ratio.
+// Every candidate computes the same result; only time differs.
+struct Tuner {
+    msgemm_handle *h;
+    int P;
+    const msgemm_csr *M, *A, *B;
+    const int *comp;
+    msgemm_semiring sr;
+    cudaEvent_t ea = nullptr, eb = nullptr;
+    Tuner(msgemm_handle *h_, int P_, const msgemm_csr *M_, const int *c_, const msgemm_csr *A_, const msgemm_csr *B_,
+          msgemm_semiring sr_)
+        : h(h_), P(P_), M(M_), A(A_), B(B_), comp(c_), sr(sr_) {}
+    ~Tuner() {
+        if (ea) cudaEventDestroy(ea);
+        if (eb) cudaEventDestroy(eb);
+    }
+
+    msgemm_status run_once(float *ms) {
+        std::vector<msgemm_csr_out> C(P);
+        std::vector<ProdIn> in(P);
+        msgemm_status rs = MSGEMM_OK;
+        for (int p = 0; p < P && rs == MSGEMM_OK; ++p) {
+            const int c = comp ? comp[p] != 0 : 0;
+            rs = alloc_out(h, &M[p], c, sr, &C[p]);
+            in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = c; in[p].C = &C[p];
+        }
+        if (rs == MSGEMM_OK && cudaEventRecord(ea, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
+        if (rs == MSGEMM_OK) rs = run_pipeline(h, in, sr, true, false);
+        if (rs == MSGEMM_OK && cudaEventRecord(eb, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
+        if (rs == MSGEMM_OK && (cudaEventSynchronize(eb) != cudaSuccess || cudaEventElapsedTime(ms, ea, eb) != cudaSuccess))
+            rs = fail(h, MSGEMM_ERR_CUDA, "autotune timing failed");
+        cudaStreamSynchronize(h->stream);
+        for (msgemm_csr_out &c : C)
+            for (void *ptr : {(void *)c.rowptr, (void *)c.colidx, c.values, (void *)c.d_nnz}) dev_free(h, ptr);
+        return rs;
+    }
+
+    // median of three timed runs after one untimed
+    msgemm_status measure(float *ms) {
+        float t[3], w;
+        CKS(run_once(&w));
+        for (float &x : t) CKS(run_once(&x));
+        std::sort(t, t + 3);
+        *ms = t[1];
+        return MSGEMM_OK;
+    }
+
+    // work per row class (sum of push flops) from the last run's binning
+    msgemm_status class_work(std::vector<double> &work) {
+        work.assign(NCLASS, 0.0);
+        const long long R = h->last_R;
+        if (R == 0) return MSGEMM_OK;
+        std::vector<long long> flops(R);
+        CK(cudaStreamSynchronize(h->stream));
+        CK(cudaMemcpy(flops.data(), h->rows.p, sizeof(long long) * R, cudaMemcpyDeviceToHost));   // ra.flops
+        long long r = 0;
+        for (int p = 0; p < P; ++p) {
+            std::vector<int> rp(M[p].nrows + 1);
+            CK(cudaMemcpy(rp.data(), M[p].rowptr, sizeof(int) * rp.size(), cudaMemcpyDeviceToHost));
+            for (int i = 0; i < M[p].nrows; ++i, ++r)
+                if (!(comp && comp[p])) work[row_class(flops[r], rp[i + 1] - rp[i])] += (double)flops[r];
+        }
+        return MSGEMM_OK;
+    }
+
+    msgemm_status tune() {
+        CK(cudaEventCreate(&ea));
+        CK(cudaEventCreate(&eb));
+        float best;
+        CKS(measure(&best));
+        std::vector<double> work;
+        CKS(class_work(work));
+        double total = 0;
+        for (double w : work) total += w;
+        std::vector<int> order;
+        for (int c = 0; c < NCLASS; ++c)
+            if (work[c] > 0.005 * total) order.push_back(c);
+        std::sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+        const float keep = 0.98f;   // a candidate must win by 2% to replace the incumbent
+        for (int c : order) {
+            unsigned char base[4];
+            memcpy(base, h->pref[c], 4);
+            unsigned char best_pref[4];
+            memcpy(best_pref, base, 4);
+            for (int fam : {F_MSA, F_HASH, F_MCA}) {
+                if (base[0] == fam) continue;
+                unsigned char cand[4] = {(unsigned char)fam, 0, 0, 0};
+                int n = 1;
+                for (int x = 0; x < 4 && base[x] != F_AUTO; ++x)
+                    if (base[x] != fam && n < 4) cand[n++] = base[x];
+                while (n < 4) cand[n++] = F_AUTO;
+                memcpy(h->pref[c], cand, 4);
+                float t;
+                CKS(measure(&t));
+                if (t < best * keep) {
+                    best = t;
+                    memcpy(best_pref, cand, 4);
+                }
+            }
+            memcpy(h->pref[c], best_pref, 4);
+        }
+        const int wbest0 = h->warp_flops_max;
+        int wbest = wbest0;
+        for (int w : {8192, 16384, 32768, 65536, 131072, 262144}) {
+            if (w == wbest0) continue;
+            h->warp_flops_max = w;
+            float t;
+            CKS(measure(&t));
+            if (t < best * keep) { best = t; wbest = w; }
+        }
+        h->warp_flops_max = wbest;
+        if (h->allow_dot) {
+            const float dbest0 = h->dot_ratio;
+            float dbest = dbest0;
+            for (float d : {0.5f, 1.0f, 2.0f, 4.0f, 8.0f}) {
+                if (d == dbest0) continue;
+                h->dot_ratio = d;
+                float t;
+                CKS(measure(&t));
+                if (t < best * keep) { best = t; dbest = d; }
+            }
+            h->dot_ratio = dbest;
+        }
+        return MSGEMM_OK;
+    }
+};
 
 }  // namespace
 
@@ -701,7 +1091,6 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
                                  const msgemm_csr *A, const msgemm_csr *B, msgemm_semiring sr, msgemm_csr_out *C,
                                  int use_graph) {
     if (!h || nprod < 0 || (nprod > 0 && (!M || !A || !B || !C))) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
-    (void)use_graph;
     h->nprof = 0;
     if (nprod == 0) return MSGEMM_OK;
     std::vector<ProdIn> in(nprod);
@@ -711,13 +1100,38 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
         CKS(alloc_out(h, &M[p], comp, sr, &C[p]));
         in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = comp; in[p].C = &C[p];
     }
-    return run_pipeline(h, in, sr, true, h->validate);
+    return run_pipeline(h, in, sr, true, h->validate, use_graph != 0);
 }
 
 msgemm_status msgemm_autotune(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,
                               const msgemm_csr *A, const msgemm_csr *B, msgemm_semiring sr, const char *cache_path) {
-    (void)nprod; (void)M; (void)complement; (void)A; (void)B; (void)sr; (void)cache_path;
-    return fail(h, MSGEMM_ERR_UNSUPPORTED, "autotune not available in this build");
+    if (!h || nprod < 0 || (nprod > 0 && (!M || !A || !B))) return fail(h, MSGEMM_ERR_INVALID, "bad arguments");
+    for (int p = 0; p < nprod; ++p) CKS(check_product(h, &M[p], &A[p], &B[p], sr));
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, h->device));
+    static const char *sr_names[3] = {"plus_times_f32", "plus_times_i64", "plus_pair_i64"};
+    const std::string key = std::string(prop.name) + "|" + sr_names[sr];
+    std::map<std::string, Tuned> cache;
+    if (cache_path) {
+        read_tuned(cache_path, cache);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            apply_tuned(h, it->second);
+            return MSGEMM_OK;
+        }
+    }
+    if (nprod == 0) return MSGEMM_OK;
+    const int saved_profile = h->profile;
+    h->profile = 0;
+    Tuner tu(h, nprod, M, complement, A, B, sr);
+    msgemm_status rs = tu.tune();
+    h->profile = saved_profile;
+    if (rs != MSGEMM_OK) return rs;
+    if (cache_path) {
+        cache[key] = current_tuned(h);
+        if (!write_tuned(cache_path, cache)) return fail(h, MSGEMM_ERR_INVALID, "cannot write %s", cache_path);
+    }
+    return MSGEMM_OK;
 }
 
 msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_bytes, int sorted, msgemm_csr_out *At) {
@@ -820,6 +1234,8 @@ void msgemm_destroy(msgemm_handle *h) {
         cudaEventDestroy(ph.a);
         cudaEventDestroy(ph.b);
     }
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix}) dev_free(h, b->p);
     delete h;
 }

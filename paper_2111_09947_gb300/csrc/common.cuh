@@ -55,15 +55,18 @@ struct DevProd {
     int *c_rp, *c_ci; void *c_v; long long *c_nnz;  // outputs
 };
 
-// Up to one product by value (grid-constant parameter), else a device table.
+// One product by value (grid-constant parameter) when by_value is set, else
+// a device table (always for batches; also for a single product replayed from
+// a CUDA graph, whose outputs change between replays).
 struct ProdSet {
     int P;
+    int by_value;
     const DevProd *tab;
     DevProd p0;
 };
 
 __device__ __forceinline__ const DevProd &prod_at(const ProdSet &ps, int p) {
-    return ps.P == 1 ? ps.p0 : ps.tab[p];
+    return ps.by_value ? ps.p0 : ps.tab[p];
 }
 
 // Product owning global row r (binary search over row0).

@@ -1,0 +1,170 @@
+"""Batched form: CUDA-graph replay and the autotuner, against the CPU oracle.
+
+Graph replay must give the oracle's result on every call, with outputs that
+move between calls (they reach the kernels through a device table), after a
+change of inputs (a new capture), for a single product (table instead of a
+by-value parameter) and with complemented masks (which run eagerly).  The
+autotuner only reorders the policy, so results must still match the oracle;
+its cache must be valid JSON that a later call reads back instead of timing.
+"""
+import json
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2111_09947_gb300 import _lib, synth
+from gpu_util import assert_parity, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def batch():
+    ps = synth.batched_problems(nprod=12, seed=31, log2_range=(8, 12))
+    devs = [to_dev(p, "plus_times_f32") for p in ps]
+    refs = [O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32") for p in ps]
+    return ps, devs, refs
+
+
+def _run(h, devs, use_graph, complement=None, semiring="plus_times_f32"):
+    return _lib.msgemm_run_batched(h, [d["M"] for d in devs], [d["A"] for d in devs], [d["B"] for d in devs],
+                                   semiring, complement=complement, use_graph=use_graph)
+
+
+def _launches():
+    return int(_lib.load().msgemm_kernel_launches())
+
+
+def test_graph_replay_matches_oracle(batch):
+    ps, devs, refs = batch
+    h = _lib.Handle()
+    try:
+        l0 = _launches()
+        eager = _run(h, devs, False)
+        torch.cuda.synchronize()
+        n_eager = _launches() - l0
+        for o, ref in zip(eager, refs):
+            assert_parity(o.trimmed(), ref, "plus_times_f32")
+        kept = []
+        for call in range(3):
+            l0 = _launches()
+            outs = _run(h, devs, True)
+            torch.cuda.synchronize()
+            # a replay launches the same kernels as the eager pipeline
+            assert _launches() - l0 == n_eager
+            for o, ref in zip(outs, refs):
+                assert_parity(o.trimmed(), ref, "plus_times_f32")
+            kept.append(outs)
+        h.sync_status()
+        # outputs of earlier replays stay intact (each call writes its own)
+        for outs in kept:
+            for o, ref in zip(outs, refs):
+                assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+
+
+def test_graph_recaptures_on_new_inputs(batch):
+    ps, devs, refs = batch
+    other = synth.batched_problems(nprod=5, seed=32, log2_range=(9, 11))
+    odevs = [to_dev(p, "plus_times_f32") for p in other]
+    orefs = [O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32") for p in other]
+    h = _lib.Handle()
+    try:
+        for ds, rs in [(devs, refs), (odevs, orefs), (devs, refs), (odevs[:1], orefs[:1])]:
+            outs = _run(h, ds, True)
+            for o, ref in zip(outs, rs):
+                assert_parity(o.trimmed(), ref, "plus_times_f32")
+        h.sync_status()
+    finally:
+        h.close()
+
+
+def test_graph_same_shape_new_values():
+    # same sizes, new value buffers: a changed pointer is a new capture
+    ps = synth.batched_problems(nprod=4, seed=33, log2_range=(9, 10))
+    h = _lib.Handle()
+    try:
+        for rep in range(2):
+            qs = [dict(p) for p in ps]
+            for q in qs:
+                q["A"] = q["A"].with_values(synth.uniform_f32(q["A"].nnz, 700 + rep, 1))
+            devs = [to_dev(q, "plus_times_f32") for q in qs]
+            outs = _run(h, devs, True)
+            for q, o in zip(qs, outs):
+                assert_parity(o.trimmed(), O.masked_spgemm(q["M"], q["A"], q["B"], "plus_times_f32"),
+                              "plus_times_f32")
+    finally:
+        h.close()
+
+
+@pytest.mark.parametrize("semiring", ["plus_times_i64", "plus_pair_i64"])
+def test_graph_integer_semirings(semiring):
+    p = synth.random_problem(700, 500, 900, 6.0, 5.0, 20.0, 34, {"plus_times_i64": "i64", "plus_pair_i64": "pair"}[semiring])
+    d = to_dev(p, semiring)
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], semiring)
+    h = _lib.Handle()
+    try:
+        for _ in range(3):
+            (o,) = _run(h, [d], True, semiring=semiring)
+            assert_parity(o.trimmed(), ref, semiring)
+    finally:
+        h.close()
+
+
+def test_graph_with_complement_runs_eagerly(batch):
+    ps, devs, refs = batch
+    comp = [i % 2 for i in range(len(devs))]
+    crefs = [O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32", complement=bool(c),
+                             method=O.ESC if c else O.MERGE)
+             for p, c in zip(ps, comp)]
+    h = _lib.Handle()
+    try:
+        for _ in range(2):
+            outs = _run(h, devs, True, complement=comp)
+            for o, ref in zip(outs, crefs):
+                assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+
+
+def test_autotune_keeps_parity_and_writes_cache(batch, tmp_path):
+    ps, devs, refs = batch
+    cache = tmp_path / "tune.json"
+    h = _lib.Handle()
+    try:
+        _lib.msgemm_autotune(h, [d["M"] for d in devs], [d["A"] for d in devs], [d["B"] for d in devs],
+                             "plus_times_f32", cache_path=cache)
+        outs = _run(h, devs, False)
+        for o, ref in zip(outs, refs):
+            assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+    d = json.loads(cache.read_text())
+    key = torch.cuda.get_device_name() + "|plus_times_f32"
+    assert key in d
+    e = d[key]
+    assert len(e["pref"]) == 16 and all(len(r) == 4 for r in e["pref"])
+    assert e["warp_flops_max"] > 0 and e["dot_ratio"] > 0
+
+
+def test_autotune_reads_cache(batch, tmp_path):
+    ps, devs, refs = batch
+    key = torch.cuda.get_device_name() + "|plus_times_f32"
+    # MCA first for every class, pull practically off: binning must follow it
+    entry = {"warp_flops_max": 65536, "dot_ratio": 1e6, "pref": [[3, 0, 0, 0]] * 16}
+    cache = tmp_path / "tune.json"
+    cache.write_text(json.dumps({"some other device|plus_times_f32": entry, key: entry}).replace("}, ", "},\n"))
+    h = _lib.Handle()
+    try:
+        _lib.msgemm_autotune(h, [], [], [], "plus_times_f32", cache_path=cache)
+        outs = _run(h, devs, False)
+        counts = h.bin_counts()
+        for o, ref in zip(outs, refs):
+            assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+    assert counts["hash_w"] == 0 and counts["hash_b"] == 0 and counts["msa_w"] == 0
+    assert counts["mca_w"] + counts["mca_b"] > 0
