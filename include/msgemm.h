@@ -82,10 +82,16 @@ typedef enum {
     MSGEMM_OPT_PROFILE = 4,       /* value 0/1 (default 0): record CUDA events around every
                                      phase and kernel launch of a call, on the handle's stream
                                      (read back with msgemm_profile_entry) */
-    MSGEMM_OPT_TILE_INDEX = 5     /* value 0/1 (default 1): heavy rows of wide products walk
-                                     their column tiles through a per-row tile index of B
+    MSGEMM_OPT_TILE_INDEX = 5,    /* value 0/1 (default 1): heavy rows of wide products walk
+                                     their column tiles through a tile index of B
                                      (rows(B) x (tiles + 1) ints, built per call, 4 GiB cap);
                                      0, or a product over the cap, uses per-entry cursors */
+    MSGEMM_OPT_GRID = 6           /* value 0/1/2 (default 1): heavy complemented rows are
+                                     processed as (row, column tile) items swept tile by tile
+                                     over the whole GPU -- 1: rows whose output is dense (room
+                                     n - nnz(M_i*) each), 2: every heavy complemented row,
+                                     0: never (one CTA walks all tiles of a row); needs the
+                                     tile index (or a single tile) */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

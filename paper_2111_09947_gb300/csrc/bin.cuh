@@ -48,16 +48,20 @@ __device__ __forceinline__ int pick_family(const Policy &pol, int fam, bool warp
 
 template <int SR>
 __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, int mnz, int anz, int n, bool comp,
-                           long long pull, bool dot_ok) {
+                           long long pull, bool dot_ok, bool index_ok) {
     constexpr int acc = SrSizes<SR>::acc;
     const bool warp = flops <= pol.warp_flops_max;
     if (comp) {
-        const long long bound = min(flops, (long long)(n - mnz));
+        const long long open = (long long)n - mnz;
+        const long long bound = min(flops, open);
         if (flops == 0 || bound <= 0) return K_EMPTY;
-        if (pol.force == F_MSA) return K_CMSA_T;
+        // heavy rows: the grid of (row, tile) items when the output is dense
+        // (its room is then all open columns, at most 4x the bound)
+        const int heavy = (pol.grid > 0 && index_ok && (pol.grid == 2 || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
+        if (pol.force == F_MSA) return heavy;
         if (warp && pol.slab[K_CHASH_W] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_W])) return K_CHASH_W;
         if (pol.slab[K_CHASH_B] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_B])) return K_CHASH_B;
-        return K_CMSA_T;
+        return heavy;
     }
     if (flops == 0 || mnz == 0) return K_EMPTY;
     if (pol.force != F_AUTO) {
@@ -108,7 +112,8 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
         }
         if (lane == 0) {
             const int mnz = m1 - m0;
-            const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok);
+            const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
+            const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
             ra.flops[r] = f;
             ra.kind[r] = (unsigned char)kind;
             ra.cnt[r] = 0;
@@ -116,7 +121,7 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
                 ra.tmpoff[r] = P.tmp0 + m0;
                 room[r] = 0;
             } else {
-                room[r] = (kind == K_EMPTY) ? 0 : min(f, (long long)(P.n - mnz));
+                room[r] = (kind == K_EMPTY) ? 0 : kind == K_CMSA_G ? (long long)(P.n - mnz) : min(f, (long long)(P.n - mnz));
             }
             atomicAdd(&hist[kind], 1);
             if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;

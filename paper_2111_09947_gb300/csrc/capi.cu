@@ -34,9 +34,9 @@ struct msgemm_handle {
     msgemm_free_fn free_fn = nullptr;
     void *ctx = nullptr;
     // workspace, reused across calls
-    Buf rows, small, tmp, bt, cur, prods, tix;
+    Buf rows, small, tmp, bt, cur, prods, tix, gbuf;
     unsigned *d_err = nullptr;   // in `small`, persistent
-    int force = 0, validate = 0, allow_dot = 1, tile_index = 1;
+    int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
     long long tile_index_budget = 4LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
@@ -136,7 +136,7 @@ struct PScope {
 
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
-                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t"};
+                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -182,7 +182,8 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;
     const long long msaw = (msa_bytes(max_n, acc) + 15) & ~15LL;
     p.slab[K_MSA_W] = msaw <= 24 * 1024 ? (int)msaw : 0;
-    p.slab[K_MSA_T] = p.slab[K_CMSA_T] = tslab;
+    p.slab[K_MSA_T] = p.slab[K_CMSA_T] = p.slab[K_CMSA_G] = tslab;
+    p.grid = h->grid;
     p.tileT[0] = p.tileT[1] = msa_tile_width(tslab, acc);
     memcpy(p.pref, h->pref, sizeof p.pref);
     return p;
@@ -252,6 +253,7 @@ struct Plan {
     // tile index of B for column-tiled products (nts[p] tiles, 0 = untiled)
     std::vector<int> nts;
     std::vector<int *> tpos;
+    int gnt = 0;   // CMSA_G: most column tiles of a complemented product
     RowLaunch L{};
     std::vector<int> kinds;
 };
@@ -288,6 +290,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         pl.any_comp |= x.comp != 0;
         max_n = std::max(max_n, d.n);
         if (d.n > pol0.tileT[x.comp ? 1 : 0]) any_tiled = true;
+        if (x.comp) pl.gnt = std::max(pl.gnt, (d.n + pol0.tileT[1] - 1) / pol0.tileT[1]);
         if (x.C) {
             d.c_rp = x.C->rowptr; d.c_ci = x.C->colidx; d.c_v = x.C->values; d.c_nnz = reinterpret_cast<long long *>(x.C->d_nnz);
             if (!x.comp) pl.cap += x.C->capacity;
@@ -327,6 +330,8 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     ra.kind_off = cs.take<int>(NKIND + 1);
     ra.any_dot = cs.take<int>(1);
     ra.bound_total = cs.take<long long>(1);
+    pl.L.gnext = cs.take<unsigned long long>(1);
+    pl.L.gnt = pl.gnt;
     pl.zero_bytes = (size_t)(cs.base + cs.off - pl.zero_begin);
     h->last_kind_count = ra.kind_count;
     h->last_kind = ra.kind;
@@ -412,7 +417,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
                 if (!pl.nts[p]) continue;
                 pl.tpos[p] = ct.take<int>((size_t)in[p].B->nrows * (pl.nts[p] + 1));
                 dp[p].tpos = pl.tpos[p];
-                dp[p].tstride = pl.nts[p] + 1;
+                dp[p].tstride = in[p].B->nrows;   // tile-major planes
             }
         } else {
             pl.nts.assign(P, 0);
@@ -432,7 +437,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
             pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
         pl.kinds.push_back(K_MSA_T);
     }
-    if (pl.any_comp) pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
+    if (pl.any_comp) pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T, K_CMSA_G});
 
     // ---- products table
     pl.ps.P = P;
@@ -474,11 +479,23 @@ msgemm_status seq_front(msgemm_handle *h, Plan &pl) {
 msgemm_status comp_room(msgemm_handle *h, Plan &pl) {
     cudaStream_t st = h->stream;
     long long comp_total = 0;
+    int ng = 0;
     {
         PScope ph(h, "room");
         CK(launch_scan_room(pl.L.ra, pl.room, pl.tmpn, pl.room_tiles, pl.L.ra.bound_total, st, h->nsm));
         CK(cudaMemcpyAsync(&comp_total, pl.L.ra.bound_total, sizeof comp_total, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(&ng, pl.L.ra.kind_count + K_CMSA_G, sizeof ng, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+    }
+    if (ng > 0) {
+        // per (row, tile) piece counts and offsets, per-row completed items
+        const size_t slots = (size_t)ng * pl.gnt;
+        CKS(grow(h, h->gbuf, carve_size<int>(slots) * 2 + carve_size<int>(ng)));
+        Carver cg(h->gbuf.p);
+        pl.L.gcnt = cg.take<int>(slots);
+        pl.L.goff = cg.take<int>(slots);
+        pl.L.gdone = cg.take<int>(ng);
+        CK(cudaMemsetAsync(pl.L.gdone, 0, sizeof(int) * (size_t)ng, st));
     }
     const long long tmp_entries = pl.tmpn + comp_total;
     const int ob = out_bytes(pl.sr);
@@ -513,13 +530,13 @@ msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
     }
     RowLaunch L = pl.L;
     for (int kd : pl.kinds) {
-        if (kd == K_MSA_T || kd == K_CMSA_T) {
+        if (kd == K_MSA_T || kd == K_CMSA_T || kd == K_CMSA_G) {
             PScope ph(h, "sort_heavy");
             CK(launch_sort_heavy(ra, kd, st));
         }
         PScope ph(h, kind_name(kd));
         L.slab = pl.pol.slab[kd];
-        L.tileT = pl.pol.tileT[kd == K_CMSA_T ? 1 : 0];
+        L.tileT = pl.pol.tileT[(kd == K_CMSA_T || kd == K_CMSA_G) ? 1 : 0];
         switch (pl.sr) {
         case MSGEMM_PLUS_TIMES_F32: CK(launch_kind_f32(kd, pl.ps, L, st, h->nsm)); break;
         case MSGEMM_PLUS_TIMES_I64: CK(launch_kind_i64(kd, pl.ps, L, st, h->nsm)); break;
@@ -986,6 +1003,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_DOT: h->allow_dot = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_PROFILE: h->profile = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_TILE_INDEX: h->tile_index = value != 0; return MSGEMM_OK;
+    case MSGEMM_OPT_GRID:
+        if (value < 0 || value > 2) return fail(h, MSGEMM_ERR_INVALID, "grid mode is 0, 1 or 2");
+        h->grid = (int)value;
+        return MSGEMM_OK;
     default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
     }
 }
@@ -1236,7 +1257,7 @@ void msgemm_destroy(msgemm_handle *h) {
     }
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix}) dev_free(h, b->p);
+    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix, &h->gbuf}) dev_free(h, b->p);
     delete h;
 }
 

@@ -31,6 +31,7 @@ enum Kind : int {
     K_CHASH_W,     // complemented: hash keyed by produced columns
     K_CHASH_B,
     K_CMSA_T,      // complemented: MSA with NOTALLOWED default flipped, tiled
+    K_CMSA_G,      // complemented, dense output: (row, tile) items over the whole grid, tile-major
     NKIND
 };
 
@@ -50,8 +51,8 @@ struct DevProd {
     long long tile0;                          // first compaction tile of this product
     long long abase;                          // first cursor slot (stored entries of A before this product)
     long long tmp0;                           // first temporary-output slot of this product (plain mask)
-    const int *tpos;                          // tile index of B (rows x tstride) or null
-    int tstride;                              // column tiles + 1
+    const int *tpos;                          // tile index of B, tile-major planes, or null
+    int tstride;                              // plane length (rows of B): row c, boundary t at tpos[t * tstride + c]
     int *c_rp, *c_ci; void *c_v; long long *c_nnz;  // outputs
 };
 
@@ -113,6 +114,7 @@ struct Policy {
     int warp_flops_max;           // rows above go to CTA-level kinds
     int slab[NKIND];              // bytes per warp (_W) or per CTA (_B, _T); 0 = disabled
     int tileT[2];                 // MSA_T tile width for [plain, complemented]
+    int grid;                     // CMSA_G: 0 off, 1 for dense-output rows, 2 for every heavy complemented row
     unsigned char pref[NCLASS][4];  // families in preference order (F_AUTO = end)
 };
 

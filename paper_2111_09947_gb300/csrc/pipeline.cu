@@ -695,26 +695,29 @@ cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, i
 namespace msg {
 
 // ------------------------------------------------------------ tile index
-// For every row k of B and column tile t (width T): tpos[k * (nt + 1) + t] =
+// For every row k of B and column tile t (width T): tpos[t * nrows + k] =
 // first position of row k whose column is >= t * T (the row end if none), so
-// the part of row k inside tile t is [tpos[.. + t], tpos[.. + t + 1]).  One
-// warp per row; every slot is first set to the row end, then each entry that
-// starts a tile writes the slots of the tiles it opens (rows are sorted).
+// the part of row k inside tile t is [tpos[t * nrows + k], tpos[(t + 1) *
+// nrows + k]).  Tile-major planes: kernels that sweep one tile for many rows
+// read one plane.  One warp per row; every slot is first set to the row end,
+// then each entry that starts a tile writes the slots of the tiles it opens
+// (rows are sorted).
 __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt,
                                                      int *tpos, const int *gate) {
-    if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0) return;   // gate = per-kind row counts
+    // gate = per-kind row counts
+    if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0 && gate[K_CMSA_G] == 0) return;
     const int lane = threadIdx.x & 31;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
     for (long long k = gw; k < nrows; k += nw) {
         const int s = rp[k], e = rp[k + 1];
-        int *base = tpos + k * (long long)(nt + 1);
-        for (int t = lane; t <= nt; t += 32) base[t] = e;
+        int *base = tpos + k;   // boundary t of row k at base[t * nrows]
+        for (int t = lane; t <= nt; t += 32) base[(long long)t * nrows] = e;
         __syncwarp();
         for (int q = s + lane; q < e; q += 32) {
             const int tq = min(nt - 1, ci[q] / T);
             const int tp = (q == s) ? -1 : min(nt - 1, ci[q - 1] / T);
-            for (int t = tp + 1; t <= tq; ++t) base[t] = q;
+            for (int t = tp + 1; t <= tq; ++t) base[(long long)t * nrows] = q;
         }
         __syncwarp();
     }

@@ -27,6 +27,11 @@ struct RowLaunch {
     int4 *cursors;     // _T kinds: one cursor per stored entry of A (global)
     int aligned;       // 1: write values only, at the mask entry's own slot (tmp + rank);
                        //    the output array is zeroed beforehand (gradient form)
+    // CMSA_G items: per (row of the kind, tile) entry count and offset in the
+    // row, per-row completed items, item cursor, tiles per row slot (max)
+    int *gcnt, *goff, *gdone;
+    unsigned long long *gnext;
+    int gnt;
 };
 
 template <int SR>
@@ -53,12 +58,12 @@ struct RowSeg {
     }
 };
 struct TileSeg {
-    const int *tpos;   // row c, tile t: [tpos[c * stride + t], tpos[c * stride + t + 1])
+    const int *tpos;   // row c, tile t: [tpos[t * stride + c], tpos[(t + 1) * stride + c])
     int stride, tile;
     __device__ __forceinline__ void operator()(int c, int &s, int &e) const {
-        const int *p = tpos + (long long)c * stride + tile;
+        const int *p = tpos + (long long)tile * stride + c;
         s = __ldg(p);
-        e = __ldg(p + 1);
+        e = __ldg(p + stride);
     }
 };
 
@@ -832,6 +837,180 @@ __global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet 
         const DevProd &P = prod_at(ps, prod_of_row(ps, r));
         const RowCtx c = row_ctx(P, r, L.ra);
         row_msa_t<SR, COMP>(P, c, L, smem, scratch);
+    }
+}
+
+// ------------------------------------------- complemented MSA, grid of tiles
+// Heavy complemented rows with dense output (their reachable columns are at
+// least a quarter of those the mask leaves open).  Work items are (row,
+// column tile) pairs handed out tile-major: the CTAs of the whole GPU sweep
+// one column tile at a time, so that tile's slice of B and of the tile index
+// stays in L2 while every such row passes over it, instead of each row
+// streaming all of B from HBM.  An item is Sec. 5.2's MSA on one tile with
+// the complemented default (the mask's columns NOTALLOWED, all others
+// ALLOWED) and writes its entries, ascending, at the row's exact offset for
+// the tile: the number of columns before the tile that the mask leaves open
+// (these rows get n - nnz(M_i*) slots of room).  The CTA that completes a
+// row's last item packs the row's pieces to the front of its room.
+template <int SR>
+__device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab,
+                                         int *scratch, int tile, int ntiles, int mq0, int mq1, long long obase) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    Team<true> team;
+    const int T = L.tileT;
+    acc_t *vals = reinterpret_cast<acc_t *>(slab);
+    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(acc_t)));
+    unsigned *setw = mbits + words32(T);
+    const int c0 = tile * T, c1 = min(c.n, c0 + T);
+    for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
+        const int jj = __ldg(P.m_ci + q) - c0;
+        if ((unsigned)jj < (unsigned)T) atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
+        else atomicOr(L.ra.err, ERR_INTERNAL);
+    }
+    cta_sync();
+    auto ins = [&](int jj, in_t a, in_t b) {
+        if ((unsigned)jj >= (unsigned)T) {   // only an unsorted row of B gets here
+            atomicOr(L.ra.err, ERR_INTERNAL);
+            return;
+        }
+        if (!test_bit(mbits, jj)) {
+            S::add(&vals[jj], S::mul(a, b));
+            set_bit_once(setw, jj);
+        }
+    };
+    if (ntiles == 1) {
+        auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
+        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, f);
+    } else {
+        auto f = [&](int, in_t a, int j, in_t b) { ins(j - c0, a, b); };
+        const TileSeg seg{P.tpos, P.tstride, tile};
+        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, f);
+    }
+    cta_sync();
+    // gather the SET columns in ascending order; each thread owns a run of words
+    const int nwords = (int)words32(c1 - c0);
+    const int per = (nwords + team.size() - 1) / team.size();
+    const int w0 = min(nwords, team.tid() * per), w1 = min(nwords, w0 + per);
+    int cw = 0;
+    for (int w = w0; w < w1; ++w) cw += __popc(setw[w]);
+    int total;
+    const int off = block_excl_scan(cw, scratch, &total);
+    long long o = obase + off;
+    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    for (int w = w0; w < w1; ++w) {
+        unsigned bits = setw[w];
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1;
+            const int jj = w * 32 + b;
+            L.tmp.ci[o] = c0 + jj;
+            tv[o] = S::out(vals[jj]);
+            vals[jj] = 0;
+            ++o;
+        }
+        setw[w] = 0;
+    }
+    cta_sync();
+    for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
+        const int jj = __ldg(P.m_ci + q) - c0;
+        if ((unsigned)jj < (unsigned)T) mbits[jj >> 5] = 0;
+    }
+    return total;
+}
+
+// Moves a row's tile pieces to the front of its room, in tile order.  Each
+// piece moves left (its destination never passes its source), chunk by chunk,
+// all reads of a chunk before its writes.  Pieces were written by other SMs:
+// read through L2.
+template <int SR>
+__device__ __forceinline__ void cmsa_pack(const RowCtx &c, const RowLaunch &L, int x, int ntiles) {
+    using out_t = typename Sr<SR>::out_t;
+    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    int *tci = L.tmp.ci;
+    long long dst = 0;
+    for (int t = 0; t < ntiles; ++t) {
+        const long long slot = (long long)x * L.gnt + t;
+        const int nt = __ldcg(L.gcnt + slot);
+        const long long src = __ldcg(L.goff + slot);
+        if (src != dst) {
+            for (int b = 0; b < nt; b += blockDim.x) {
+                const int q = b + threadIdx.x;
+                int col = 0;
+                out_t v{};
+                if (q < nt) {
+                    col = __ldcg(tci + c.tmp + src + q);
+                    v = __ldcg(tv + c.tmp + src + q);
+                }
+                __syncthreads();
+                if (q < nt) {
+                    tci[c.tmp + dst + q] = col;
+                    tv[c.tmp + dst + q] = v;
+                }
+            }
+        }
+        dst += nt;
+    }
+    if (threadIdx.x == 0) L.ra.cnt[c.r] = (int)dst;
+}
+
+template <int SR>
+__global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int scratch[64];
+    __shared__ long long s_item;
+    __shared__ int s_mq[2];
+    __shared__ int s_last;
+    const int count = L.ra.kind_count[K_CMSA_G];
+    const int off = L.ra.kind_off[K_CMSA_G];
+    const int T = L.tileT;
+    {   // zero the tile arrays once; every item leaves them zeroed
+        unsigned *w = reinterpret_cast<unsigned *>(smem);
+        for (int x = threadIdx.x; x < L.slab / 4; x += blockDim.x) w[x] = 0;
+    }
+    const long long nitems = (long long)count * L.gnt;
+    for (;;) {
+        cta_sync();
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(L.gnext, 1ULL);
+        cta_sync();
+        const long long item = s_item;
+        if (item >= nitems) break;
+        const int tile = (int)(item / count), x = (int)(item % count);
+        const long long r = L.ra.perm[off + x];
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const RowCtx c = row_ctx(P, r, L.ra);
+        const int ntiles = (c.n + T - 1) / T;
+        if (tile >= ntiles) continue;
+        const int c0 = tile * T, c1 = min(c.n, c0 + T);
+        if (threadIdx.x < 2) {   // first mask entry at or after the tile's start / end
+            const int bound = threadIdx.x ? c1 : c0;
+            int lo = c.m0, hi = c.m1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (__ldg(P.m_ci + mid) < bound) lo = mid + 1; else hi = mid;
+            }
+            s_mq[threadIdx.x] = lo;
+        }
+        cta_sync();
+        const int mq0 = s_mq[0], mq1 = s_mq[1];
+        const long long rel = (long long)c0 - (mq0 - c.m0);   // open columns before the tile
+        const int cnt = cmsa_tile<SR>(P, c, L, smem, scratch, tile, ntiles, mq0, mq1, c.tmp + rel);
+        __threadfence();   // this item's entries, before the row's completion count
+        cta_sync();
+        if (threadIdx.x == 0) {
+            const long long slot = (long long)x * L.gnt + tile;
+            L.gcnt[slot] = cnt;
+            L.goff[slot] = (int)rel;
+            __threadfence();
+            s_last = atomicAdd(&L.gdone[x], 1) == ntiles - 1;
+        }
+        cta_sync();
+        if (s_last) {
+            __threadfence();
+            cmsa_pack<SR>(c, L, x, ntiles);
+        }
     }
 }
 

@@ -157,3 +157,69 @@ def test_tiled_rows_index_and_cursor_paths(handle, tile_index):
     finally:
         handle.force("auto")
         handle.set_option(_lib.OPT_TILE_INDEX, 1)
+
+
+def _varied_rows(m, k, n, a_deg, m_deg, seed, gen):
+    """A (m x k) and M (m x n) whose rows cycle through the given degrees,
+    columns uniform without replacement; B (k x n) Erdos-Renyi, 400 per row."""
+    rng = np.random.default_rng(seed)
+
+    def csr(rows, ncols, degs):
+        d = np.array([degs[i % len(degs)] for i in range(rows)], np.int64)
+        rp = np.concatenate([[0], np.cumsum(d)]).astype(np.int32)
+        ci = np.concatenate([np.sort(rng.choice(ncols, size=x, replace=False)) for x in d]).astype(np.int32) \
+            if d.sum() else np.zeros(0, np.int32)
+        return synth.Csr(rows, ncols, rp, ci)
+    A, M = csr(m, k, a_deg), csr(m, n, m_deg)
+    B = synth.er_pattern(k, n, 400.0, seed, 1)
+    if gen == "f32":
+        A = A.with_values(rng.uniform(-1, 1, A.nnz).astype(np.float32))
+        B = B.with_values(rng.uniform(-1, 1, B.nnz).astype(np.float32))
+    elif gen == "i64":
+        A = A.with_values(rng.integers(-3, 4, A.nnz).astype(np.int64))
+        B = B.with_values(rng.integers(-3, 4, B.nnz).astype(np.int64))
+    return {"M": M, "A": A, "B": B}
+
+
+@pytest.mark.parametrize("grid", [0, 1, 2])
+@pytest.mark.parametrize("semiring", ["plus_times_i64", "plus_times_f32", "plus_pair_i64"])
+def test_complemented_heavy_rows_grid_modes(handle, grid, semiring):
+    """Heavy complemented rows: one CTA walking every tile of a row (grid 0),
+    the tile-major grid of (row, tile) items for dense-output rows (1) or for
+    every heavy row (2).  130000 columns: 3 fp32 tiles, 5 int64 tiles, both
+    with a partial last one.  A's rows give 400 to 240000 products (sparse to
+    dense outputs); masks range from empty to half the columns."""
+    gen = {"plus_times_i64": "i64", "plus_times_f32": "f32", "plus_pair_i64": "pair"}[semiring]
+    q = _varied_rows(240, 3000, 130000, (1, 60, 600, 10, 300), (0, 2000, 65000, 50, 9000, 120000), 61, gen)
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring, complement=True, method=O.ESC)
+    handle.set_option(_lib.OPT_GRID, grid)
+    try:
+        for force in ("msa", "auto"):
+            handle.force(force)
+            dq = to_dev(q, semiring)
+            for rep in range(2):   # a second call finds the tile arrays as the first left them
+                res = _lib.msgemm_run(handle, dq["M"], dq["A"], dq["B"], semiring, complement=True).trimmed()
+                handle.sync_status()
+                assert_parity(res, ref, semiring, ctx=f"grid={grid} force={force} rep={rep}")
+            counts = handle.bin_counts()
+            if grid == 2 and force == "msa":
+                assert counts["cmsa_g"] > 0 and counts["cmsa_t"] == 0
+            if grid == 1:
+                assert counts["cmsa_g"] > 0
+            if grid == 0:
+                assert counts["cmsa_g"] == 0
+    finally:
+        handle.force("auto")
+        handle.set_option(_lib.OPT_GRID, 1)
+
+
+def test_bfs_grid_rows_scale16(handle):
+    """The BFS step at scale 16 with the default policy: its heavy rows take
+    the grid kind; every row against the oracle."""
+    p = synth.bfs_step(scale=16, ef=16, nsrc=128, seed=30)
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64", complement=True, method=O.ESC)
+    d = to_dev(p, "plus_times_i64")
+    res = _lib.msgemm_run(handle, d["M"], d["A"], d["B"], "plus_times_i64", complement=True).trimmed()
+    handle.sync_status()
+    assert handle.bin_counts()["cmsa_g"] > 0
+    assert_parity(res, ref, "plus_times_i64", ctx="bfs scale 16 grid")
