@@ -55,6 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--scale", type=int, default=None, help="R-MAT scale (tc: 20, bfs: 20, autograd: 18)")
     ap.add_argument("--no-forms", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="time the default policy (no untimed tuning first)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args(argv)
 
@@ -380,10 +381,21 @@ def kept_from_oracle(M, A, B, complement):
 
 
 # ----------------------------------------------------------------- measurement
-def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks_gpu=None):
-    """Times `steps` steps of a workload; returns a dict of measurements."""
+def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks_gpu=None, autotune=True):
+    """Times `steps` steps of a workload; returns a dict of measurements.
+    With autotune, a fresh handle's policy is first tuned on the workload's
+    products by the library's autotuner (untimed; its duration is reported)."""
+    if autotune:
+        h = _lib.Handle(dev)
     run = DeviceRun(torch, _lib, synth, h, wl, dev)
     wl.kept, wl.nnz_c = run.count_kept()
+    tune_s = None
+    if autotune:
+        t0 = time.perf_counter()
+        Ms, As, Bs, comps = (list(x) for x in zip(*run.prods))
+        _lib.msgemm_autotune(h, Ms, As, Bs, wl.semiring, complement=comps)
+        torch.cuda.synchronize()
+        tune_s = round(time.perf_counter() - t0, 2)
     h.set_option(_lib.OPT_PROFILE, 1)
     for _ in range(warmup):
         run.step()
@@ -401,7 +413,8 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
     times = timed_steps(torch, run.step, steps, flush, stream, after=collect)
     launches = _lib.load().msgemm_kernel_launches() - l0
     clk = clocks.stop() if clocks else None
-    out = {"times": times, "launches": launches, "clocks": clk, "per_phase": per_phase, "kinds": kinds, "run": run}
+    out = {"times": times, "launches": launches, "clocks": clk, "per_phase": per_phase, "kinds": kinds, "run": run,
+           "autotune_s": tune_s}
     if wl.name == "batched":
         run.per_product_step()
         torch.cuda.synchronize()
@@ -482,7 +495,7 @@ def e2e_measure(torch, run, flush, stream, steps):
 def form_summary(wl, meas):
     ms = statistics.mean(meas["times"])
     d = {"ms_per_step": round(ms, 4), "masked_products": wl.kept,
-         "masked_gflops": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3)}
+         "masked_gflops": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3), "autotune_s": meas.get("autotune_s")}
     if len(wl.mats) == 1:
         M, A, B, comp = wl.mats[0]
         vb_in, vb_out = VB[wl.semiring]
@@ -525,7 +538,8 @@ def run_ours(args):
     log("measuring")
     if world > 1:
         dist.barrier()
-    meas = measure(torch, _lib, synth, h, wl, dev, stream, flush, args.steps, args.warmup, local)
+    meas = measure(torch, _lib, synth, h, wl, dev, stream, flush, args.steps, args.warmup, local,
+                   autotune=not args.no_autotune)
     total_ms = sum(meas["times"])
     flops = 2.0 * wl.kept
     if world > 1:
@@ -552,7 +566,7 @@ def run_ours(args):
         "data": "synthetic (seeded R-MAT / Erdos-Renyi; the paper's SuiteSparse graphs are not used)",
         "config": cfg, "gpu_launches": int(meas["launches"]), "roofline": roof,
         "hbm_min_gbs": summary.get("hbm_min_gbs"), "phase_ms": summary.get("phase_ms"),
-        "clocks": meas["clocks"], "e2e": e2e, "gen_seconds": round(gen_s, 2),
+        "clocks": meas["clocks"], "e2e": e2e, "gen_seconds": round(gen_s, 2), "autotune_s": meas["autotune_s"],
     }
     if "push_products" in summary:
         line["push_gflops"] = round(2 * summary["push_products"] / (ms_per_step * 1e-3) / 1e9, 2)
@@ -578,7 +592,7 @@ def run_ours(args):
                 continue
             log(f"form: {name}")
             fw = build_workload(name, None, synth.BASE_SEED)
-            fm = measure(torch, _lib, synth, h, fw, dev, stream, flush, 5, 2, None)
+            fm = measure(torch, _lib, synth, h, fw, dev, stream, flush, 5, 2, None, autotune=not args.no_autotune)
             forms[name] = dict(config=fw.config["workload"], **form_summary(fw, fm))
             del fm
             torch.cuda.empty_cache()

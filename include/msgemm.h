@@ -86,12 +86,15 @@ typedef enum {
                                      their column tiles through a tile index of B
                                      (rows(B) x (tiles + 1) ints, built per call, 4 GiB cap);
                                      0, or a product over the cap, uses per-entry cursors */
-    MSGEMM_OPT_GRID = 6           /* value 0/1/2 (default 1): heavy complemented rows are
+    MSGEMM_OPT_GRID = 6,          /* value 0/1/2 (default 1): heavy complemented rows are
                                      processed as (row, column tile) items swept tile by tile
                                      over the whole GPU -- 1: rows whose output is dense (room
                                      n - nnz(M_i*) each), 2: every heavy complemented row,
                                      0: never (one CTA walks all tiles of a row); needs the
                                      tile index (or a single tile) */
+    MSGEMM_OPT_WARP_SLAB = 7      /* value 1024..24576, a multiple of 16 (default 4608): shared
+                                     bytes per warp of the one-warp row kinds (hash, MCA, pull);
+                                     rows whose table does not fit go to the one-CTA kinds */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

@@ -80,7 +80,13 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
     return K_MSA_T;
 }
 
-// One warp per row: flops, pull work, kind, temporary room.
+// Flops, pull work, kind and temporary room of every row.  A warp takes up
+// to 32 consecutive rows, one per lane: rows whose A row and (when pull is
+// possible) mask row have at most SHORT_ROW entries are summed by their own
+// lane; longer rows are then summed by the whole warp one at a time; finally
+// every lane picks its row's kind.
+constexpr int SHORT_ROW = 32;
+
 template <int SR>
 __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
                                                    const __grid_constant__ Policy pol, long long *room) {
@@ -90,27 +96,68 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
     const int lane = lane_id();
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long r = gw; r < ra.R; r += nw) {
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
-        const int i = (int)(r - P.row0);
-        const int a0 = __ldg(P.a_rp + i), a1 = __ldg(P.a_rp + i + 1);
-        const int m0 = __ldg(P.m_rp + i), m1 = __ldg(P.m_rp + i + 1);
-        long long f = 0;
-        for (int t = a0 + lane; t < a1; t += 32) {
-            const int k = __ldg(P.a_ci + t);
-            f += __ldg(P.b_rp + k + 1) - __ldg(P.b_rp + k);
+    // rows per warp and pass: 32, or fewer when there are few rows, so that
+    // few long rows still spread over many warps
+    const int W = (int)min(32LL, max(1LL, (ra.R + nw - 1) / nw));
+    for (long long r0 = gw * W; r0 < ra.R; r0 += nw * W) {
+        const long long r = r0 + lane;
+        const bool valid = lane < W && r < ra.R;
+        const int p = valid ? prod_of_row(ps, r) : 0;
+        const DevProd &P = prod_at(ps, p);
+        int a0 = 0, a1 = 0, m0 = 0, m1 = 0;
+        if (valid) {
+            const int i = (int)(r - P.row0);
+            a0 = __ldg(P.a_rp + i); a1 = __ldg(P.a_rp + i + 1);
+            m0 = __ldg(P.m_rp + i); m1 = __ldg(P.m_rp + i + 1);
         }
-        f = warp_sum_ll(f);
-        const bool dot_ok = !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
-        long long pull = 0;
-        if (dot_ok) {
-            for (int q = m0 + lane; q < m1; q += 32) {
-                const int j = __ldg(P.m_ci + q);
-                pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
+        const bool dot_ok = valid && !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
+        const bool is_short = a1 - a0 <= SHORT_ROW && (!dot_ok || m1 - m0 <= SHORT_ROW);
+        long long f = 0, pull = 0;
+        if (valid && is_short) {
+            for (int t = a0; t < a1; ++t) {
+                const int k = __ldg(P.a_ci + t);
+                f += __ldg(P.b_rp + k + 1) - __ldg(P.b_rp + k);
             }
-            pull = warp_sum_ll(pull);
+            if (dot_ok)
+                for (int q = m0; q < m1; ++q) {
+                    const int j = __ldg(P.m_ci + q);
+                    pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
+                }
         }
-        if (lane == 0) {
+        unsigned longs = __ballot_sync(FULL, valid && !is_short);
+        while (longs) {
+            const int u = __ffs(longs) - 1;
+            longs &= longs - 1;
+            const int pu = __shfl_sync(FULL, p, u);
+            const DevProd &Q = prod_at(ps, pu);
+            const int ua0 = __shfl_sync(FULL, a0, u), ua1 = __shfl_sync(FULL, a1, u);
+            const int um0 = __shfl_sync(FULL, m0, u), um1 = __shfl_sync(FULL, m1, u);
+            const bool udot = __shfl_sync(FULL, dot_ok, u);
+            // four entries per lane in flight: the row-pointer loads depend
+            // on the column loads, and long rows are latency-bound
+            auto lensum = [&](const int *idx, const int *rp, int q0, int q1) {
+                long long acc = 0;
+                for (int b = q0; b < q1; b += 128) {
+                    int c[4];
+#pragma unroll
+                    for (int x = 0; x < 4; ++x) {
+                        const int q = b + x * 32 + lane;
+                        c[x] = q < q1 ? __ldg(idx + q) : -1;
+                    }
+#pragma unroll
+                    for (int x = 0; x < 4; ++x)
+                        if (c[x] >= 0) acc += __ldg(rp + c[x] + 1) - __ldg(rp + c[x]);
+                }
+                return warp_sum_ll(acc);
+            };
+            const long long fu = lensum(Q.a_ci, Q.b_rp, ua0, ua1);
+            const long long pu_ = udot ? lensum(Q.m_ci, Q.bt_rp, um0, um1) : 0;
+            if (lane == u) {
+                f = fu;
+                pull = pu_;
+            }
+        }
+        if (valid) {
             const int mnz = m1 - m0;
             const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
             const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);

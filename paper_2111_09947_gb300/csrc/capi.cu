@@ -41,6 +41,7 @@ struct msgemm_handle {
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
+    int warp_slab = 4608;   // shared bytes per warp of the one-warp row kinds
     int *last_kind_count = nullptr;
     unsigned char *last_kind = nullptr;
     long long last_R = 0;
@@ -175,7 +176,7 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.dot_ratio = h->dot_ratio;
     p.warp_flops_max = h->warp_flops_max;
     const int acc = acc_bytes(sr);
-    const int wslab = 4608;   // per warp: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
+    const int wslab = h->warp_slab;   // default 4.5 KB: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
     const int bslab = 32 * 1024;  // per CTA-row: 7 CTAs per SM
     const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
     p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
@@ -339,12 +340,16 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
 
     // ---- B^T for the pull kernel: row pointers in the front of the sequence,
     // entries only if some row picked it.  Building B^T costs a pass over B;
-    // it pays only where the pull work (mask entries x average column length
-    // of B) is well below the push work (entries of A x average row length of
-    // B), or when DOT is forced.
+    // for one product it pays only where the pull work (mask entries x
+    // average column length of B) is well below the push work (entries of A
+    // x average row length of B), or when DOT is forced.  Batches always get
+    // the row pointers (one pass over all their B's together): averages miss
+    // the skew of graphs whose hubs are shared by A's columns and B's rows,
+    // where push work per row far exceeds the estimate, and the binning's
+    // exact per-row costs then decide.
     auto want_bt = [&](const ProdIn &x) {
         if (x.comp || x.bt_rp || !x.a_sorted) return false;
-        if (h->force == F_DOT) return true;
+        if (h->force == F_DOT || P > 1) return true;
         const double bnz = (double)x.B->nnz;
         const double push = (double)x.A->nnz * bnz / std::max(1, x.B->nrows);
         const double pull = (double)x.M->nnz * bnz / std::max(1, x.B->ncols);
@@ -742,6 +747,7 @@ msgemm_status check_product(msgemm_handle *h, const msgemm_csr *M, const msgemm_
 struct Tuned {
     int warp_flops_max = 65536;
     float dot_ratio = 2.0f;
+    int warp_slab = 4608;
     unsigned char pref[NCLASS][4];
 };
 
@@ -749,6 +755,7 @@ Tuned current_tuned(const msgemm_handle *h) {
     Tuned t;
     t.warp_flops_max = h->warp_flops_max;
     t.dot_ratio = h->dot_ratio;
+    t.warp_slab = h->warp_slab;
     memcpy(t.pref, h->pref, sizeof t.pref);
     return t;
 }
@@ -756,11 +763,12 @@ Tuned current_tuned(const msgemm_handle *h) {
 void apply_tuned(msgemm_handle *h, const Tuned &t) {
     h->warp_flops_max = t.warp_flops_max;
     h->dot_ratio = t.dot_ratio;
+    h->warp_slab = t.warp_slab;
     memcpy(h->pref, t.pref, sizeof t.pref);
 }
 
 // Cache file: a JSON object, one entry per line,
-//   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "pref": [[f,f,f,f], ...]}
+//   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "pref": [[f,f,f,f], ...]}
 // with NCLASS preference rows of accumulator families (msgemm_accumulator).
 void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
     FILE *f = fopen(path, "r");
@@ -782,15 +790,17 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ++c;
             }
         }
-        if (num.size() != 2 + NCLASS * 4) continue;
+        if (num.size() != 3 + NCLASS * 4) continue;
         Tuned t;
         if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
+        if (num[2] < 1024 || num[2] > 24576 || (int)num[2] % 16) continue;
         t.warp_flops_max = (int)num[0];
         t.dot_ratio = (float)num[1];
+        t.warp_slab = (int)num[2];
         bool ok = true;
         for (int c = 0; c < NCLASS; ++c)
             for (int x = 0; x < 4; ++x) {
-                const double v = num[2 + c * 4 + x];
+                const double v = num[3 + c * 4 + x];
                 ok &= v >= F_AUTO && v <= F_DOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
@@ -807,8 +817,8 @@ bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
     size_t i = 0;
     for (const auto &kv : m) {
         const Tuned &t = kv.second;
-        fprintf(f, "\"%s\": {\"warp_flops_max\": %d, \"dot_ratio\": %g, \"pref\": [", kv.first.c_str(),
-                t.warp_flops_max, (double)t.dot_ratio);
+        fprintf(f, "\"%s\": {\"warp_flops_max\": %d, \"dot_ratio\": %g, \"warp_slab\": %d, \"pref\": [",
+                kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab);
         for (int c = 0; c < NCLASS; ++c)
             fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
         fprintf(f, "]}%s\n", ++i < m.size() ? "," : "");
@@ -931,6 +941,16 @@ struct Tuner {
             if (t < best * keep) { best = t; wbest = w; }
         }
         h->warp_flops_max = wbest;
+        const int sbest0 = h->warp_slab;
+        int sbest = sbest0;
+        for (int sl : {3072, 3584, 4096, 4608, 6144, 9216}) {
+            if (sl == sbest0) continue;
+            h->warp_slab = sl;
+            float t;
+            CKS(measure(&t));
+            if (t < best * keep) { best = t; sbest = sl; }
+        }
+        h->warp_slab = sbest;
         if (h->allow_dot) {
             const float dbest0 = h->dot_ratio;
             float dbest = dbest0;
@@ -1003,6 +1023,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_DOT: h->allow_dot = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_PROFILE: h->profile = value != 0; return MSGEMM_OK;
     case MSGEMM_OPT_TILE_INDEX: h->tile_index = value != 0; return MSGEMM_OK;
+    case MSGEMM_OPT_WARP_SLAB:
+        if (value < 1024 || value > 24576 || value % 16) return fail(h, MSGEMM_ERR_INVALID, "warp slab bytes");
+        h->warp_slab = (int)value;
+        return MSGEMM_OK;
     case MSGEMM_OPT_GRID:
         if (value < 0 || value > 2) return fail(h, MSGEMM_ERR_INVALID, "grid mode is 0, 1 or 2");
         h->grid = (int)value;

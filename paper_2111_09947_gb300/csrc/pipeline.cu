@@ -699,34 +699,48 @@ namespace msg {
 // first position of row k whose column is >= t * T (the row end if none), so
 // the part of row k inside tile t is [tpos[t * nrows + k], tpos[(t + 1) *
 // nrows + k]).  Tile-major planes: kernels that sweep one tile for many rows
-// read one plane.  One warp per row; every slot is first set to the row end,
-// then each entry that starts a tile writes the slots of the tiles it opens
-// (rows are sorted).
+// read one plane.  One thread per row, the warp's 32 rows consecutive, planes
+// in order: each lane advances a cursor through its (sorted) row -- linearly
+// for short rows, by binary search from the cursor for long ones -- and the
+// warp writes 32 consecutive slots of a plane at a time.
 __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt,
                                                      int *tpos, const int *gate) {
     // gate = per-kind row counts
     if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0 && gate[K_CMSA_G] == 0) return;
-    const int lane = threadIdx.x & 31;
-    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long k = gw; k < nrows; k += nw) {
-        const int s = rp[k], e = rp[k + 1];
-        int *base = tpos + k;   // boundary t of row k at base[t * nrows]
-        for (int t = lane; t <= nt; t += 32) base[(long long)t * nrows] = e;
-        __syncwarp();
-        for (int q = s + lane; q < e; q += 32) {
-            const int tq = min(nt - 1, ci[q] / T);
-            const int tp = (q == s) ? -1 : min(nt - 1, ci[q - 1] / T);
-            for (int t = tp + 1; t <= tq; ++t) base[(long long)t * nrows] = q;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < nrows; k0 += stride) {
+        const long long k = k0 + threadIdx.x;
+        const bool valid = k < nrows;
+        int pos = valid ? rp[k] : 0;
+        const int e = valid ? rp[k + 1] : 0;
+        const bool longrow = e - pos > 64;
+        for (int t = 0; t <= nt; ++t) {
+            if (valid) {
+                if (t == nt) {
+                    pos = e;
+                } else {
+                    const long long lo_col = (long long)t * T;
+                    if (!longrow) {
+                        while (pos < e && ci[pos] < lo_col) ++pos;
+                    } else {
+                        int lo = pos, hi = e;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (ci[mid] < lo_col) lo = mid + 1; else hi = mid;
+                        }
+                        pos = lo;
+                    }
+                }
+                tpos[(long long)t * nrows + k] = pos;
+            }
         }
-        __syncwarp();
     }
 }
 
 cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, const int *gate,
                                cudaStream_t st, int nsm) {
     if (nrows == 0) return cudaSuccess;
-    k_tile_bounds<<<grid_cap(((long long)nrows + 7) / 8, nsm, 16), 256, 0, st>>>(rp, ci, nrows, T, nt, tpos, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_tile_bounds<<<grid_cap(((long long)nrows + 255) / 256, nsm, 16), 256, 0, st>>>(rp, ci, nrows, T, nt, tpos, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 

@@ -41,6 +41,7 @@ cudaError_t go(const ProdSet &ps, const RowLaunch &L, int threads, size_t smem, 
 cudaError_t MSG_CAT(launch_bin_score_, MSG_SUFFIX)(const ProdSet &ps, const RowArrays &ra, const Policy &pol,
                                                    long long *room, cudaStream_t st, int nsm) {
     if (ra.R == 0) return cudaSuccess;
+    // up to one warp per row; the kernel packs up to 32 rows per warp when rows outnumber warps
     const long long blocks = std::min<long long>((ra.R + 7) / 8, (long long)nsm * 16);
     k_bin_score<MSG_SR><<<(int)blocks, 256, 0, st>>>(ps, ra, pol, room); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
