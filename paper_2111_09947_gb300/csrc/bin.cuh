@@ -80,12 +80,55 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
     return K_MSA_T;
 }
 
+// Kind, flops and temporary room of row r, and the per-CTA kind histogram.
+template <int SR>
+__device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra, const Policy &pol, long long *room,
+                                           int *hist, long long r, int a0, int a1, int m0, int m1, bool dot_ok,
+                                           long long f, long long pull) {
+    const int mnz = m1 - m0;
+    const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
+    const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
+    ra.flops[r] = f;
+    ra.kind[r] = (unsigned char)kind;
+    ra.cnt[r] = 0;
+    if (!P.complement) {
+        ra.tmpoff[r] = P.tmp0 + m0;
+        room[r] = 0;
+    } else {
+        room[r] = (kind == K_EMPTY) ? 0 : kind == K_CMSA_G ? (long long)(P.n - mnz) : min(f, (long long)(P.n - mnz));
+    }
+    atomicAdd(&hist[kind], 1);
+    if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;
+}
+
+// Sum over idx[q0..q1) of the row length rp[c + 1] - rp[c], by the whole warp
+// with four entries per lane in flight (the row-pointer loads depend on the
+// column loads, and long rows are latency-bound).
+__device__ __forceinline__ long long warp_len_sum(const int *idx, const int *rp, int q0, int q1) {
+    const int lane = lane_id();
+    long long acc = 0;
+    for (int b = q0; b < q1; b += 128) {
+        int c[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int q = b + x * 32 + lane;
+            c[x] = q < q1 ? __ldg(idx + q) : -1;
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if (c[x] >= 0) acc += __ldg(rp + c[x] + 1) - __ldg(rp + c[x]);
+    }
+    return warp_sum_ll(acc);
+}
+
 // Flops, pull work, kind and temporary room of every row.  A warp takes up
 // to 32 consecutive rows, one per lane: rows whose A row and (when pull is
 // possible) mask row have at most SHORT_ROW entries are summed by their own
-// lane; longer rows are then summed by the whole warp one at a time; finally
-// every lane picks its row's kind.
+// lane; longer rows up to LONG_ROW entries are then summed by the whole warp
+// one at a time; rows beyond go to a list that k_bin_long sums with a whole
+// CTA each.  Every lane then picks its row's kind.
 constexpr int SHORT_ROW = 32;
+constexpr int LONG_ROW = 1024;
 
 template <int SR>
 __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
@@ -112,6 +155,7 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
         }
         const bool dot_ok = valid && !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
         const bool is_short = a1 - a0 <= SHORT_ROW && (!dot_ok || m1 - m0 <= SHORT_ROW);
+        const bool is_huge = a1 - a0 > LONG_ROW || (dot_ok && m1 - m0 > LONG_ROW);
         long long f = 0, pull = 0;
         if (valid && is_short) {
             for (int t = a0; t < a1; ++t) {
@@ -124,55 +168,75 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
                     pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
                 }
         }
-        unsigned longs = __ballot_sync(FULL, valid && !is_short);
+        if (valid && is_huge) ra.perm[atomicAdd(ra.nlong, 1)] = (int)r;   // to k_bin_long
+        unsigned longs = __ballot_sync(FULL, valid && !is_short && !is_huge);
         while (longs) {
             const int u = __ffs(longs) - 1;
             longs &= longs - 1;
-            const int pu = __shfl_sync(FULL, p, u);
-            const DevProd &Q = prod_at(ps, pu);
+            const DevProd &Q = prod_at(ps, __shfl_sync(FULL, p, u));
             const int ua0 = __shfl_sync(FULL, a0, u), ua1 = __shfl_sync(FULL, a1, u);
             const int um0 = __shfl_sync(FULL, m0, u), um1 = __shfl_sync(FULL, m1, u);
             const bool udot = __shfl_sync(FULL, dot_ok, u);
-            // four entries per lane in flight: the row-pointer loads depend
-            // on the column loads, and long rows are latency-bound
-            auto lensum = [&](const int *idx, const int *rp, int q0, int q1) {
-                long long acc = 0;
-                for (int b = q0; b < q1; b += 128) {
-                    int c[4];
-#pragma unroll
-                    for (int x = 0; x < 4; ++x) {
-                        const int q = b + x * 32 + lane;
-                        c[x] = q < q1 ? __ldg(idx + q) : -1;
-                    }
-#pragma unroll
-                    for (int x = 0; x < 4; ++x)
-                        if (c[x] >= 0) acc += __ldg(rp + c[x] + 1) - __ldg(rp + c[x]);
-                }
-                return warp_sum_ll(acc);
-            };
-            const long long fu = lensum(Q.a_ci, Q.b_rp, ua0, ua1);
-            const long long pu_ = udot ? lensum(Q.m_ci, Q.bt_rp, um0, um1) : 0;
+            const long long fu = warp_len_sum(Q.a_ci, Q.b_rp, ua0, ua1);
+            const long long pu = udot ? warp_len_sum(Q.m_ci, Q.bt_rp, um0, um1) : 0;
             if (lane == u) {
                 f = fu;
-                pull = pu_;
+                pull = pu;
             }
         }
-        if (valid) {
-            const int mnz = m1 - m0;
-            const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
-            const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
-            ra.flops[r] = f;
-            ra.kind[r] = (unsigned char)kind;
-            ra.cnt[r] = 0;
-            if (!P.complement) {
-                ra.tmpoff[r] = P.tmp0 + m0;
-                room[r] = 0;
-            } else {
-                room[r] = (kind == K_EMPTY) ? 0 : kind == K_CMSA_G ? (long long)(P.n - mnz) : min(f, (long long)(P.n - mnz));
-            }
-            atomicAdd(&hist[kind], 1);
-            if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;
+        if (valid && !is_huge) finish_row<SR>(P, ra, pol, room, hist, r, a0, a1, m0, m1, dot_ok, f, pull);
+    }
+    __syncthreads();
+    for (int x = threadIdx.x; x < NKIND; x += blockDim.x)
+        if (hist[x]) atomicAdd(&ra.kind_count[x], hist[x]);
+}
+
+// The listed rows (more than LONG_ROW entries), one CTA per row: each warp
+// sums a share of the row, the CTA adds the shares.  The list lives in
+// ra.perm, which k_bin_scatter fills only afterwards.
+template <int SR>
+__global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
+                                                  const __grid_constant__ Policy pol, long long *room) {
+    __shared__ int hist[NKIND];
+    __shared__ long long part[2][8];
+    for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
+    __syncthreads();
+    const int nlong = *ra.nlong;
+    const int w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int x = blockIdx.x; x < nlong; x += gridDim.x) {
+        const long long r = ra.perm[x];
+        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const int i = (int)(r - P.row0);
+        const int a0 = __ldg(P.a_rp + i), a1 = __ldg(P.a_rp + i + 1);
+        const int m0 = __ldg(P.m_rp + i), m1 = __ldg(P.m_rp + i + 1);
+        const bool dot_ok = !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
+        auto share = [&](int q0, int q1, int &s0, int &s1) {   // warp w's contiguous share
+            const long long len = q1 - q0, per = (len + nwarp - 1) / nwarp;
+            s0 = (int)min((long long)q1, q0 + per * w);
+            s1 = (int)min((long long)q1, (long long)s0 + per);
+        };
+        int s0, s1;
+        share(a0, a1, s0, s1);
+        const long long f = warp_len_sum(P.a_ci, P.b_rp, s0, s1);
+        long long pull = 0;
+        if (dot_ok) {
+            share(m0, m1, s0, s1);
+            pull = warp_len_sum(P.m_ci, P.bt_rp, s0, s1);
         }
+        if (lane_id() == 0) {
+            part[0][w] = f;
+            part[1][w] = pull;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long ft = 0, pt = 0;
+            for (int q = 0; q < nwarp; ++q) {
+                ft += part[0][q];
+                pt += part[1][q];
+            }
+            finish_row<SR>(P, ra, pol, room, hist, r, a0, a1, m0, m1, dot_ok, ft, pt);
+        }
+        __syncthreads();
     }
     __syncthreads();
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x)

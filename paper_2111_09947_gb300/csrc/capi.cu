@@ -330,6 +330,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     ra.kind_next = cs.take<int>(NKIND);
     ra.kind_off = cs.take<int>(NKIND + 1);
     ra.any_dot = cs.take<int>(1);
+    ra.nlong = cs.take<int>(1);
     ra.bound_total = cs.take<long long>(1);
     pl.L.gnext = cs.take<unsigned long long>(1);
     pl.L.gnt = pl.gnt;

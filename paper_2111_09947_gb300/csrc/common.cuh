@@ -95,6 +95,7 @@ struct RowArrays {
     int *kind_next;         // [NKIND] dynamic work cursors (heavy kinds)
     long long *bound_total; // complemented: total temporary room
     int *any_dot;           // set when a row picked the pull kernel
+    int *nlong;             // binning: rows listed for the one-CTA-per-row pass
     unsigned *err;          // device error word
 };
 

@@ -44,6 +44,10 @@ cudaError_t MSG_CAT(launch_bin_score_, MSG_SUFFIX)(const ProdSet &ps, const RowA
     // up to one warp per row; the kernel packs up to 32 rows per warp when rows outnumber warps
     const long long blocks = std::min<long long>((ra.R + 7) / 8, (long long)nsm * 16);
     k_bin_score<MSG_SR><<<(int)blocks, 256, 0, st>>>(ps, ra, pol, room); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // rows longer than LONG_ROW entries, listed by the pass above
+    k_bin_long<MSG_SR><<<nsm * 4, 256, 0, st>>>(ps, ra, pol, room); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
