@@ -34,7 +34,7 @@ struct msgemm_handle {
     msgemm_free_fn free_fn = nullptr;
     void *ctx = nullptr;
     // workspace, reused across calls
-    Buf rows, small, tmp, bt, cur, prods, tix, gbuf;
+    Buf rows, small, tmp, bt, cur, prods, tix, gbuf, thi;
     unsigned *d_err = nullptr;   // in `small`, persistent
     int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
     long long tile_index_budget = 4LL << 30;   // bytes
@@ -185,7 +185,7 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.slab[K_MSA_W] = msaw <= 24 * 1024 ? (int)msaw : 0;
     p.slab[K_MSA_T] = p.slab[K_CMSA_T] = p.slab[K_CMSA_G] = tslab;
     p.grid = h->grid;
-    p.tileT[0] = p.tileT[1] = msa_tile_width(tslab, acc);
+    p.tileT[0] = p.tileT[1] = msa_tile_width(tslab, TILE_ACC_BYTES);
     memcpy(p.pref, h->pref, sizeof p.pref);
     return p;
 }
@@ -255,6 +255,7 @@ struct Plan {
     std::vector<int> nts;
     std::vector<int *> tpos;
     int gnt = 0;   // CMSA_G: most column tiles of a complemented product
+    size_t thi_bytes = 0;   // int64 tiled kinds: high-word arrays to zero
     RowLaunch L{};
     std::vector<int> kinds;
 };
@@ -432,6 +433,16 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         }
     }
 
+    // ---- int64 tiled kinds: a high-word array per resident CTA (one CTA per
+    // SM: their slab takes the SM's shared memory), zeroed by every call
+    if (sr == MSGEMM_PLUS_TIMES_I64) {
+        const size_t bytes = (size_t)h->nsm * pl.pol.tileT[0] * sizeof(unsigned);
+        CKS(grow(h, h->thi, bytes));
+        pl.L.tile_hi = static_cast<unsigned *>(h->thi.p);
+        pl.L.tile_hi_slots = h->nsm;
+        pl.thi_bytes = bytes;
+    }
+
     // ---- accumulator kinds to launch
     bool any_plain = false;
     for (int p = 0; p < P; ++p) any_plain |= !in[p].comp;
@@ -466,6 +477,7 @@ msgemm_status plan_upload(msgemm_handle *h, Plan &pl) {
 msgemm_status seq_front(msgemm_handle *h, Plan &pl) {
     cudaStream_t st = h->stream;
     CK(cudaMemsetAsync(pl.zero_begin, 0, pl.zero_bytes, st));
+    if (pl.thi_bytes) CK(cudaMemsetAsync(pl.L.tile_hi, 0, pl.thi_bytes, st));
     if (!pl.bd.empty()) {
         PScope ph(h, "bt_counts");
         CK(launch_bt_counts_multi(pl.bt_tab, (int)pl.bd.size(), pl.bt_nnz, pl.bt_cur, pl.bt_counts, st, h->nsm));
@@ -1282,7 +1294,8 @@ void msgemm_destroy(msgemm_handle *h) {
     }
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix, &h->gbuf}) dev_free(h, b->p);
+    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix, &h->gbuf, &h->thi})
+        dev_free(h, b->p);
     delete h;
 }
 

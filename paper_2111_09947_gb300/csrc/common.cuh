@@ -194,6 +194,57 @@ __device__ __forceinline__ typename Sr<SR>::in_t load_val(const void *base, long
     }
 }
 
+// Accumulator of the column-tiled MSA kinds.  int64 keeps only the low
+// 32-bit word per column in shared memory (so its tiles are as wide as the
+// 32-bit semirings'); the high word lives in a per-CTA global array `hi` of
+// one word per tile column, touched only by products whose high half is
+// non-zero and by low-word carries.  As for the two-word shared add, every
+// wrap of the low word is counted once by the add that caused it, so
+// lo + 2^32 hi is the exact sum mod 2^64 in any order.  `get` reads a column,
+// `clear` zeroes it (both words), `take` does both.  hi is read through L2:
+// its words are changed by global atomics.
+template <int SR> struct TileAcc {
+    using acc_t = typename Sr<SR>::acc_t;
+    using lo_t = acc_t;
+    static constexpr bool split = false;
+    __device__ static __forceinline__ void add(lo_t *lo, unsigned *, int jj, acc_t v) { Sr<SR>::add(&lo[jj], v); }
+    __device__ static __forceinline__ acc_t get(const lo_t *lo, const unsigned *, int jj) { return lo[jj]; }
+    __device__ static __forceinline__ void clear(lo_t *lo, unsigned *, int jj) { lo[jj] = 0; }
+    __device__ static __forceinline__ acc_t take(lo_t *lo, unsigned *, int jj) {
+        const acc_t v = lo[jj];
+        lo[jj] = 0;
+        return v;
+    }
+};
+template <> struct TileAcc<MSGEMM_PLUS_TIMES_I64> {
+    using acc_t = unsigned long long;
+    using lo_t = unsigned;
+    static constexpr bool split = true;
+    __device__ static __forceinline__ void add(lo_t *lo, unsigned *hi, int jj, acc_t v) {
+        const unsigned l = (unsigned)v;
+        const unsigned old = atomicAdd(&lo[jj], l);
+        const unsigned h = (unsigned)(v >> 32) + (old + l < old ? 1u : 0u);
+        if (h) atomicAdd(&hi[jj], h);
+    }
+    __device__ static __forceinline__ acc_t get(const lo_t *lo, const unsigned *hi, int jj) {
+        return ((acc_t)__ldcg(hi + jj) << 32) | lo[jj];
+    }
+    __device__ static __forceinline__ void clear(lo_t *lo, unsigned *hi, int jj) {
+        lo[jj] = 0;
+        if (__ldcg(hi + jj)) hi[jj] = 0;
+    }
+    __device__ static __forceinline__ acc_t take(lo_t *lo, unsigned *hi, int jj) {
+        const unsigned h = __ldcg(hi + jj);
+        const acc_t v = ((acc_t)h << 32) | lo[jj];
+        lo[jj] = 0;
+        if (h) hi[jj] = 0;
+        return v;
+    }
+};
+// Shared bytes per column of a tiled accumulator's value array: 4 for every
+// semiring (fp32, 32-bit plus-pair counts, the low word of int64).
+constexpr int TILE_ACC_BYTES = 4;
+
 template <int SR> struct SrSizes {
     static constexpr int acc = sizeof(typename Sr<SR>::acc_t);
     static constexpr int in = Sr<SR>::vals ? (int)sizeof(typename Sr<SR>::in_t) : 0;

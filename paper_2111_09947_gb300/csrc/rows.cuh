@@ -32,7 +32,22 @@ struct RowLaunch {
     int *gcnt, *goff, *gdone;
     unsigned long long *gnext;
     int gnt;
+    // int64 tiled kinds: high words, tileT per CTA (CTA b at tile_hi + b * tileT)
+    unsigned *tile_hi;
+    int tile_hi_slots;
 };
+
+// This CTA's high-word array of the tiled kinds (null unless split int64);
+// a grid larger than the workspace flags an error and gets null.
+template <int SR>
+__device__ __forceinline__ unsigned *tile_hi_of(const RowLaunch &L) {
+    if constexpr (!TileAcc<SR>::split) {
+        return nullptr;
+    } else {
+        if ((int)blockIdx.x >= L.tile_hi_slots || !L.tile_hi) return nullptr;
+        return L.tile_hi + (size_t)blockIdx.x * L.tileT;
+    }
+}
 
 template <int SR>
 __device__ __forceinline__ typename Sr<SR>::in_t shfl_val(typename Sr<SR>::in_t v, int src) {
@@ -549,12 +564,19 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
     using acc_t = typename S::acc_t;
     using in_t = typename S::in_t;
     using out_t = typename S::out_t;
+    using TA = TileAcc<SR>;
+    using lo_t = typename TA::lo_t;
     Team<true> team;
     const int lane = lane_id();
     const int T = L.tileT;
-    acc_t *vals = reinterpret_cast<acc_t *>(slab);
-    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(acc_t)));
+    lo_t *vals = reinterpret_cast<lo_t *>(slab);
+    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(lo_t)));
     unsigned *setw = mbits + words32(T);
+    unsigned *hi = tile_hi_of<SR>(L);
+    if (TA::split && !hi) {   // uniform over the CTA
+        if (threadIdx.x == 0) atomicOr(L.ra.err, ERR_INTERNAL);
+        return;
+    }
     const int n = c.n;
     const int ntiles = (n + T - 1) / T;
     // Column tiles come from the product's tile index when it has one (exact
@@ -603,7 +625,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             }
             const bool m = test_bit(mbits, jj);
             if (m != COMP) {   // plain: allowed iff in mask; complemented: iff not
-                S::add(&vals[jj], S::mul(a, b));
+                TA::add(vals, hi, jj, S::mul(a, b));
                 if constexpr (COMP || SrSizes<SR>::setbits) set_bit_once(setw, jj);
             }
         };
@@ -706,7 +728,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             for (int r0 = s0; r0 < s1; r0 += 32) {
                 const int q = r0 + lane;
                 const bool keep = q < s1 && kept(__ldg(P.m_ci + q) - c0);
-                if (L.aligned && keep) tv[c.tmp + (q - c.m0)] = S::out(vals[__ldg(P.m_ci + q) - c0]);
+                if (L.aligned && keep) tv[c.tmp + (q - c.m0)] = S::out(TA::get(vals, hi, __ldg(P.m_ci + q) - c0));
                 cw += __popc(__ballot_sync(FULL, keep));
             }
             int total;
@@ -724,7 +746,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                 if (keep && !L.aligned) {
                     const long long o = c.tmp + base + __popc(bal & lanemask_lt());
                     L.tmp.ci[o] = j;
-                    tv[o] = S::out(vals[j - c0]);
+                    tv[o] = S::out(TA::get(vals, hi, j - c0));
                 }
                 base += __popc(bal);
             }
@@ -732,7 +754,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
             for (int q = s0 + lane; q < s1; q += 32) {
                 const int jj = __ldg(P.m_ci + q) - c0;
                 if ((unsigned)jj >= (unsigned)T) continue;
-                vals[jj] = 0;
+                TA::clear(vals, hi, jj);
                 mbits[jj >> 5] = 0;
                 setw[jj >> 5] = 0;
             }
@@ -754,8 +776,7 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                     bits &= bits - 1;
                     const int jj = w * 32 + b;
                     L.tmp.ci[o] = c0 + jj;
-                    tv[o] = S::out(vals[jj]);
-                    vals[jj] = 0;
+                    tv[o] = S::out(TA::take(vals, hi, jj));
                     ++o;
                 }
                 setw[w] = 0;
@@ -859,11 +880,14 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
     using acc_t = typename S::acc_t;
     using in_t = typename S::in_t;
     using out_t = typename S::out_t;
+    using TA = TileAcc<SR>;
+    using lo_t = typename TA::lo_t;
     Team<true> team;
     const int T = L.tileT;
-    acc_t *vals = reinterpret_cast<acc_t *>(slab);
-    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(acc_t)));
+    lo_t *vals = reinterpret_cast<lo_t *>(slab);
+    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(lo_t)));
     unsigned *setw = mbits + words32(T);
+    unsigned *hi = tile_hi_of<SR>(L);   // checked by the caller
     const int c0 = tile * T, c1 = min(c.n, c0 + T);
     for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
         const int jj = __ldg(P.m_ci + q) - c0;
@@ -877,7 +901,7 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
             return;
         }
         if (!test_bit(mbits, jj)) {
-            S::add(&vals[jj], S::mul(a, b));
+            TA::add(vals, hi, jj, S::mul(a, b));
             set_bit_once(setw, jj);
         }
     };
@@ -907,8 +931,7 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
             bits &= bits - 1;
             const int jj = w * 32 + b;
             L.tmp.ci[o] = c0 + jj;
-            tv[o] = S::out(vals[jj]);
-            vals[jj] = 0;
+            tv[o] = S::out(TA::take(vals, hi, jj));
             ++o;
         }
         setw[w] = 0;
@@ -966,6 +989,10 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
     const int count = L.ra.kind_count[K_CMSA_G];
     const int off = L.ra.kind_off[K_CMSA_G];
     const int T = L.tileT;
+    if (TileAcc<SR>::split && !tile_hi_of<SR>(L)) {   // uniform over the CTA
+        if (threadIdx.x == 0 && count > 0) atomicOr(L.ra.err, ERR_INTERNAL);
+        return;
+    }
     {   // zero the tile arrays once; every item leaves them zeroed
         unsigned *w = reinterpret_cast<unsigned *>(smem);
         for (int x = threadIdx.x; x < L.slab / 4; x += blockDim.x) w[x] = 0;

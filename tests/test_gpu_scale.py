@@ -140,7 +140,7 @@ def test_tiled_rows_index_and_cursor_paths(handle, tile_index):
     index of B (default) and through per-entry cursors (fallback)."""
     handle.set_option(_lib.OPT_TILE_INDEX, tile_index)
     try:
-        p = synth.bfs_step(scale=16, ef=16, nsrc=256, seed=29)        # 65536 columns: 3 int64 tiles
+        p = synth.bfs_step(scale=16, ef=16, nsrc=256, seed=29)        # 65536 columns: 2 tiles
         ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64", complement=True, method=O.ESC)
         handle.force("msa")
         d = to_dev(p, "plus_times_i64")
@@ -186,8 +186,8 @@ def _varied_rows(m, k, n, a_deg, m_deg, seed, gen):
 def test_complemented_heavy_rows_grid_modes(handle, grid, semiring):
     """Heavy complemented rows: one CTA walking every tile of a row (grid 0),
     the tile-major grid of (row, tile) items for dense-output rows (1) or for
-    every heavy row (2).  130000 columns: 3 fp32 tiles, 5 int64 tiles, both
-    with a partial last one.  A's rows give 400 to 240000 products (sparse to
+    every heavy row (2).  130000 columns: 3 tiles of 52000 columns (every
+    semiring keeps 4 bytes per column in shared memory), the last partial.  A's rows give 400 to 240000 products (sparse to
     dense outputs); masks range from empty to half the columns."""
     gen = {"plus_times_i64": "i64", "plus_times_f32": "f32", "plus_pair_i64": "pair"}[semiring]
     q = _varied_rows(240, 3000, 130000, (1, 60, 600, 10, 300), (0, 2000, 65000, 50, 9000, 120000), 61, gen)
@@ -223,3 +223,30 @@ def test_bfs_grid_rows_scale16(handle):
     handle.sync_status()
     assert handle.bin_counts()["cmsa_g"] > 0
     assert_parity(res, ref, "plus_times_i64", ctx="bfs scale 16 grid")
+
+
+@pytest.mark.parametrize("grid", [0, 2])
+@pytest.mark.parametrize("complement", [False, True])
+def test_int64_tiled_high_words(handle, grid, complement):
+    """int64 through the column-tiled kinds, whose shared memory keeps only
+    each column's low word: values near +-2^50 make every product carry a
+    non-zero high half, sums wrap mod 2^64, and the high words must come back
+    exactly and be cleared for the next row and call."""
+    rng = np.random.default_rng(71 + grid + 2 * complement)
+    q = _varied_rows(160, 2000, 120000, (3, 40, 400), (0, 900, 60000, 20), 72 + grid, "i64")
+    big = np.int64(1) << np.int64(50)
+    q["A"] = q["A"].with_values(rng.integers(-big, big, q["A"].nnz, dtype=np.int64))
+    q["B"] = q["B"].with_values(rng.integers(-(1 << 12), 1 << 12, q["B"].nnz, dtype=np.int64))
+    method = O.ESC if complement else O.MERGE
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], "plus_times_i64", complement=complement, method=method)
+    handle.set_option(_lib.OPT_GRID, grid)
+    try:
+        handle.force("msa")
+        dq = to_dev(q, "plus_times_i64")
+        for rep in range(2):
+            res = _lib.msgemm_run(handle, dq["M"], dq["A"], dq["B"], "plus_times_i64", complement=complement).trimmed()
+            handle.sync_status()
+            assert_parity(res, ref, "plus_times_i64", ctx=f"grid={grid} complement={complement} rep={rep}")
+    finally:
+        handle.force("auto")
+        handle.set_option(_lib.OPT_GRID, 1)
