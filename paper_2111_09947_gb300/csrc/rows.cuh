@@ -139,25 +139,39 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
                     if (col[x] >= 0) f(tbase + nw * u, au, col[x], bv[x]);
             }
         }
-        // short ranges: load-balanced flat enumeration
+        // short ranges: load-balanced flat enumeration, two products per lane
+        // per pass (both searches and both loads in flight together)
         const int sl = len < LONG_SEG ? len : 0;
         const int incl = warp_incl_scan(sl);
         const int total = __shfl_sync(FULL, incl, 31);
         const int excl = incl - sl;
-        for (int base = 0; base < total; base += 32) {
-            const int p = base + lane;
-            int k = 0;
+        for (int base = 0; base < total; base += 64) {
+            const int p0 = base + lane, p1 = p0 + 32;
+            int k0 = 0, k1 = 0;
 #pragma unroll
             for (int st = 16; st > 0; st >>= 1) {
-                const int cc = __shfl_sync(FULL, incl, k + st - 1);
-                if (cc <= p) k += st;
+                const int c0 = __shfl_sync(FULL, incl, k0 + st - 1);
+                const int c1 = __shfl_sync(FULL, incl, k1 + st - 1);
+                if (c0 <= p0) k0 += st;
+                if (c1 <= p1) k1 += st;
             }
-            const int sk = __shfl_sync(FULL, s, k & 31), xk = __shfl_sync(FULL, excl, k & 31);
-            const in_t ak = shfl_val<SR>(av, k & 31);
-            if (p < total) {
-                const int q = sk + p - xk;
-                f(tbase + nw * k, ak, __ldg(ici + q), load_val<SR>(iv, q));
+            k0 &= 31;
+            k1 &= 31;
+            const int q0 = __shfl_sync(FULL, s, k0) + p0 - __shfl_sync(FULL, excl, k0);
+            const int q1 = __shfl_sync(FULL, s, k1) + p1 - __shfl_sync(FULL, excl, k1);
+            const in_t a0 = shfl_val<SR>(av, k0), a1 = shfl_val<SR>(av, k1);
+            int col0 = -1, col1 = -1;
+            in_t b0{}, b1{};
+            if (p0 < total) {
+                col0 = __ldg(ici + q0);
+                b0 = load_val<SR>(iv, q0);
             }
+            if (p1 < total) {
+                col1 = __ldg(ici + q1);
+                b1 = load_val<SR>(iv, q1);
+            }
+            if (p0 < total) f(tbase + nw * k0, a0, col0, b0);
+            if (p1 < total) f(tbase + nw * k1, a1, col1, b1);
         }
     }
 }
