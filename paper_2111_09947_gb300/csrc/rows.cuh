@@ -97,6 +97,38 @@ struct TileSeg {
 #endif
 constexpr int LONG_SEG = MSG_LONG_SEG;
 
+// The walk of one range [s, e) by the whole warp, chunks of 128 entries
+// (4 loads per lane in flight), from chunk c0 in steps of cstep chunks.
+template <int SR, class F>
+__device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
+                                           const int *__restrict__ ici, const void *iv, F &f) {
+    using in_t = typename Sr<SR>::in_t;
+    const int lane = lane_id();
+    for (long long q0 = s + 128LL * c0; q0 < e; q0 += 128LL * cstep) {
+        int col[4];
+        in_t bv[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const long long q = q0 + x * 32 + lane;
+            col[x] = -1;
+            if (q < e) {
+                col[x] = __ldg(ici + q);
+                bv[x] = load_val<SR>(iv, q);
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if (col[x] >= 0) f(t, a, col[x], bv[x]);
+    }
+}
+
+// CTA teams: ranges of BIG_SEG or more entries (hub rows of B) are not walked
+// by the warp that meets them but listed, and after the windows every warp
+// takes chunks of every listed range, so one hub does not hold the team's
+// next barrier; a full list falls back to the warp walk.
+constexpr int BIG_SEG = 2048;
+constexpr int BIG_LIST = 128;
+
 template <int SR, bool CTA, bool OUTV, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
                                               const Seg &seg, const int *__restrict__ ici, const void *iv, F &f) {
@@ -105,6 +137,13 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
     const int lane = lane_id();
     const int nw = team.nwarps(), wq = team.warp();
     const int cnt = o1 - o0;
+    __shared__ int s_nbig;
+    __shared__ int s_big[CTA ? BIG_LIST : 1][3];
+    __shared__ in_t s_biga[CTA ? BIG_LIST : 1];
+    if constexpr (CTA) {
+        if (threadIdx.x == 0) s_nbig = 0;
+        __syncthreads();
+    }
     for (int b0 = 0; wq + nw * b0 < cnt; b0 += 32) {
         const int t = o0 + wq + nw * (b0 + lane);
         int s = 0, e = 0;
@@ -115,29 +154,27 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
         }
         const int tbase = o0 + wq + nw * b0;   // outer position of lane 0's entry
         const int len = max(0, e - s);         // an unsorted row can give e < s in a tile index
-        // long ranges: cooperative walk
-        unsigned lmask = __ballot_sync(FULL, len >= LONG_SEG);
+        // long ranges: cooperative walk (CTA teams list the biggest)
+        bool listed = false;
+        if constexpr (CTA) {
+            if (len >= BIG_SEG) {
+                const int slot = atomicAdd(&s_nbig, 1);
+                if (slot < BIG_LIST) {
+                    s_big[slot][0] = t;
+                    s_big[slot][1] = s;
+                    s_big[slot][2] = e;
+                    s_biga[slot] = av;
+                    listed = true;
+                }
+            }
+        }
+        unsigned lmask = __ballot_sync(FULL, len >= LONG_SEG && !listed);
         while (lmask) {
             const int u = __ffs(lmask) - 1;
             lmask &= lmask - 1;
             const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
             const in_t au = shfl_val<SR>(av, u);
-            for (int q0 = su; q0 < eu; q0 += 128) {
-                int col[4];
-                in_t bv[4];
-#pragma unroll
-                for (int x = 0; x < 4; ++x) {
-                    const int q = q0 + x * 32 + lane;
-                    col[x] = -1;
-                    if (q < eu) {
-                        col[x] = __ldg(ici + q);
-                        bv[x] = load_val<SR>(iv, q);
-                    }
-                }
-#pragma unroll
-                for (int x = 0; x < 4; ++x)
-                    if (col[x] >= 0) f(tbase + nw * u, au, col[x], bv[x]);
-            }
+            walk_range<SR>(tbase + nw * u, au, su, eu, 0, 1, ici, iv, f);
         }
         // short ranges: load-balanced flat enumeration, two products per lane
         // per pass (both searches and both loads in flight together)
@@ -173,6 +210,20 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             if (p0 < total) f(tbase + nw * k0, a0, col0, b0);
             if (p1 < total) f(tbase + nw * k1, a1, col1, b1);
         }
+    }
+    if constexpr (CTA) {
+        // listed ranges: their 128-entry chunks, concatenated, dealt to the
+        // warps round-robin
+        __syncthreads();
+        const int nb = min(s_nbig, BIG_LIST);
+        long long g = 0;   // chunks of the ranges before this one
+        for (int i = 0; i < nb; ++i) {
+            const int s0 = s_big[i][1], e0 = s_big[i][2];
+            const int first = (int)(((long long)wq - g % nw + nw) % nw);
+            walk_range<SR>(s_big[i][0], s_biga[i], s0, e0, first, nw, ici, iv, f);
+            g += (e0 - s0 + 127) / 128;
+        }
+        __syncthreads();   // the list is reused by the team's next call
     }
 }
 
