@@ -938,11 +938,14 @@ __global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet 
 // the tile: the number of columns before the tile that the mask leaves open
 // (these rows get n - nnz(M_i*) slots of room).  The CTA that completes a
 // row's last item packs the row's pieces to the front of its room.
+// One item: the tile's column states are two bits per column in one word
+// array (bit 0 NOTALLOWED -- the mask's columns --, bit 1 SET), so a product
+// reads one word to learn both, and sets SET only on its column's first
+// product.
 template <int SR>
 __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab,
                                          int *scratch, int tile, int ntiles, int mq0, int mq1, long long obase) {
     using S = Sr<SR>;
-    using acc_t = typename S::acc_t;
     using in_t = typename S::in_t;
     using out_t = typename S::out_t;
     using TA = TileAcc<SR>;
@@ -950,13 +953,12 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
     Team<true> team;
     const int T = L.tileT;
     lo_t *vals = reinterpret_cast<lo_t *>(slab);
-    unsigned *mbits = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(lo_t)));
-    unsigned *setw = mbits + words32(T);
+    unsigned *st = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(lo_t)));   // T / 16 words
     unsigned *hi = tile_hi_of<SR>(L);   // checked by the caller
     const int c0 = tile * T, c1 = min(c.n, c0 + T);
     for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
         const int jj = __ldg(P.m_ci + q) - c0;
-        if ((unsigned)jj < (unsigned)T) atomicOr(&mbits[jj >> 5], 1u << (jj & 31));
+        if ((unsigned)jj < (unsigned)T) atomicOr(&st[jj >> 4], 1u << (2 * (jj & 15)));
         else atomicOr(L.ra.err, ERR_INTERNAL);
     }
     cta_sync();
@@ -965,9 +967,10 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
             atomicOr(L.ra.err, ERR_INTERNAL);
             return;
         }
-        if (!test_bit(mbits, jj)) {
+        const unsigned w = st[jj >> 4] >> (2 * (jj & 15));
+        if (!(w & 1u)) {
             TA::add(vals, hi, jj, S::mul(a, b));
-            set_bit_once(setw, jj);
+            if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
         }
     };
     if (ntiles == 1) {
@@ -979,32 +982,28 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
         enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, f);
     }
     cta_sync();
-    // gather the SET columns in ascending order; each thread owns a run of words
-    const int nwords = (int)words32(c1 - c0);
+    // gather the SET columns in ascending order; each thread owns a run of
+    // state words (16 columns each), and clears them
+    const int nwords = (c1 - c0 + 15) >> 4;
     const int per = (nwords + team.size() - 1) / team.size();
     const int w0 = min(nwords, team.tid() * per), w1 = min(nwords, w0 + per);
     int cw = 0;
-    for (int w = w0; w < w1; ++w) cw += __popc(setw[w]);
+    for (int w = w0; w < w1; ++w) cw += __popc((st[w] >> 1) & 0x55555555u);
     int total;
     const int off = block_excl_scan(cw, scratch, &total);
     long long o = obase + off;
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     for (int w = w0; w < w1; ++w) {
-        unsigned bits = setw[w];
+        unsigned bits = (st[w] >> 1) & 0x55555555u;
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
-            const int jj = w * 32 + b;
+            const int jj = w * 16 + (b >> 1);
             L.tmp.ci[o] = c0 + jj;
             tv[o] = S::out(TA::take(vals, hi, jj));
             ++o;
         }
-        setw[w] = 0;
-    }
-    cta_sync();
-    for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
-        const int jj = __ldg(P.m_ci + q) - c0;
-        if ((unsigned)jj < (unsigned)T) mbits[jj >> 5] = 0;
+        st[w] = 0;
     }
     return total;
 }
