@@ -83,8 +83,8 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
 // Kind, flops and temporary room of row r, and the per-CTA kind histogram.
 template <int SR>
 __device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra, const Policy &pol, long long *room,
-                                           int *hist, long long r, int a0, int a1, int m0, int m1, bool dot_ok,
-                                           long long f, long long pull) {
+                                           int *hist, int *hsub, long long r, int a0, int a1, int m0, int m1,
+                                           bool dot_ok, long long f, long long pull) {
     const int mnz = m1 - m0;
     const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
     const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
@@ -98,7 +98,15 @@ __device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra
         room[r] = (kind == K_EMPTY) ? 0 : kind == K_CMSA_G ? (long long)(P.n - mnz) : min(f, (long long)(P.n - mnz));
     }
     atomicAdd(&hist[kind], 1);
+    atomicAdd(&hsub[kind * NCLS_FLOPS + flops_sub(f)], 1);
     if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;
+}
+
+__device__ __forceinline__ void flush_hist(const RowArrays &ra, const int *hist, const int *hsub) {
+    for (int x = threadIdx.x; x < NKIND; x += blockDim.x)
+        if (hist[x]) atomicAdd(&ra.kind_count[x], hist[x]);
+    for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x)
+        if (hsub[x]) atomicAdd(&ra.sub_count[x], hsub[x]);
 }
 
 // Sum over idx[q0..q1) of the row length rp[c + 1] - rp[c], by the whole warp
@@ -134,7 +142,9 @@ template <int SR>
 __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
                                                    const __grid_constant__ Policy pol, long long *room) {
     __shared__ int hist[NKIND];
+    __shared__ int hsub[NKIND * NCLS_FLOPS];
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
+    for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x) hsub[x] = 0;
     __syncthreads();
     const int lane = lane_id();
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -184,11 +194,10 @@ __global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdS
                 pull = pu;
             }
         }
-        if (valid && !is_huge) finish_row<SR>(P, ra, pol, room, hist, r, a0, a1, m0, m1, dot_ok, f, pull);
+        if (valid && !is_huge) finish_row<SR>(P, ra, pol, room, hist, hsub, r, a0, a1, m0, m1, dot_ok, f, pull);
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < NKIND; x += blockDim.x)
-        if (hist[x]) atomicAdd(&ra.kind_count[x], hist[x]);
+    flush_hist(ra, hist, hsub);
 }
 
 // The listed rows (more than LONG_ROW entries), one CTA per row: each warp
@@ -198,8 +207,10 @@ template <int SR>
 __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
                                                   const __grid_constant__ Policy pol, long long *room) {
     __shared__ int hist[NKIND];
+    __shared__ int hsub[NKIND * NCLS_FLOPS];
     __shared__ long long part[2][8];
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
+    for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x) hsub[x] = 0;
     __syncthreads();
     const int nlong = *ra.nlong;
     const int w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
@@ -234,13 +245,12 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
                 ft += part[0][q];
                 pt += part[1][q];
             }
-            finish_row<SR>(P, ra, pol, room, hist, r, a0, a1, m0, m1, dot_ok, ft, pt);
+            finish_row<SR>(P, ra, pol, room, hist, hsub, r, a0, a1, m0, m1, dot_ok, ft, pt);
         }
         __syncthreads();
     }
     __syncthreads();
-    for (int x = threadIdx.x; x < NKIND; x += blockDim.x)
-        if (hist[x]) atomicAdd(&ra.kind_count[x], hist[x]);
+    flush_hist(ra, hist, hsub);
 }
 
 }  // namespace msg

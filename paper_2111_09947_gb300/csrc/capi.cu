@@ -332,6 +332,8 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     ra.kind_off = cs.take<int>(NKIND + 1);
     ra.any_dot = cs.take<int>(1);
     ra.nlong = cs.take<int>(1);
+    ra.sub_count = cs.take<int>(NKIND * NCLS_FLOPS);
+    ra.sub_fill = cs.take<int>(NKIND * NCLS_FLOPS);
     ra.bound_total = cs.take<long long>(1);
     pl.L.gnext = cs.take<unsigned long long>(1);
     pl.L.gnt = pl.gnt;
@@ -1003,7 +1005,7 @@ msgemm_status msgemm_create(msgemm_handle **handle, void *stream, msgemm_alloc_f
         delete h;
         return MSGEMM_ERR_CUDA;
     }
-    if (grow(h, h->small, 8192) != MSGEMM_OK) {
+    if (grow(h, h->small, 16384) != MSGEMM_OK) {
         delete h;
         return MSGEMM_ERR_OOM;
     }

@@ -96,6 +96,8 @@ struct RowArrays {
     long long *bound_total; // complemented: total temporary room
     int *any_dot;           // set when a row picked the pull kernel
     int *nlong;             // binning: rows listed for the one-CTA-per-row pass
+    int *sub_count;         // [NKIND * NCLS_FLOPS] rows per (kind, flops class)
+    int *sub_fill;          // [NKIND * NCLS_FLOPS] scatter cursors
     unsigned *err;          // device error word
 };
 
@@ -105,6 +107,14 @@ struct TmpOut {
     int *ci;
     void *v;
 };
+
+// Rows of a kind are listed heaviest first by flops class: class
+// NCLS_FLOPS - 1 - min(NCLS_FLOPS - 1, floor(log2 flops)) ascending.
+constexpr int NCLS_FLOPS = 32;
+__device__ __forceinline__ int flops_sub(long long f) {
+    const int lg = 63 - __clzll((unsigned long long)f | 1ULL);
+    return NCLS_FLOPS - 1 - min(NCLS_FLOPS - 1, lg);
+}
 
 // Per-kind shared-memory budget and preference lists used by binning.
 constexpr int NCLASS = 16;

@@ -17,30 +17,37 @@ static int grid_cap(long long work_blocks, int nsm, int per_sm) {
 }
 
 // ------------------------------------------------------------ bucket scatter
-// perm holds the rows grouped by kind; within a kind the order is arbitrary.
+// perm holds the rows grouped by kind and, within a kind, by flops class
+// heaviest first (the order the row kernels take them in); within a class the
+// order is arbitrary.
+constexpr int NSUB = NKIND * NCLS_FLOPS;
 __global__ void __launch_bounds__(256) k_bin_scatter(const __grid_constant__ RowArrays ra) {
-    __shared__ int off[NKIND + 1];
-    __shared__ int loc[NKIND];
-    __shared__ int base[NKIND];
+    __shared__ int off[NSUB + 1];
+    __shared__ int loc[NSUB];
+    __shared__ int base[NSUB];
     if (threadIdx.x == 0) {
         off[0] = 0;
-        for (int k = 0; k < NKIND; ++k) off[k + 1] = off[k] + ra.kind_count[k];
+        for (int k = 0; k < NSUB; ++k) off[k + 1] = off[k] + ra.sub_count[k];
         if (blockIdx.x == 0)
-            for (int k = 0; k <= NKIND; ++k) ra.kind_off[k] = off[k];
+            for (int k = 0; k <= NKIND; ++k) ra.kind_off[k] = off[k * NCLS_FLOPS];
     }
     for (long long r0 = (long long)blockIdx.x * blockDim.x; r0 < ra.R; r0 += (long long)gridDim.x * blockDim.x) {
-        if (threadIdx.x < NKIND) loc[threadIdx.x] = 0;
+        for (int x = threadIdx.x; x < NSUB; x += blockDim.x) loc[x] = 0;
         __syncthreads();
         const long long r = r0 + threadIdx.x;
-        int k = -1, rank = 0;
+        int key = -1, rank = 0;
         if (r < ra.R) {
-            k = ra.kind[r];
-            if (k != K_EMPTY) rank = atomicAdd(&loc[k], 1);
+            const int k = ra.kind[r];
+            if (k != K_EMPTY) {
+                key = k * NCLS_FLOPS + flops_sub(ra.flops[r]);
+                rank = atomicAdd(&loc[key], 1);
+            }
         }
         __syncthreads();
-        if (threadIdx.x < NKIND && loc[threadIdx.x]) base[threadIdx.x] = atomicAdd(&ra.kind_fill[threadIdx.x], loc[threadIdx.x]);
+        for (int x = threadIdx.x; x < NSUB; x += blockDim.x)
+            if (loc[x]) base[x] = atomicAdd(&ra.sub_fill[x], loc[x]);
         __syncthreads();
-        if (k > K_EMPTY) ra.perm[off[k] + base[k] + rank] = (int)r;
+        if (key >= 0) ra.perm[off[key] + base[key] + rank] = (int)r;
         __syncthreads();
     }
 }

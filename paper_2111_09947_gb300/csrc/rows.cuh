@@ -871,8 +871,13 @@ __global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet 
         for (int x = lane_id(); x < L.slab / 4; x += 32) reinterpret_cast<unsigned *>(slab)[x] = 0;
         __syncwarp();
     }
-    const int nwarp = gridDim.x * (blockDim.x >> 5);
-    for (int x = blockIdx.x * (blockDim.x >> 5) + wib; x < count; x += nwarp) {
+    // rows from a device counter, one per warp at a time (the bucket lists
+    // heavy rows first): no warp is left with a tail of heavy rows
+    for (;;) {
+        int x = 0;
+        if (lane_id() == 0) x = atomicAdd(&L.ra.kind_next[KIND], 1);
+        x = __shfl_sync(FULL, x, 0);
+        if (x >= count) break;
         const long long r = L.ra.perm[off + x];
         const DevProd &P = prod_at(ps, prod_of_row(ps, r));
         const RowCtx c = row_ctx(P, r, L.ra);
@@ -888,9 +893,16 @@ template <int SR, int KIND>
 __global__ void __launch_bounds__(256) k_rows_b(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int scratch[40];
+    __shared__ int s_row;
     const int count = L.ra.kind_count[KIND];
     const int off = L.ra.kind_off[KIND];
-    for (int x = blockIdx.x; x < count; x += gridDim.x) {
+    // rows from a device counter, heavy rows first (bucket order)
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_row = atomicAdd(&L.ra.kind_next[KIND], 1);
+        __syncthreads();
+        const int x = s_row;
+        if (x >= count) break;
         const long long r = L.ra.perm[off + x];
         const DevProd &P = prod_at(ps, prod_of_row(ps, r));
         const RowCtx c = row_ctx(P, r, L.ra);
