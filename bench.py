@@ -410,10 +410,19 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
     def collect():
         for name, ms in h.profile():
             per_phase.setdefault(name, []).append(ms)
+    def sync_all():
+        # every rank enters and leaves the timed region together
+        torch.cuda.synchronize()
+        import torch.distributed as dist
+        if dist.is_available() and dist.is_initialized():
+            dist.barrier()
+        torch.cuda.synchronize()
+    sync_all()
     # profiler range = the timed region (for ncu --profile-from-start off; no effect otherwise)
     torch.cuda.profiler.start()
     times = timed_steps(torch, run.step, steps, flush, stream, after=collect)
     torch.cuda.profiler.stop()
+    sync_all()
     launches = _lib.load().msgemm_kernel_launches() - l0
     clk = clocks.stop() if clocks else None
     out = {"times": times, "launches": launches, "clocks": clk, "per_phase": per_phase, "kinds": kinds, "run": run,
