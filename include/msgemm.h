@@ -86,15 +86,21 @@ typedef enum {
                                      their column tiles through a tile index of B
                                      (rows(B) x (tiles + 1) ints, built per call, 4 GiB cap);
                                      0, or a product over the cap, uses per-entry cursors */
-    MSGEMM_OPT_GRID = 6,          /* value 0/1/2 (default 1): heavy complemented rows are
-                                     processed as (row, column tile) items swept tile by tile
-                                     over the whole GPU -- 1: rows whose output is dense (room
-                                     n - nnz(M_i*) each), 2: every heavy complemented row,
+    MSGEMM_OPT_GRID = 6,          /* value 0/1/2 (default 1): heavy rows are processed as
+                                     (row, column tile) items swept tile by tile over the whole
+                                     GPU -- 1: complemented rows whose output is dense (room
+                                     n - nnz(M_i*) each) and plain rows over the flop bound of
+                                     MSGEMM_OPT_GRID_MIN_FLOPS, 2: every heavy row (tests),
                                      0: never (one CTA walks all tiles of a row); needs the
                                      tile index (or a single tile) */
-    MSGEMM_OPT_WARP_SLAB = 7      /* value 1024..24576, a multiple of 16 (default 4608): shared
+    MSGEMM_OPT_WARP_SLAB = 7,     /* value 1024..24576, a multiple of 16 (default 4608): shared
                                      bytes per warp of the one-warp row kinds (hash, MCA, pull);
                                      rows whose table does not fit go to the one-CTA kinds */
+    MSGEMM_OPT_GRID_MIN_FLOPS = 8 /* value >= 0 (default 2^20): plain-mask rows with at least
+                                     this many push products, in products wider than one
+                                     column tile, are processed as (row, tile) items over the
+                                     whole GPU (at most 4096 such rows per call; the rest and
+                                     every lighter row keep one CTA or warp per row) */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

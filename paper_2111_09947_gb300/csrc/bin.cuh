@@ -57,13 +57,19 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
         if (flops == 0 || bound <= 0) return K_EMPTY;
         // heavy rows: the grid of (row, tile) items when the output is dense
         // (its room is then all open columns, at most 4x the bound)
-        const int heavy = (pol.grid > 0 && index_ok && (pol.grid == 2 || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
+        const int heavy = (pol.grid > 0 && index_ok && (n + pol.tileT[1] - 1) / pol.tileT[1] <= GRID_MAX_TILES &&
+                           (pol.grid == 2 || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
         if (pol.force == F_MSA) return heavy;
         if (warp && pol.slab[K_CHASH_W] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_W])) return K_CHASH_W;
         if (pol.slab[K_CHASH_B] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_B])) return K_CHASH_B;
         return heavy;
     }
     if (flops == 0 || mnz == 0) return K_EMPTY;
+    // heaviest rows of products wider than a tile: (row, tile) items over the GPU
+    const bool grid_ok = pol.grid > 0 && !warp && index_ok && n > pol.tileT[0] &&
+                         (n + pol.tileT[0] - 1) / pol.tileT[0] <= GRID_MAX_TILES;
+    if (grid_ok && (pol.grid == 2 ? (pol.force == F_AUTO || pol.force == F_MSA) : flops >= pol.grid_min_flops))
+        return K_MSA_G;
     if (pol.force != F_AUTO) {
         const int k = pick_family<SR>(pol, pol.force, warp, flops, mnz, anz, n, dot_ok, true);
         return k >= 0 ? k : K_MSA_T;
@@ -87,7 +93,8 @@ __device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra
                                            bool dot_ok, long long f, long long pull) {
     const int mnz = m1 - m0;
     const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
-    const int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
+    int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
+    if (kind == K_MSA_G && atomicAdd(ra.gplain, 1) >= GRID_PLAIN_CAP) kind = K_MSA_T;   // piece tables are full
     ra.flops[r] = f;
     ra.kind[r] = (unsigned char)kind;
     ra.cnt[r] = 0;

@@ -34,7 +34,7 @@ struct msgemm_handle {
     msgemm_free_fn free_fn = nullptr;
     void *ctx = nullptr;
     // workspace, reused across calls
-    Buf rows, small, tmp, bt, cur, prods, tix, gbuf, thi;
+    Buf rows, small, tmp, bt, cur, prods, tix, gbuf, thi, gpbuf;
     unsigned *d_err = nullptr;   // in `small`, persistent
     int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
     long long tile_index_budget = 4LL << 30;   // bytes
@@ -42,6 +42,7 @@ struct msgemm_handle {
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
     int warp_slab = 4608;   // shared bytes per warp of the one-warp row kinds
+    long long grid_min_flops = 1LL << 20;   // MSA_G: plain CTA rows with at least this push work
     int *last_kind_count = nullptr;
     unsigned char *last_kind = nullptr;
     long long last_R = 0;
@@ -137,7 +138,7 @@ struct PScope {
 
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
-                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g"};
+                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -183,8 +184,9 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;
     const long long msaw = (msa_bytes(max_n, acc) + 15) & ~15LL;
     p.slab[K_MSA_W] = msaw <= 24 * 1024 ? (int)msaw : 0;
-    p.slab[K_MSA_T] = p.slab[K_CMSA_T] = p.slab[K_CMSA_G] = tslab;
+    p.slab[K_MSA_T] = p.slab[K_CMSA_T] = p.slab[K_CMSA_G] = p.slab[K_MSA_G] = tslab;
     p.grid = h->grid;
+    p.grid_min_flops = h->grid_min_flops;
     p.tileT[0] = p.tileT[1] = msa_tile_width(tslab, TILE_ACC_BYTES);
     memcpy(p.pref, h->pref, sizeof p.pref);
     return p;
@@ -254,7 +256,8 @@ struct Plan {
     // tile index of B for column-tiled products (nts[p] tiles, 0 = untiled)
     std::vector<int> nts;
     std::vector<int *> tpos;
-    int gnt = 0;   // CMSA_G: most column tiles of a complemented product
+    int gnt = 0;   // grid kinds: most column tiles of a product
+    size_t gp_done_bytes = 0;   // MSA_G: per-row completion counts to zero
     size_t thi_bytes = 0;   // int64 tiled kinds: high-word arrays to zero
     RowLaunch L{};
     std::vector<int> kinds;
@@ -292,7 +295,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         pl.any_comp |= x.comp != 0;
         max_n = std::max(max_n, d.n);
         if (d.n > pol0.tileT[x.comp ? 1 : 0]) any_tiled = true;
-        if (x.comp) pl.gnt = std::max(pl.gnt, (d.n + pol0.tileT[1] - 1) / pol0.tileT[1]);
+        pl.gnt = std::max(pl.gnt, std::min(GRID_MAX_TILES, (d.n + pol0.tileT[0] - 1) / pol0.tileT[0]));
         if (x.C) {
             d.c_rp = x.C->rowptr; d.c_ci = x.C->colidx; d.c_v = x.C->values; d.c_nnz = reinterpret_cast<long long *>(x.C->d_nnz);
             if (!x.comp) pl.cap += x.C->capacity;
@@ -335,7 +338,9 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     ra.sub_count = cs.take<int>(NKIND * NCLS_FLOPS);
     ra.sub_fill = cs.take<int>(NKIND * NCLS_FLOPS);
     ra.bound_total = cs.take<long long>(1);
-    pl.L.gnext = cs.take<unsigned long long>(1);
+    pl.L.g[0].next = cs.take<unsigned long long>(1);
+    pl.L.g[1].next = cs.take<unsigned long long>(1);
+    ra.gplain = cs.take<int>(1);
     pl.L.gnt = pl.gnt;
     pl.zero_bytes = (size_t)(cs.base + cs.off - pl.zero_begin);
     h->last_kind_count = ra.kind_count;
@@ -445,6 +450,22 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         pl.thi_bytes = bytes;
     }
 
+    // ---- MSA_G piece tables: sized by the row cap (binning assigns at most
+    // GRID_PLAIN_CAP rows to the kind), so no host synchronisation is needed
+    {
+        bool plain_wide = false;
+        for (int p = 0; p < P; ++p) plain_wide |= !in[p].comp && dp[p].n > pl.pol.tileT[0];
+        if (plain_wide && h->grid > 0) {
+            const size_t slots = (size_t)GRID_PLAIN_CAP * pl.gnt;
+            CKS(grow(h, h->gpbuf, carve_size<int>(slots) * 2 + carve_size<int>(GRID_PLAIN_CAP)));
+            Carver cg(h->gpbuf.p);
+            pl.L.g[0].cnt = cg.take<int>(slots);
+            pl.L.g[0].off = cg.take<int>(slots);
+            pl.L.g[0].done = cg.take<int>(GRID_PLAIN_CAP);
+            pl.gp_done_bytes = sizeof(int) * (size_t)GRID_PLAIN_CAP;
+        }
+    }
+
     // ---- accumulator kinds to launch
     bool any_plain = false;
     for (int p = 0; p < P; ++p) any_plain |= !in[p].comp;
@@ -455,6 +476,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
             std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
             pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
         pl.kinds.push_back(K_MSA_T);
+        if (pl.L.g[0].cnt) pl.kinds.push_back(K_MSA_G);
     }
     if (pl.any_comp) pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T, K_CMSA_G});
 
@@ -480,6 +502,7 @@ msgemm_status seq_front(msgemm_handle *h, Plan &pl) {
     cudaStream_t st = h->stream;
     CK(cudaMemsetAsync(pl.zero_begin, 0, pl.zero_bytes, st));
     if (pl.thi_bytes) CK(cudaMemsetAsync(pl.L.tile_hi, 0, pl.thi_bytes, st));
+    if (pl.gp_done_bytes) CK(cudaMemsetAsync(pl.L.g[0].done, 0, pl.gp_done_bytes, st));
     if (!pl.bd.empty()) {
         PScope ph(h, "bt_counts");
         CK(launch_bt_counts_multi(pl.bt_tab, (int)pl.bd.size(), pl.bt_nnz, pl.bt_cur, pl.bt_counts, st, h->nsm));
@@ -512,10 +535,10 @@ msgemm_status comp_room(msgemm_handle *h, Plan &pl) {
         const size_t slots = (size_t)ng * pl.gnt;
         CKS(grow(h, h->gbuf, carve_size<int>(slots) * 2 + carve_size<int>(ng)));
         Carver cg(h->gbuf.p);
-        pl.L.gcnt = cg.take<int>(slots);
-        pl.L.goff = cg.take<int>(slots);
-        pl.L.gdone = cg.take<int>(ng);
-        CK(cudaMemsetAsync(pl.L.gdone, 0, sizeof(int) * (size_t)ng, st));
+        pl.L.g[1].cnt = cg.take<int>(slots);
+        pl.L.g[1].off = cg.take<int>(slots);
+        pl.L.g[1].done = cg.take<int>(ng);
+        CK(cudaMemsetAsync(pl.L.g[1].done, 0, sizeof(int) * (size_t)ng, st));
     }
     const long long tmp_entries = pl.tmpn + comp_total;
     const int ob = out_bytes(pl.sr);
@@ -550,7 +573,7 @@ msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
     }
     RowLaunch L = pl.L;
     for (int kd : pl.kinds) {
-        if (kd == K_MSA_T || kd == K_CMSA_T || kd == K_CMSA_G) {
+        if (kd == K_MSA_T || kd == K_CMSA_T || kd == K_CMSA_G || kd == K_MSA_G) {
             PScope ph(h, "sort_heavy");
             CK(launch_sort_heavy(ra, kd, st));
         }
@@ -763,6 +786,7 @@ struct Tuned {
     int warp_flops_max = 65536;
     float dot_ratio = 2.0f;
     int warp_slab = 4608;
+    long long grid_min_flops = 1LL << 20;
     unsigned char pref[NCLASS][4];
 };
 
@@ -771,6 +795,7 @@ Tuned current_tuned(const msgemm_handle *h) {
     t.warp_flops_max = h->warp_flops_max;
     t.dot_ratio = h->dot_ratio;
     t.warp_slab = h->warp_slab;
+    t.grid_min_flops = h->grid_min_flops;
     memcpy(t.pref, h->pref, sizeof t.pref);
     return t;
 }
@@ -779,11 +804,13 @@ void apply_tuned(msgemm_handle *h, const Tuned &t) {
     h->warp_flops_max = t.warp_flops_max;
     h->dot_ratio = t.dot_ratio;
     h->warp_slab = t.warp_slab;
+    h->grid_min_flops = t.grid_min_flops;
     memcpy(h->pref, t.pref, sizeof t.pref);
 }
 
 // Cache file: a JSON object, one entry per line,
-//   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "pref": [[f,f,f,f], ...]}
+//   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "grid_min_flops": G,
+//                                "pref": [[f,f,f,f], ...]}
 // with NCLASS preference rows of accumulator families (msgemm_accumulator).
 void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
     FILE *f = fopen(path, "r");
@@ -805,17 +832,19 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ++c;
             }
         }
-        if (num.size() != 3 + NCLASS * 4) continue;
+        if (num.size() != 4 + NCLASS * 4) continue;
         Tuned t;
         if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
         if (num[2] < 1024 || num[2] > 24576 || (int)num[2] % 16) continue;
         t.warp_flops_max = (int)num[0];
         t.dot_ratio = (float)num[1];
         t.warp_slab = (int)num[2];
+        if (num[3] < 0 || num[3] > 9.3e18) continue;
+        t.grid_min_flops = (long long)num[3];
         bool ok = true;
         for (int c = 0; c < NCLASS; ++c)
             for (int x = 0; x < 4; ++x) {
-                const double v = num[3 + c * 4 + x];
+                const double v = num[4 + c * 4 + x];
                 ok &= v >= F_AUTO && v <= F_DOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
@@ -832,8 +861,8 @@ bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
     size_t i = 0;
     for (const auto &kv : m) {
         const Tuned &t = kv.second;
-        fprintf(f, "\"%s\": {\"warp_flops_max\": %d, \"dot_ratio\": %g, \"warp_slab\": %d, \"pref\": [",
-                kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab);
+        fprintf(f, "\"%s\": {\"warp_flops_max\": %d, \"dot_ratio\": %g, \"warp_slab\": %d, \"grid_min_flops\": %lld, \"pref\": [",
+                kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab, t.grid_min_flops);
         for (int c = 0; c < NCLASS; ++c)
             fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
         fprintf(f, "]}%s\n", ++i < m.size() ? "," : "");
@@ -966,6 +995,16 @@ struct Tuner {
             if (t < best * keep) { best = t; sbest = sl; }
         }
         h->warp_slab = sbest;
+        const long long gbest0 = h->grid_min_flops;
+        long long gbest = gbest0;
+        for (long long g : {1LL << 18, 1LL << 20, 1LL << 22, 1LL << 62}) {
+            if (g == gbest0) continue;
+            h->grid_min_flops = g;
+            float t;
+            CKS(measure(&t));
+            if (t < best * keep) { best = t; gbest = g; }
+        }
+        h->grid_min_flops = gbest;
         if (h->allow_dot) {
             const float dbest0 = h->dot_ratio;
             float dbest = dbest0;
@@ -1041,6 +1080,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_WARP_SLAB:
         if (value < 1024 || value > 24576 || value % 16) return fail(h, MSGEMM_ERR_INVALID, "warp slab bytes");
         h->warp_slab = (int)value;
+        return MSGEMM_OK;
+    case MSGEMM_OPT_GRID_MIN_FLOPS:
+        if (value < 0) return fail(h, MSGEMM_ERR_INVALID, "grid flop bound must be >= 0");
+        h->grid_min_flops = value;
         return MSGEMM_OK;
     case MSGEMM_OPT_GRID:
         if (value < 0 || value > 2) return fail(h, MSGEMM_ERR_INVALID, "grid mode is 0, 1 or 2");
@@ -1296,7 +1339,7 @@ void msgemm_destroy(msgemm_handle *h) {
     }
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
-    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix, &h->gbuf, &h->thi})
+    for (Buf *b : {&h->rows, &h->small, &h->tmp, &h->bt, &h->cur, &h->prods, &h->tix, &h->gbuf, &h->thi, &h->gpbuf})
         dev_free(h, b->p);
     delete h;
 }

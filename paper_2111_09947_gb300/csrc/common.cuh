@@ -32,6 +32,7 @@ enum Kind : int {
     K_CHASH_B,
     K_CMSA_T,      // complemented: MSA with NOTALLOWED default flipped, tiled
     K_CMSA_G,      // complemented, dense output: (row, tile) items over the whole grid, tile-major
+    K_MSA_G,       // plain, heaviest rows of wide products: (row, tile) items, tile-major
     NKIND
 };
 
@@ -96,6 +97,7 @@ struct RowArrays {
     long long *bound_total; // complemented: total temporary room
     int *any_dot;           // set when a row picked the pull kernel
     int *nlong;             // binning: rows listed for the one-CTA-per-row pass
+    int *gplain;            // MSA_G rows assigned so far (capped at GRID_PLAIN_CAP)
     int *sub_count;         // [NKIND * NCLS_FLOPS] rows per (kind, flops class)
     int *sub_fill;          // [NKIND * NCLS_FLOPS] scatter cursors
     unsigned *err;          // device error word
@@ -116,6 +118,12 @@ __device__ __forceinline__ int flops_sub(long long f) {
     return NCLS_FLOPS - 1 - min(NCLS_FLOPS - 1, lg);
 }
 
+// Most MSA_G rows per call: their piece tables are sized on the host before
+// binning, by this cap (rows beyond it take MSA_T).
+constexpr int GRID_PLAIN_CAP = 4096;
+// Most column tiles of a product for the grid kinds (beyond: one CTA per row).
+constexpr int GRID_MAX_TILES = 4096;
+
 // Per-kind shared-memory budget and preference lists used by binning.
 constexpr int NCLASS = 16;
 struct Policy {
@@ -125,7 +133,8 @@ struct Policy {
     int warp_flops_max;           // rows above go to CTA-level kinds
     int slab[NKIND];              // bytes per warp (_W) or per CTA (_B, _T); 0 = disabled
     int tileT[2];                 // MSA_T tile width for [plain, complemented]
-    int grid;                     // CMSA_G: 0 off, 1 for dense-output rows, 2 for every heavy complemented row
+    int grid;                     // grid kinds: 0 off, 1 by the rules below, 2 for every heavy row
+    long long grid_min_flops;     // MSA_G: CTA rows with at least this much push work (grid 1)
     unsigned char pref[NCLASS][4];  // families in preference order (F_AUTO = end)
 };
 

@@ -31,7 +31,7 @@ inline int kind_threads(int kind) {
     switch (kind) {
     case K_MSA_W: return 128;
     case K_MSA_T: case K_CMSA_T: return 512;
-    case K_CMSA_G: return 1024;
+    case K_CMSA_G: case K_MSA_G: return 1024;
     default: return 256;
     }
 }

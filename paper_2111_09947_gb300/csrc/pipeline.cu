@@ -713,7 +713,7 @@ namespace msg {
 __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt,
                                                      int *tpos, const int *gate) {
     // gate = per-kind row counts
-    if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0 && gate[K_CMSA_G] == 0) return;
+    if (gate && gate[K_MSA_T] == 0 && gate[K_CMSA_T] == 0 && gate[K_CMSA_G] == 0 && gate[K_MSA_G] == 0) return;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k0 = (long long)blockIdx.x * blockDim.x; k0 < nrows; k0 += stride) {
         const long long k = k0 + threadIdx.x;

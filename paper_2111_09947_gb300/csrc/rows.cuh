@@ -19,6 +19,11 @@ constexpr unsigned long long EMPTY64 = ~0ULL;
 constexpr unsigned EMPTY32 = 0xffffffffu;
 
 // Launch parameters of one accumulator kernel.
+struct GridTab {
+    int *cnt, *off, *done;
+    unsigned long long *next;
+};
+
 struct RowLaunch {
     RowArrays ra;
     TmpOut tmp;
@@ -27,10 +32,10 @@ struct RowLaunch {
     int4 *cursors;     // _T kinds: one cursor per stored entry of A (global)
     int aligned;       // 1: write values only, at the mask entry's own slot (tmp + rank);
                        //    the output array is zeroed beforehand (gradient form)
-    // CMSA_G items: per (row of the kind, tile) entry count and offset in the
-    // row, per-row completed items, item cursor, tiles per row slot (max)
-    int *gcnt, *goff, *gdone;
-    unsigned long long *gnext;
+    // grid kinds ([0] MSA_G, [1] CMSA_G): per (row of the kind, tile) entry
+    // count and offset in the row, per-row completed items, item cursor;
+    // tiles per row slot (the most of any product)
+    GridTab g[2];
     int gnt;
     // int64 tiled kinds: high words, tileT per CTA (CTA b at tile_hi + b * tileT)
     unsigned *tile_hi;
@@ -938,27 +943,59 @@ __global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet 
     }
 }
 
-// ------------------------------------------- complemented MSA, grid of tiles
-// Heavy complemented rows with dense output (their reachable columns are at
-// least a quarter of those the mask leaves open).  Work items are (row,
-// column tile) pairs handed out tile-major: the CTAs of the whole GPU sweep
-// one column tile at a time, so that tile's slice of B and of the tile index
-// stays in L2 while every such row passes over it, instead of each row
-// streaming all of B from HBM.  An item is Sec. 5.2's MSA on one tile with
-// the complemented default (the mask's columns NOTALLOWED, all others
-// ALLOWED) and writes its entries, ascending, at the row's exact offset for
-// the tile: the number of columns before the tile that the mask leaves open
-// (these rows get n - nnz(M_i*) slots of room).  The CTA that completes a
-// row's last item packs the row's pieces to the front of its room.
-// One item: the tile's column states are two bits per column in one word
-// array (bit 0 NOTALLOWED -- the mask's columns --, bit 1 SET), so a product
-// reads one word to learn both, and sets SET only on its column's first
-// product.
-template <int SR>
-__device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab,
+// ------------------------------------------------------ MSA, grid of tiles
+// Heavy rows as (row, column tile) items swept tile-major over the whole GPU:
+// complemented rows with dense output (CMSA_G: their reachable columns are at
+// least a quarter of those the mask leaves open), and plain rows with the
+// most push work in products wider than one tile (MSA_G), which one CTA per
+// row would leave most SMs idle for.  Items go out tile-major from a device
+// counter: the CTAs of the whole GPU sweep one column tile at a time, so that
+// tile's slice of B and of the tile index stays in L2 while every such row
+// passes over it, instead of each row streaming all of B from HBM.  An item
+// is Sec. 5.2's MSA on one tile and writes its entries, ascending, at the
+// row's exact offset for the tile: for a plain mask the mask entries before
+// the tile (the row's room is its mask row); complemented, the columns before
+// the tile that the mask leaves open (room n - nnz(M_i*)).  The CTA that
+// completes a row's last item (a device-scope count after a fence; nothing
+// waits) packs the row's pieces to the front of its room.
+
+// Insertion of product (j, a*b) into a grid item's tile.  Column state bits:
+// bit 0 the mask (ALLOWED for a plain mask, NOTALLOWED when complemented),
+// bit 1 SET; two bits per column in one word array, so a product reads one
+// word to learn both.  A product is added when the mask allows it, and marks
+// its column SET on the column's first product.
+template <int SR, bool COMP>
+struct GridIns {
+    using S = Sr<SR>;
+    using TA = TileAcc<SR>;
+    using lo_t = typename TA::lo_t;
+    using in_t = typename S::in_t;
+    lo_t *vals;
+    unsigned *st;
+    unsigned *hi;
+    unsigned *err;
+    int c0, T;
+    __device__ __forceinline__ void operator()(int, in_t a, int j, in_t b) const {
+        const int jj = j - c0;
+        if ((unsigned)jj >= (unsigned)T) {   // only an unsorted row of B gets here
+            atomicOr(err, ERR_INTERNAL);
+            return;
+        }
+        const unsigned w = st[jj >> 4] >> (2 * (jj & 15));
+        if ((w & 1u) != (COMP ? 1u : 0u)) {
+            TA::add(vals, hi, jj, S::mul(a, b));
+            if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
+        }
+    }
+};
+
+// One item.  Entries are written ascending from obase; in the gradient form
+// (aligned, plain masks) values go to their mask entry's own slot instead.
+// Returns the entries written.
+template <int SR, bool COMP>
+__device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab,
                                          int *scratch, int tile, int ntiles, int mq0, int mq1, long long obase) {
     using S = Sr<SR>;
-    using in_t = typename S::in_t;
     using out_t = typename S::out_t;
     using TA = TileAcc<SR>;
     using lo_t = typename TA::lo_t;
@@ -974,24 +1011,12 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
         else atomicOr(L.ra.err, ERR_INTERNAL);
     }
     cta_sync();
-    auto ins = [&](int jj, in_t a, in_t b) {
-        if ((unsigned)jj >= (unsigned)T) {   // only an unsorted row of B gets here
-            atomicOr(L.ra.err, ERR_INTERNAL);
-            return;
-        }
-        const unsigned w = st[jj >> 4] >> (2 * (jj & 15));
-        if (!(w & 1u)) {
-            TA::add(vals, hi, jj, S::mul(a, b));
-            if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
-        }
-    };
+    GridIns<SR, COMP> ins{vals, st, hi, L.ra.err, c0, T};
     if (ntiles == 1) {
-        auto f = [&](int, in_t a, int j, in_t b) { ins(j, a, b); };
-        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, f);
+        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     } else {
-        auto f = [&](int, in_t a, int j, in_t b) { ins(j - c0, a, b); };
         const TileSeg seg{P.tpos, P.tstride, tile};
-        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, f);
+        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, ins);
     }
     cta_sync();
     // gather the SET columns in ascending order; each thread owns a run of
@@ -1011,9 +1036,20 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
             const int jj = w * 16 + (b >> 1);
-            L.tmp.ci[o] = c0 + jj;
-            tv[o] = S::out(TA::take(vals, hi, jj));
-            ++o;
+            const out_t v = S::out(TA::take(vals, hi, jj));
+            if (!COMP && L.aligned) {
+                // the column's rank in the mask row (SET columns are mask columns)
+                int lo = mq0, up = mq1;
+                while (lo < up) {
+                    const int mid = (lo + up) >> 1;
+                    if (__ldg(P.m_ci + mid) < c0 + jj) lo = mid + 1; else up = mid;
+                }
+                tv[c.tmp + (lo - c.m0)] = v;
+            } else {
+                L.tmp.ci[o] = c0 + jj;
+                tv[o] = v;
+                ++o;
+            }
         }
         st[w] = 0;
     }
@@ -1025,15 +1061,15 @@ __device__ __forceinline__ int cmsa_tile(const DevProd &P, const RowCtx &c, cons
 // all reads of a chunk before its writes.  Pieces were written by other SMs:
 // read through L2.
 template <int SR>
-__device__ __forceinline__ void cmsa_pack(const RowCtx &c, const RowLaunch &L, int x, int ntiles) {
+__device__ __forceinline__ void grid_pack(const RowCtx &c, const RowLaunch &L, const GridTab &G, int x, int ntiles) {
     using out_t = typename Sr<SR>::out_t;
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     int *tci = L.tmp.ci;
     long long dst = 0;
     for (int t = 0; t < ntiles; ++t) {
         const long long slot = (long long)x * L.gnt + t;
-        const int nt = __ldcg(L.gcnt + slot);
-        const long long src = __ldcg(L.goff + slot);
+        const int nt = __ldcg(G.cnt + slot);
+        const long long src = __ldcg(G.off + slot);
         if (src != dst) {
             for (int b = 0; b < nt; b += blockDim.x) {
                 const int q = b + threadIdx.x;
@@ -1055,20 +1091,23 @@ __device__ __forceinline__ void cmsa_pack(const RowCtx &c, const RowLaunch &L, i
     if (threadIdx.x == 0) L.ra.cnt[c.r] = (int)dst;
 }
 
-template <int SR>
+template <int SR, bool COMP>
 __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int scratch[64];
     __shared__ long long s_item;
     __shared__ int s_mq[2];
     __shared__ int s_last;
-    const int count = L.ra.kind_count[K_CMSA_G];
-    const int off = L.ra.kind_off[K_CMSA_G];
+    constexpr int KIND = COMP ? K_CMSA_G : K_MSA_G;
+    const GridTab &G = L.g[COMP ? 1 : 0];
+    const int count = L.ra.kind_count[KIND];
+    const int off = L.ra.kind_off[KIND];
     const int T = L.tileT;
     if (TileAcc<SR>::split && !tile_hi_of<SR>(L)) {   // uniform over the CTA
         if (threadIdx.x == 0 && count > 0) atomicOr(L.ra.err, ERR_INTERNAL);
         return;
     }
+    if (count == 0) return;
     {   // zero the tile arrays once; every item leaves them zeroed
         unsigned *w = reinterpret_cast<unsigned *>(smem);
         for (int x = threadIdx.x; x < L.slab / 4; x += blockDim.x) w[x] = 0;
@@ -1076,7 +1115,7 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
     const long long nitems = (long long)count * L.gnt;
     for (;;) {
         cta_sync();
-        if (threadIdx.x == 0) s_item = (long long)atomicAdd(L.gnext, 1ULL);
+        if (threadIdx.x == 0) s_item = (long long)atomicAdd(G.next, 1ULL);
         cta_sync();
         const long long item = s_item;
         if (item >= nitems) break;
@@ -1098,21 +1137,23 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
         }
         cta_sync();
         const int mq0 = s_mq[0], mq1 = s_mq[1];
-        const long long rel = (long long)c0 - (mq0 - c.m0);   // open columns before the tile
-        const int cnt = cmsa_tile<SR>(P, c, L, smem, scratch, tile, ntiles, mq0, mq1, c.tmp + rel);
+        // the piece's offset in the row: mask entries before the tile (plain),
+        // or columns before the tile the mask leaves open (complemented)
+        const long long rel = COMP ? (long long)c0 - (mq0 - c.m0) : (long long)(mq0 - c.m0);
+        const int cnt = grid_tile<SR, COMP>(P, c, L, smem, scratch, tile, ntiles, mq0, mq1, c.tmp + rel);
         __threadfence();   // this item's entries, before the row's completion count
         cta_sync();
         if (threadIdx.x == 0) {
             const long long slot = (long long)x * L.gnt + tile;
-            L.gcnt[slot] = cnt;
-            L.goff[slot] = (int)rel;
+            G.cnt[slot] = cnt;
+            G.off[slot] = (int)rel;
             __threadfence();
-            s_last = atomicAdd(&L.gdone[x], 1) == ntiles - 1;
+            s_last = atomicAdd(&G.done[x], 1) == ntiles - 1;
         }
         cta_sync();
-        if (s_last) {
+        if (s_last && (COMP || !L.aligned)) {
             __threadfence();
-            cmsa_pack<SR>(c, L, x, ntiles);
+            grid_pack<SR>(c, L, G, x, ntiles);
         }
     }
 }

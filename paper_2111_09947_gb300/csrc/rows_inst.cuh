@@ -67,7 +67,8 @@ cudaError_t MSG_CAT(launch_kind_, MSG_SUFFIX)(int kind, const ProdSet &ps, const
     case K_CHASH_B: return go<k_rows_b<MSG_SR, K_CHASH_B>>(ps, L, th, sm, st, nsm);
     case K_MSA_T: return go<k_rows_t<MSG_SR, false>>(ps, L, th, sm, st, nsm);
     case K_CMSA_T: return go<k_rows_t<MSG_SR, true>>(ps, L, th, sm, st, nsm);
-    case K_CMSA_G: return go<k_rows_g<MSG_SR>>(ps, L, th, sm, st, nsm);
+    case K_CMSA_G: return go<k_rows_g<MSG_SR, true>>(ps, L, th, sm, st, nsm);
+    case K_MSA_G: return go<k_rows_g<MSG_SR, false>>(ps, L, th, sm, st, nsm);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -154,7 +154,8 @@ def test_autotune_reads_cache(batch, tmp_path):
     ps, devs, refs = batch
     key = torch.cuda.get_device_name() + "|plus_times_f32"
     # MCA first for every class, pull practically off: binning must follow it
-    entry = {"warp_flops_max": 65536, "dot_ratio": 1e6, "warp_slab": 4608, "pref": [[3, 0, 0, 0]] * 16}
+    entry = {"warp_flops_max": 65536, "dot_ratio": 1e6, "warp_slab": 4608, "grid_min_flops": 1 << 62,
+             "pref": [[3, 0, 0, 0]] * 16}
     cache = tmp_path / "tune.json"
     cache.write_text(json.dumps({"some other device|plus_times_f32": entry, key: entry}).replace("}, ", "},\n"))
     h = _lib.Handle()

@@ -250,3 +250,66 @@ def test_int64_tiled_high_words(handle, grid, complement):
     finally:
         handle.force("auto")
         handle.set_option(_lib.OPT_GRID, 1)
+
+
+@pytest.mark.parametrize("grid", [0, 1, 2])
+@pytest.mark.parametrize("semiring", ["plus_times_f32", "plus_times_i64", "plus_pair_i64"])
+def test_plain_heavy_rows_grid_modes(handle, grid, semiring):
+    """Heavy plain-mask rows of a product wider than one tile: one CTA per row
+    (grid 0), (row, tile) items for rows over the flop bound (1, bound lowered
+    so the heavy rows qualify) or for every CTA row (2)."""
+    gen = {"plus_times_i64": "i64", "plus_times_f32": "f32", "plus_pair_i64": "pair"}[semiring]
+    q = _varied_rows(200, 3000, 130000, (2, 60, 900, 20), (0, 30, 4000, 60000, 700), 81 + grid, gen)
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring)
+    handle.set_option(_lib.OPT_GRID, grid)
+    handle.set_option(_lib.OPT_GRID_MIN_FLOPS, 1 << 16)
+    try:
+        for force in ("auto", "msa"):
+            handle.force(force)
+            dq = to_dev(q, semiring)
+            for rep in range(2):
+                res = _lib.msgemm_run(handle, dq["M"], dq["A"], dq["B"], semiring).trimmed()
+                handle.sync_status()
+                assert_parity(res, ref, semiring, ctx=f"grid={grid} force={force} rep={rep}")
+            counts = handle.bin_counts()
+            if grid == 0:
+                assert counts["msa_g"] == 0
+            else:
+                assert counts["msa_g"] > 0
+    finally:
+        handle.force("auto")
+        handle.set_option(_lib.OPT_GRID, 1)
+        handle.set_option(_lib.OPT_GRID_MIN_FLOPS, 1 << 20)
+
+
+def test_backward_through_grid_rows(tmp_path):
+    """Gradient form (values written at each mask entry's own slot) through
+    the (row, tile) items: every row made a CTA row by a policy loaded from an
+    autotuner cache (warp flop bound 0), grid mode 2; dA and dB against the
+    oracle's closed forms."""
+    import json
+    m, k, n = 150, 60000, 60000
+    p = synth.random_problem(m, k, n, 300.0, 3.0, 30.0, 315, "f32")
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    G = synth.Csr(m, n, ref["rowptr"].astype(np.int32), ref["colidx"], synth.upstream_grad(len(ref["colidx"]), 3))
+    dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+    d = to_dev(p, "plus_times_f32")
+    cache = tmp_path / "policy.json"
+    entry = {"warp_flops_max": 0, "dot_ratio": 2, "warp_slab": 4608, "grid_min_flops": 1 << 20,
+             "pref": [[1, 2, 3, 0]] * 16}
+    cache.write_text(json.dumps({torch.cuda.get_device_name() + "|plus_times_f32": entry}))
+    h = _lib.Handle()
+    try:
+        _lib.msgemm_autotune(h, [], [], [], "plus_times_f32", cache_path=cache)
+        h.set_option(_lib.OPT_GRID, 2)
+        dA, dB = _lib.msgemm_backward(h, d["A"], d["B"], _lib.DeviceCsr.from_host(G))
+        h.sync_status()
+        assert h.bin_counts()["msa_g"] > 0
+    finally:
+        h.close()
+    Aabs = p["A"].with_values(np.abs(p["A"].values))
+    Babs = p["B"].with_values(np.abs(p["B"].values))
+    Gabs = G.with_values(np.abs(G.values))
+    SA, SB = O.grad(Aabs, Babs, Gabs)
+    assert np.all(np.abs(dA.cpu().numpy() - dA_ref) <= 1e-5 * SA + 1e-30)
+    assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
