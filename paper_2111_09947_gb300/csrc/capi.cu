@@ -1148,7 +1148,7 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
         CK(cudaMemcpyAsync(t.cur, t.rp, sizeof(int) * ((size_t)X->ncols + 1), cudaMemcpyDeviceToDevice, st));
         CK(launch_transpose_fill(X->rowptr, X->colidx, X->values, 4, X->nrows, t.rp, t.cur, t.ci, t.v, nullptr, st,
                                  h->nsm));
-        if (sorted) CK(launch_segsort(t.rp, t.ci, t.v, 4, X->ncols, st, h->nsm));
+        if (sorted) CK(launch_segsort(t.rp, t.ci, t.v, 4, X->ncols, t.cur, st, h->nsm));   // cursors are free now
         return MSGEMM_OK;
     };
     if (dA_vals) {
@@ -1261,7 +1261,7 @@ msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_
     CK(cudaMemcpyAsync(cur, At->rowptr, sizeof(int) * ((size_t)A->ncols + 1), cudaMemcpyDeviceToDevice, st));
     CK(launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At->rowptr, cur, At->colidx,
                              At->values, nullptr, st, h->nsm));
-    if (sorted) CK(launch_segsort(At->rowptr, At->colidx, At->values, value_bytes, A->ncols, st, h->nsm));
+    if (sorted) CK(launch_segsort(At->rowptr, At->colidx, At->values, value_bytes, A->ncols, cur, st, h->nsm));
     int64_t nnz = A->nnz;
     CK(cudaMemcpyAsync(At->d_nnz, &nnz, sizeof nnz, cudaMemcpyHostToDevice, st));
     CK(cudaStreamSynchronize(st));

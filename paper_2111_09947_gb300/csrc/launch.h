@@ -79,7 +79,9 @@ cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, i
                                  void *tv, const int *gate, cudaStream_t, int nsm);
 cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, int nt, int *tpos, const int *gate,
                                cudaStream_t, int nsm);
-cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t, int nsm);
+// scratch: nrows + 1 ints of device memory (a list of the long rows)
+cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, int *scratch, cudaStream_t,
+                           int nsm);
 
 constexpr int CTILE = 1024;        // rows per compaction tile
 constexpr int CCH = 8192;          // output entries per compaction chunk

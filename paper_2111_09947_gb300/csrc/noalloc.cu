@@ -80,7 +80,8 @@ extern "C" msgemm_status msgemm_transpose_noalloc(const msgemm_csr *A, int value
     if (launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At_rowptr, cursor, At_colidx,
                               At_values, nullptr, st, nsm) != cudaSuccess)
         return MSGEMM_ERR_CUDA;
-    if (sorted && launch_segsort(At_rowptr, At_colidx, At_values, value_bytes, n, st, nsm) != cudaSuccess)
+    // the cursors (n + 1 ints) are free after the scatter: they hold the sort's row list
+    if (sorted && launch_segsort(At_rowptr, At_colidx, At_values, value_bytes, n, cursor, st, nsm) != cudaSuccess)
         return MSGEMM_ERR_CUDA;
     return MSGEMM_OK;
 }

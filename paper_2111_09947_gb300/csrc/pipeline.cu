@@ -522,10 +522,12 @@ namespace msg {
 // place.  Bitonic network written with ascending comparators only (the first
 // step of each merge compares i with i ^ (k - 1)), so positions past the row
 // end act as +infinity without storage.  Rows up to 256 entries: one warp in
-// shared memory; up to SEG_SMEM entries: one CTA in shared memory; longer
-// rows: one CTA on global memory.
+// shared memory; the warp pass lists longer rows, which 1024-thread CTAs
+// then take from the list: up to SEG_SMEM entries in shared memory, longer
+// ones on global memory.
 constexpr int SEG_WARP = 256;
-constexpr int SEG_SMEM = 8192;
+constexpr int SEG_SMEM = 16384;
+constexpr int SEG_CTA = 1024;
 
 template <int VB> struct ValT { using T = unsigned char; };
 template <> struct ValT<4> { using T = unsigned; };
@@ -548,7 +550,7 @@ __device__ __forceinline__ void bitonic_asc(int len, int tid, int nthreads, KeyA
 }
 
 template <int VB>
-__global__ void __launch_bounds__(256) k_segsort_warp(const int *rp, int *ci, void *v, int nrows) {
+__global__ void __launch_bounds__(256) k_segsort_warp(const int *rp, int *ci, void *v, int nrows, int *list) {
     using V = typename ValT<VB>::T;
     __shared__ int sk[8][SEG_WARP];
     __shared__ V sv[8][VB ? SEG_WARP : 1];
@@ -556,6 +558,7 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const int *rp, int *ci, vo
     const long long gw = (long long)blockIdx.x * 8 + w, nw = (long long)gridDim.x * 8;
     for (long long i = gw; i < nrows; i += nw) {
         const int s = rp[i], len = rp[i + 1] - s;
+        if (len > SEG_WARP && lane == 0) list[1 + atomicAdd(list, 1)] = (int)i;   // for k_segsort_cta
         if (len < 2 || len > SEG_WARP) continue;
         for (int x = lane; x < len; x += 32) {
             sk[w][x] = ci[s + x];
@@ -576,14 +579,15 @@ __global__ void __launch_bounds__(256) k_segsort_warp(const int *rp, int *ci, vo
 }
 
 template <int VB>
-__global__ void __launch_bounds__(256) k_segsort_cta(const int *rp, int *ci, void *v, int nrows) {
+__global__ void __launch_bounds__(SEG_CTA) k_segsort_cta(const int *rp, int *ci, void *v, const int *list) {
     using V = typename ValT<VB>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     int *sk = reinterpret_cast<int *>(smem);
     V *sv = reinterpret_cast<V *>(smem + 4 * SEG_SMEM);
-    for (long long i = blockIdx.x; i < nrows; i += gridDim.x) {
+    const int nlist = list[0];
+    for (int x0 = blockIdx.x; x0 < nlist; x0 += gridDim.x) {
+        const long long i = list[1 + x0];
         const int s = rp[i], len = rp[i + 1] - s;
-        if (len <= SEG_WARP) continue;
         if (len <= SEG_SMEM) {
             for (int x = threadIdx.x; x < len; x += blockDim.x) {
                 sk[x] = ci[s + x];
@@ -613,7 +617,7 @@ __global__ void __launch_bounds__(256) k_segsort_cta(const int *rp, int *ci, voi
 }
 
 template <int VB>
-static cudaError_t segsort_t(const int *rp, int *ci, void *v, int nrows, cudaStream_t st, int nsm) {
+static cudaError_t segsort_t(const int *rp, int *ci, void *v, int nrows, int *list, cudaStream_t st, int nsm) {
     const size_t smem = 4 * SEG_SMEM + (VB ? (size_t)VB * SEG_SMEM : 0);
     static bool attr = false;
     if (!attr) {
@@ -621,16 +625,19 @@ static cudaError_t segsort_t(const int *rp, int *ci, void *v, int nrows, cudaStr
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    k_segsort_warp<VB><<<grid_cap(((long long)nrows + 7) / 8, nsm, 8), 256, 0, st>>>(rp, ci, v, nrows); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-    k_segsort_cta<VB><<<nsm * 2, 256, smem, st>>>(rp, ci, v, nrows); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    k_segsort_warp<VB><<<grid_cap(((long long)nrows + 7) / 8, nsm, 8), 256, 0, st>>>(rp, ci, v, nrows, list); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_segsort_cta<VB><<<nsm, SEG_CTA, smem, st>>>(rp, ci, v, list); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
-cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, cudaStream_t st, int nsm) {
+cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, int *scratch, cudaStream_t st,
+                           int nsm) {
     if (nrows == 0) return cudaSuccess;
-    if (vbytes == 4) return segsort_t<4>(rp, ci, v, nrows, st, nsm);
-    if (vbytes == 8) return segsort_t<8>(rp, ci, v, nrows, st, nsm);
-    return segsort_t<0>(rp, ci, nullptr, nrows, st, nsm);
+    if (vbytes == 4) return segsort_t<4>(rp, ci, v, nrows, scratch, st, nsm);
+    if (vbytes == 8) return segsort_t<8>(rp, ci, v, nrows, scratch, st, nsm);
+    return segsort_t<0>(rp, ci, nullptr, nrows, scratch, st, nsm);
 }
 
 }  // namespace msg
