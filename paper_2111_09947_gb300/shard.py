@@ -65,3 +65,48 @@ def gather_row_offsets(local_nnz: int, device=None, group=None) -> list[int]:
     dist.all_gather(parts, x, group=group)
     counts = [int(p.item()) for p in parts]
     return [0] + list(np.cumsum(counts)[:-1].tolist()) if world else []
+
+
+def row_block(X, r0: int, r1: int):
+    """Rows [r0, r1) of a CSR matrix X (numpy or torch arrays) as a CSR of
+    r1 - r0 rows over the same columns: row pointers rebased, column and
+    value slices are views.  Returns an object of X's type when it accepts
+    (nrows, ncols, rowptr, colidx, values), else a dict."""
+    base = int(X.rowptr[r0])
+    end = int(X.rowptr[r1])
+    rp = X.rowptr[r0:r1 + 1] - base
+    ci = X.colidx[base:end]
+    vals = getattr(X, "values", None)
+    v = vals[base:end] if vals is not None else None
+    try:
+        return type(X)(r1 - r0, X.ncols, rp, ci, v)
+    except TypeError:
+        return {"nrows": r1 - r0, "ncols": X.ncols, "rowptr": rp, "colidx": ci, "values": v}
+
+
+def push_work(A, B) -> np.ndarray:
+    """Push products per row of A B (sum over A_i* of nnz(B_k*)), on host."""
+    def host(x):
+        return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+    arp, aci, brp = host(A.rowptr).astype(np.int64), host(A.colidx), host(B.rowptr).astype(np.int64)
+    blen = np.diff(brp)
+    cs = np.concatenate([[0], np.cumsum(blen[aci])]) if len(aci) else np.zeros(1, np.int64)
+    return cs[arp[1:]] - cs[arp[:-1]]
+
+
+def sharded_product(M, A, B, compute, rank: int, world: int, group=None, device=None):
+    """This rank's share of C = M .* (A B) (or its complement, as compute
+    decides): the contiguous block of rows [r0, r1) that partition_rows gives
+    it by push work, computed by compute(M_block, A_block, B) (the library's
+    GPU product in use; any CSR-returning function in tests), plus the number
+    of entries of C before the block (an all-gather of per-rank counts), so
+    the blocks stitch into one CSR.  B is replicated on every rank.
+
+    Returns dict(r0, r1, offset, nnz, result)."""
+    b = partition_rows(push_work(A, B), world)
+    r0, r1 = int(b[rank]), int(b[rank + 1])
+    res = compute(row_block(M, r0, r1), row_block(A, r0, r1), B)
+    rp = res["rowptr"] if isinstance(res, dict) else res.rowptr
+    nnz = int(rp[-1]) if len(rp) else 0
+    offsets = gather_row_offsets(nnz, device=device, group=group)
+    return {"r0": r0, "r1": r1, "offset": int(offsets[rank]), "nnz": nnz, "result": res}

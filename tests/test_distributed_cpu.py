@@ -21,6 +21,30 @@ def _free_port():
     return p
 
 
+def _sharded_worker(rank, world, port, q):
+    """Each rank computes its row block of one product with the oracle as the
+    compute function; rank 0 stitches the blocks."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        from oracle import oracle as O
+        from paper_2111_09947_gb300 import synth
+        p = synth.random_problem(300, 200, 250, 6.0, 9.0, 20.0, 91, "i64")
+
+        def compute(Mb, Ab, B):
+            return O.masked_spgemm(Mb, Ab, B, "plus_times_i64")
+        out = shard.sharded_product(p["M"], p["A"], p["B"], compute, rank, world)
+        parts = [None] * world
+        dist.all_gather_object(parts, {k: out[k] for k in ("r0", "r1", "offset", "nnz")} |
+                               {"rowptr": out["result"]["rowptr"], "colidx": out["result"]["colidx"],
+                                "values": out["result"]["values"]})
+        q.put((rank, parts))
+    finally:
+        dist.destroy_process_group()
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
@@ -66,3 +90,33 @@ def test_partition_products_covers_all():
     assert sorted(sum(parts, [])) == list(range(len(costs)))
     loads = [sum(costs[p] for p in part) for part in parts]
     assert max(loads) - min(loads) <= max(costs)
+
+
+def test_two_rank_row_sharded_product_stitches():
+    from oracle import oracle as O
+    from paper_2111_09947_gb300 import synth
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_sharded_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    parts = res[0]
+    assert parts[0]["r0"] == 0 and parts[0]["r1"] == parts[1]["r0"] and parts[1]["r1"] == 300
+    assert parts[0]["offset"] == 0 and parts[1]["offset"] == parts[0]["nnz"]
+    # stitched CSR: row pointers shifted by each block's offset
+    rp = np.concatenate([parts[0]["rowptr"][:-1] + parts[0]["offset"], parts[1]["rowptr"] + parts[1]["offset"]])
+    ci = np.concatenate([x["colidx"] for x in parts])
+    va = np.concatenate([x["values"] for x in parts])
+    p = synth.random_problem(300, 200, 250, 6.0, 9.0, 20.0, 91, "i64")
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_i64")
+    assert np.array_equal(rp, ref["rowptr"]) and np.array_equal(ci, ref["colidx"])
+    assert np.array_equal(va, ref["values"])
+    # the split balances push work
+    w = shard.push_work(p["A"], p["B"])
+    b = parts[0]["r1"]
+    assert abs(w[:b].sum() - w[b:].sum()) <= w.max()
