@@ -350,3 +350,65 @@ int oracle_grad(int64_t m, int64_t k, int64_t n,
     free(Atrp); free(Atci); free(Atsrc); free(Gtrp); free(Gtci); free(Gtsrc);
     return ORACLE_OK;
 }
+
+/* ---- betweenness centrality (Brandes), the application of Sec. 8.3 ------
+ * For each source s of the batch: a breadth-first search from s gives each
+ * reached vertex v its level and sigma_sv, the number of shortest s-v paths
+ * (sigma_s = 1; sigma_w = sum of sigma_v over v -> w edges with
+ * level(v) = level(w) - 1); then, in decreasing level order, the dependency
+ * delta_s(v) = sum over v -> w edges with level(w) = level(v) + 1 of
+ * sigma_v / sigma_w * (1 + delta_s(w)).  bc(v) = sum over the sources s != v
+ * of delta_s(v).  Edges are the stored entries of the n x n CSR (v -> w for
+ * entry (v, w)); values are ignored.  fp64 throughout; sources in parallel. */
+int oracle_bc(int64_t n, const int32_t *rp, const int32_t *ci, int64_t nsrc, const int32_t *src, double *bc) {
+    int err;
+    if ((err = oracle_validate_csr(n, n, rp, ci))) return err;
+    for (int64_t s = 0; s < nsrc; ++s)
+        if (src[s] < 0 || src[s] >= n) return ORACLE_BAD_ARGS;
+    for (int64_t v = 0; v < n; ++v) bc[v] = 0.0;
+    int failed = 0;
+    #pragma omp parallel
+    {
+        int32_t *level = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+        double *sigma = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        double *delta = (double *)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+        double *local = (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+        if (!level || !order || !sigma || !delta || !local) {
+            #pragma omp atomic write
+            failed = 1;
+        } else {
+            #pragma omp for schedule(dynamic, 1)
+            for (int64_t s = 0; s < nsrc; ++s) {
+                for (int64_t v = 0; v < n; ++v) { level[v] = -1; sigma[v] = 0.0; delta[v] = 0.0; }
+                int64_t head = 0, tail = 0;
+                const int32_t s0 = src[s];
+                level[s0] = 0;
+                sigma[s0] = 1.0;
+                order[tail++] = s0;
+                while (head < tail) {                 /* BFS; order = visit order */
+                    const int32_t v = order[head++];
+                    for (int64_t t = rp[v]; t < rp[v + 1]; ++t) {
+                        const int32_t w = ci[t];
+                        if (level[w] < 0) { level[w] = level[v] + 1; order[tail++] = w; }
+                        if (level[w] == level[v] + 1) sigma[w] += sigma[v];
+                    }
+                }
+                for (int64_t x = tail - 1; x >= 0; --x) {   /* decreasing level */
+                    const int32_t v = order[x];
+                    double d = 0.0;
+                    for (int64_t t = rp[v]; t < rp[v + 1]; ++t) {
+                        const int32_t w = ci[t];
+                        if (level[w] == level[v] + 1) d += sigma[v] / sigma[w] * (1.0 + delta[w]);
+                    }
+                    delta[v] = d;
+                    if (v != s0) local[v] += d;
+                }
+            }
+            #pragma omp critical
+            for (int64_t v = 0; v < n; ++v) bc[v] += local[v];
+        }
+        free(level); free(order); free(sigma); free(delta); free(local);
+    }
+    return failed ? ORACLE_NOMEM : ORACLE_OK;
+}

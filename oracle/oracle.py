@@ -48,6 +48,8 @@ def _load() -> C.CDLL:
         lib.oracle_validate_csr.argtypes = [i64, i64, vp, vp]
         lib.oracle_grad.restype = i32
         lib.oracle_grad.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.oracle_bc.argtypes = [i64, vp, vp, i64, vp, vp]
+        lib.oracle_bc.restype = i32
         _lib = lib
     return _lib
 
@@ -125,3 +127,21 @@ def grad(A, B, G) -> tuple[np.ndarray, np.ndarray]:
     if e:
         raise OracleError(ERRORS.get(e, f"error {e}"))
     return dA, dB
+
+
+def bc(A, sources) -> np.ndarray:
+    """Betweenness centrality of every vertex from the given sources (Brandes,
+    fp64; the application benchmarked in Sec. 8.3): for each source s, the
+    dependencies delta_s(v) of a breadth-first search over the stored entries
+    of A (edge v -> w for entry (v, w)); bc(v) = sum over sources s != v of
+    delta_s(v)."""
+    lib = _load()
+    if A.nrows != A.ncols:
+        raise OracleError("shape mismatch")
+    rp, ci = _arr(A.rowptr, np.int32), _arr(A.colidx, np.int32)
+    src = _arr(sources, np.int32)
+    out = np.zeros(A.nrows, np.float64)
+    err = lib.oracle_bc(A.nrows, _ptr(rp), _ptr(ci), len(src), _ptr(src), _ptr(out))
+    if err:
+        raise OracleError(ERRORS.get(err, f"error {err}"))
+    return out
