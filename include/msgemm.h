@@ -203,6 +203,22 @@ msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr
                               const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                               msgemm_semiring semiring, const char *cache_path);
 
+/* Betweenness centrality from a batch of sources (the application of Sec.
+ * 8.3, Brandes' algorithm in matrix form over this library's products).
+ * Forward: level 0 = the sources (one row per source), level d + 1 =
+ * !visited .* (level_d A) on plus-times int64, so each entry carries sigma,
+ * the number of shortest paths from its row's source; visited = levels
+ * 0..d.  Backward, from the deepest level: W = (1 + delta) / sigma on level
+ * d, T = level_{d-1} .* (W A^T) on plus-times fp32 (values at each entry's
+ * own slot), delta = sigma T on level d-1.  centrality[v] (device, n
+ * doubles, overwritten) = sum over the sources s != v of delta_s(v).  A is
+ * n x n, an edge v -> w per stored entry (v, w); its values are ignored.
+ * sources: device int32[nsrc], each in [0, n) (checked on the host).
+ * *levels (host, optional) = number of BFS levels including level 0.
+ * Synchronises once per level; allocates its workspace through the handle. */
+msgemm_status msgemm_bc(msgemm_handle *handle, const msgemm_csr *A, const int32_t *sources, int nsrc,
+                        double *centrality, int32_t *levels);
+
 /* Transpose (CSR of A^T), value_bytes in {0, 4, 8}.  At is allocated like an
  * output (capacity nnz(A)).  Column indices within a row of A^T are in
  * arbitrary order unless sorted != 0, which adds a segmented sort pass

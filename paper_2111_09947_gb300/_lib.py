@@ -31,7 +31,7 @@ EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_ru
            "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
            "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
            "msgemm_profile_count", "msgemm_profile_entry", "msgemm_last_row_kinds", "msgemm_kernel_launches",
-           "msgemm_transpose_noalloc", "msgemm_destroy"]
+           "msgemm_transpose_noalloc", "msgemm_bc", "msgemm_destroy"]
 
 
 class MsgemmError(RuntimeError):
@@ -94,6 +94,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "msgemm_last_row_kinds": (i32, [vp, vp, i64]),
         "msgemm_kernel_launches": (i64, []),
         "msgemm_transpose_noalloc": (i32, [P(Csr), i32, i32, vp, vp, vp, vp]),
+        "msgemm_bc": (i32, [vp, P(Csr), vp, i32, vp, P(C.c_int32)]),
         "msgemm_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
@@ -361,3 +362,16 @@ def msgemm_transpose_noalloc(A: DeviceCsr, value_bytes: int, sorted_rows: bool =
     if st != 0:
         raise MsgemmError(st, "msgemm_transpose_noalloc")
     return rp, ci[:A.nnz], (v[:A.nnz] if v is not None else None)
+
+
+def msgemm_bc(h: Handle, A: DeviceCsr, sources: torch.Tensor):
+    """Betweenness centrality of every vertex from the given sources (device
+    int32): returns (centrality fp64 tensor of n, number of BFS levels)."""
+    h.bind_stream()
+    src = sources.to(device=A.rowptr.device, dtype=torch.int32).contiguous()
+    out = torch.empty(max(A.nrows, 1), dtype=torch.float64, device=A.rowptr.device)
+    a = A.abi()
+    lv = C.c_int32(0)
+    h.check(h.lib.msgemm_bc(h.h, C.byref(a), src.data_ptr() if src.numel() else None, int(src.numel()),
+                            out.data_ptr(), C.byref(lv)))
+    return out[:A.nrows], int(lv.value)

@@ -1237,6 +1237,141 @@ msgemm_status msgemm_autotune(msgemm_handle *h, int nprod, const msgemm_csr *M, 
     return MSGEMM_OK;
 }
 
+msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *sources, int nsrc, double *centrality,
+                        int32_t *levels) {
+    if (!h) return MSGEMM_ERR_INVALID;
+    h->nprof = 0;
+    CKS(check_csr(h, A, "A", false));
+    if (A->nrows != A->ncols) return fail(h, MSGEMM_ERR_SHAPE, "A is %dx%d, not square", A->nrows, A->ncols);
+    if (nsrc < 0 || (nsrc > 0 && !sources) || (A->nrows > 0 && !centrality))
+        return fail(h, MSGEMM_ERR_INVALID, "bad sources or output");
+    cudaStream_t st = h->stream;
+    const int n = A->nrows;
+    if (levels) *levels = 0;
+    if (n > 0) CK(cudaMemsetAsync(centrality, 0, sizeof(double) * (size_t)n, st));
+    if (nsrc == 0 || n == 0) return MSGEMM_OK;
+    if (h->validate) CKS(validate_inputs(h, {A}));
+    {   // sources in range (host check; synchronises)
+        std::vector<int32_t> hs(nsrc);
+        CK(cudaMemcpyAsync(hs.data(), sources, sizeof(int32_t) * (size_t)nsrc, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        for (int32_t x : hs)
+            if (x < 0 || x >= n) return fail(h, MSGEMM_ERR_INVALID, "source %d out of range", x);
+    }
+    const long long nnz = A->nnz;
+    const long long wpr = ((long long)n + 31) / 32;
+    // every allocation of this call, released at the end (stream-ordered)
+    std::vector<void *> owned;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = dev_alloc(h, bytes);
+        if (p) owned.push_back(p);
+        return p;
+    };
+    struct Guard {
+        msgemm_handle *h;
+        std::vector<void *> &v;
+        ~Guard() {
+            for (void *p : v) dev_free(h, p);
+        }
+    } guard{h, owned};
+    // A with int64 ones (forward), and A^T with fp32 ones, rows sorted
+    // (backward right operand; its transpose, A with fp32 ones, serves pull rows)
+    long long *a1 = static_cast<long long *>(take(sizeof(long long) * (size_t)std::max(nnz, 1LL)));
+    float *f1 = static_cast<float *>(take(sizeof(float) * (size_t)std::max(nnz, 1LL)));
+    int *at_rp = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
+    int *at_cur = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
+    int *at_ci = static_cast<int *>(take(sizeof(int) * (size_t)std::max(nnz, 1LL)));
+    long long *tb = static_cast<long long *>(take(sizeof(long long) * ((size_t)n / STILE + 4)));
+    unsigned *bm = static_cast<unsigned *>(take(sizeof(unsigned) * (size_t)(nsrc * wpr)));
+    int *vrp = static_cast<int *>(take(sizeof(int) * ((size_t)nsrc + 1)));
+    int *vcnt = static_cast<int *>(take(sizeof(int) * ((size_t)nsrc + 1)));
+    long long *vtb = static_cast<long long *>(take(sizeof(long long) * ((size_t)nsrc / STILE + 4)));
+    if (!a1 || !f1 || !at_rp || !at_cur || !at_ci || !tb || !bm || !vrp || !vcnt || !vtb)
+        return fail(h, MSGEMM_ERR_OOM, "bc workspace allocation failed");
+    CK(launch_fill_i64(a1, nnz, 1, st, h->nsm));
+    CK(launch_fill_f32(f1, nnz, 1.0f, st, h->nsm));
+    CK(launch_col_counts(A->colidx, nnz, n, at_cur, st, h->nsm));
+    CK(launch_excl_scan_int(at_cur, n, at_rp, tb, st, h->nsm));
+    CK(cudaMemcpyAsync(at_cur, at_rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
+    CK(launch_transpose_fill(A->rowptr, A->colidx, nullptr, 0, n, at_rp, at_cur, at_ci, nullptr, nullptr, st, h->nsm));
+    CK(launch_segsort(at_rp, at_ci, nullptr, 0, n, at_cur, st, h->nsm));
+    CK(cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)(nsrc * wpr), st));
+    const msgemm_csr Aone{n, n, nnz, A->rowptr, A->colidx, a1};
+    const msgemm_csr AtOne{n, n, nnz, at_rp, at_ci, f1};
+
+    // ---- forward: level 0 = the sources, level d + 1 = !visited .* (level d A)
+    struct Level {
+        int32_t *rp, *ci;
+        long long *sigma;
+        long long nnz;
+    };
+    std::vector<Level> lv;
+    {
+        Level l0;
+        l0.rp = static_cast<int *>(take(sizeof(int) * ((size_t)nsrc + 1)));
+        l0.ci = static_cast<int *>(take(sizeof(int) * (size_t)nsrc));
+        l0.sigma = static_cast<long long *>(take(sizeof(long long) * (size_t)nsrc));
+        if (!l0.rp || !l0.ci || !l0.sigma) return fail(h, MSGEMM_ERR_OOM, "bc workspace allocation failed");
+        l0.nnz = nsrc;
+        CK(launch_bc_sources(sources, nsrc, l0.rp, l0.ci, l0.sigma, st, h->nsm));
+        lv.push_back(l0);
+    }
+    int *vci = nullptr;
+    long long vcap = 0;
+    for (;;) {
+        const Level &cur = lv.back();
+        // visited pattern: levels 0..d as CSR
+        CK(launch_bitmap_or(cur.rp, cur.ci, nsrc, wpr, bm, st, h->nsm));
+        CK(launch_bitmap_counts(bm, nsrc, wpr, vcnt, st, h->nsm));
+        CK(launch_excl_scan_int(vcnt, nsrc, vrp, vtb, st, h->nsm));
+        int vtot = 0;
+        CK(cudaMemcpyAsync(&vtot, vrp + nsrc, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (vtot > vcap) {
+            vcap = std::max<long long>(vtot, vcap * 2);
+            vci = static_cast<int *>(take(sizeof(int) * (size_t)vcap));
+            if (!vci) return fail(h, MSGEMM_ERR_OOM, "bc workspace allocation failed");
+        }
+        CK(launch_bitmap_cols(bm, nsrc, wpr, vrp, vci, st, h->nsm));
+        const msgemm_csr V{nsrc, n, vtot, vrp, vci, nullptr};
+        const msgemm_csr F{nsrc, n, cur.nnz, cur.rp, cur.ci, cur.sigma};
+        msgemm_csr_out C;
+        CKS(alloc_out(h, &V, 1, MSGEMM_PLUS_TIMES_I64, &C));
+        for (void *p : {(void *)C.rowptr, (void *)C.d_nnz}) owned.push_back(p);
+        std::vector<ProdIn> in(1);
+        in[0].M = &V; in[0].A = &F; in[0].B = &Aone; in[0].comp = 1; in[0].C = &C;
+        CKS(run_pipeline(h, in, MSGEMM_PLUS_TIMES_I64, false, false));
+        for (void *p : {(void *)C.colidx, C.values}) owned.push_back(p);
+        if (C.capacity == 0) break;   // no new vertex in any row (the pipeline set the exact count)
+        lv.push_back(Level{C.rowptr, C.colidx, static_cast<long long *>(C.values), C.capacity});
+    }
+    const int D = (int)lv.size() - 1;   // deepest level
+    if (levels) *levels = D + 1;
+
+    // ---- backward: W_d = 1/sigma_d + T_d on level d, T_{d-1} = level_{d-1} .* (W_d A^T)
+    // (values at each level entry's own slot), delta_{d-1} = sigma_{d-1} T_{d-1}
+    float *T = nullptr;   // T_d, aligned with level d (none for the deepest level)
+    for (int d = D; d >= 2; --d) {
+        const Level &L = lv[d], &P = lv[d - 1];
+        float *W = static_cast<float *>(take(sizeof(float) * (size_t)std::max(L.nnz, 1LL)));
+        float *Tp = static_cast<float *>(take(sizeof(float) * (size_t)std::max(P.nnz, 1LL)));
+        if (!W || !Tp) return fail(h, MSGEMM_ERR_OOM, "bc workspace allocation failed");
+        CK(launch_bc_weight(L.sigma, T, L.nnz, W, st, h->nsm));
+        CK(cudaMemsetAsync(Tp, 0, sizeof(float) * (size_t)std::max(P.nnz, 1LL), st));
+        const msgemm_csr Mx{nsrc, n, P.nnz, P.rp, P.ci, nullptr};
+        const msgemm_csr Wx{nsrc, n, L.nnz, L.rp, L.ci, W};
+        std::vector<ProdIn> in(1);
+        in[0].M = &Mx; in[0].A = &Wx; in[0].B = &AtOne; in[0].comp = 0;
+        in[0].bt_rp = A->rowptr; in[0].bt_ci = A->colidx; in[0].bt_v = f1;
+        in[0].aligned_out = Tp;
+        if (P.nnz > 0) CKS(run_pipeline(h, in, MSGEMM_PLUS_TIMES_F32, false, false));
+        CK(launch_bc_accum(P.ci, P.sigma, Tp, P.nnz, centrality, st, h->nsm));
+        T = Tp;
+    }
+    // the workspace is released in stream order by the guard
+    return MSGEMM_OK;
+}
+
 msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_bytes, int sorted, msgemm_csr_out *At) {
     if (!h || !At) return MSGEMM_ERR_INVALID;
     CKS(check_csr(h, A, "A", value_bytes > 0));
