@@ -13,6 +13,8 @@ Other workloads (also reported under "forms" of the default run):
   bfs       complemented step of multi-source BFS (512 sources, scale 20)
   batched   256 independent fp32 products in one call (vs 256 calls)
   autograd  forward + backward of the differentiable form (R-MAT scale 18)
+  bc        (form only) betweenness centrality from 512 sources, R-MAT scale
+            20, reported in TEPS
 
 --impl reference times the CPU oracle (the plain C program under oracle/)
 on bounded row samples of the same workload.
@@ -452,6 +454,32 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
     return out
 
 
+def bc_form(torch, _lib, synth, dev, stream, flush, steps, warmup, scale=20, nsrc=512):
+    """Betweenness centrality from 512 sources on the R-MAT scale-20 graph
+    (forward and backward stages, Sec. 8.3), timed as whole calls; TEPS =
+    sources x edges / time, edges = undirected edges (stored entries / 2)."""
+    g = synth.rmat_graph(scale, 16, synth.BASE_SEED, synth.S_A)
+    src = synth.pick_sources(g, nsrc, synth.BASE_SEED)
+    h = _lib.Handle(dev)
+    A = _lib.DeviceCsr.from_host(synth.Csr(g.nrows, g.ncols, g.rowptr, g.colidx), device=dev)
+    s = torch.from_numpy(np.asarray(src, np.int32)).to(dev)
+    out = {}
+
+    def step():
+        out["r"] = _lib.msgemm_bc(h, A, s)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times = timed_steps(torch, step, steps, flush, stream)
+    h.close()
+    ms = statistics.median(times)
+    edges = g.nnz / 2
+    return {"config": f"betweenness centrality, {nsrc} sources, R-MAT scale {scale} ef 16 symmetrised "
+                      f"(forward: complemented int64 products, backward: plain fp32 products)",
+            "ms_per_step": round(ms, 3), "levels": out["r"][1], "edges": int(edges),
+            "gteps": round(nsrc * edges / (ms * 1e-3) / 1e9, 3)}
+
+
 def roofline_of(_lib, wl, meas):
     """Roofline of the dominant accumulator kernel (single-product workloads):
     its compulsory bytes (rows of A and M it processes, distinct rows of B
@@ -608,6 +636,9 @@ def run_ours(args):
             forms[name] = dict(config=fw.config["workload"], **form_summary(fw, fm))
             del fm
             torch.cuda.empty_cache()
+        log("form: bc")
+        forms["bc"] = bc_form(torch, _lib, synth, dev, stream, flush, 3, 2)
+        torch.cuda.empty_cache()
         line["forms"] = forms
 
     h.close()
