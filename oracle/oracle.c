@@ -412,3 +412,48 @@ int oracle_bc(int64_t n, const int32_t *rp, const int32_t *ci, int64_t nsrc, con
     }
     return failed ? ORACLE_NOMEM : ORACLE_OK;
 }
+
+/* ---- k-truss, the application of Sec. 8.2: the largest subgraph in which
+ * every edge (u, v) lies on at least k - 2 triangles of the subgraph.
+ * Support of a kept edge = number of w with (u, w) and (v, w) both kept (a
+ * merge of the two kept neighbour rows); edges below k - 2 are removed, and
+ * the supports recomputed, until nothing changes.  A is a symmetric n x n
+ * pattern; self loops are never kept.  keep[e] = 1 for the stored entries of
+ * the k-truss, support[e] their final support (0 where not kept). */
+int oracle_ktruss(int64_t n, const int32_t *rp, const int32_t *ci, int64_t k, uint8_t *keep, int64_t *support,
+                  int64_t *iterations) {
+    int err;
+    if ((err = oracle_validate_csr(n, n, rp, ci))) return err;
+    const int64_t nnz = rp[n];
+    for (int64_t v = 0; v < n; ++v)
+        for (int64_t t = rp[v]; t < rp[v + 1]; ++t) keep[t] = ci[t] != v;
+    int64_t it = 0;
+    for (;;) {
+        ++it;
+        #pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t u = 0; u < n; ++u) {
+            for (int64_t t = rp[u]; t < rp[u + 1]; ++t) {
+                support[t] = 0;
+                if (!keep[t]) continue;
+                const int32_t v = ci[t];
+                int64_t a = rp[u], ea = rp[u + 1], b = rp[v], eb = rp[v + 1], s = 0;
+                while (a < ea && b < eb) {
+                    if (!keep[a]) { ++a; continue; }
+                    if (!keep[b]) { ++b; continue; }
+                    if (ci[a] < ci[b]) ++a;
+                    else if (ci[b] < ci[a]) ++b;
+                    else { ++s; ++a; ++b; }
+                }
+                support[t] = s;
+            }
+        }
+        int64_t removed = 0;
+        for (int64_t t = 0; t < nnz; ++t)
+            if (keep[t] && support[t] < k - 2) { keep[t] = 0; ++removed; }
+        if (!removed) break;
+    }
+    for (int64_t t = 0; t < nnz; ++t)
+        if (!keep[t]) support[t] = 0;
+    *iterations = it;
+    return ORACLE_OK;
+}

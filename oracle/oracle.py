@@ -49,6 +49,8 @@ def _load() -> C.CDLL:
         lib.oracle_grad.restype = i32
         lib.oracle_grad.argtypes = [i64, i64, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.oracle_bc.argtypes = [i64, vp, vp, i64, vp, vp]
+        lib.oracle_ktruss.argtypes = [i64, vp, vp, i64, vp, vp, vp]
+        lib.oracle_ktruss.restype = i32
         lib.oracle_bc.restype = i32
         _lib = lib
     return _lib
@@ -145,3 +147,21 @@ def bc(A, sources) -> np.ndarray:
     if err:
         raise OracleError(ERRORS.get(err, f"error {err}"))
     return out
+
+
+def ktruss(A, k: int):
+    """k-truss of a symmetric pattern A (Sec. 8.2): the largest subgraph where
+    every edge lies on at least k - 2 of its triangles, by repeated support
+    counting and pruning.  Returns (keep mask over A's entries, final support
+    per entry, iterations)."""
+    lib = _load()
+    if A.nrows != A.ncols:
+        raise OracleError("shape mismatch")
+    rp, ci = _arr(A.rowptr, np.int32), _arr(A.colidx, np.int32)
+    keep = np.zeros(len(ci), np.uint8)
+    sup = np.zeros(len(ci), np.int64)
+    it = np.zeros(1, np.int64)
+    err = lib.oracle_ktruss(A.nrows, _ptr(rp), _ptr(ci), int(k), _ptr(keep), _ptr(sup), _ptr(it))
+    if err:
+        raise OracleError(ERRORS.get(err, f"error {err}"))
+    return keep.astype(bool), sup, int(it[0])
