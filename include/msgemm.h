@@ -219,6 +219,19 @@ msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr
 msgemm_status msgemm_bc(msgemm_handle *handle, const msgemm_csr *A, const int32_t *sources, int nsrc,
                         double *centrality, int32_t *levels);
 
+/* k-truss (the application of Sec. 8.2; k = 5 in its benchmark): the
+ * largest subgraph of the symmetric n x n pattern A in which every edge lies
+ * on at least k - 2 triangles of the subgraph.  Each round computes every
+ * edge's support as A .* (A A) on plus-pair (values at each entry's own
+ * slot) and drops the edges below k - 2; it stops when a round drops none.
+ * Self loops are dropped first.  T (allocated like an output) = the truss's
+ * pattern, values = each edge's support (int64).  *iterations (optional) =
+ * rounds run; *products (optional) = products kept by the masks over all
+ * rounds (the sum of the supports; masked flops = 2x).  Synchronises every
+ * round. */
+msgemm_status msgemm_ktruss(msgemm_handle *handle, const msgemm_csr *A, int64_t k, msgemm_csr_out *T,
+                            int32_t *iterations, int64_t *products);
+
 /* Transpose (CSR of A^T), value_bytes in {0, 4, 8}.  At is allocated like an
  * output (capacity nnz(A)).  Column indices within a row of A^T are in
  * arbitrary order unless sorted != 0, which adds a segmented sort pass

@@ -31,7 +31,7 @@ EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_ru
            "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
            "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
            "msgemm_profile_count", "msgemm_profile_entry", "msgemm_last_row_kinds", "msgemm_kernel_launches",
-           "msgemm_transpose_noalloc", "msgemm_bc", "msgemm_destroy"]
+           "msgemm_transpose_noalloc", "msgemm_bc", "msgemm_ktruss", "msgemm_destroy"]
 
 
 class MsgemmError(RuntimeError):
@@ -95,6 +95,7 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "msgemm_kernel_launches": (i64, []),
         "msgemm_transpose_noalloc": (i32, [P(Csr), i32, i32, vp, vp, vp, vp]),
         "msgemm_bc": (i32, [vp, P(Csr), vp, i32, vp, P(C.c_int32)]),
+        "msgemm_ktruss": (i32, [vp, P(Csr), i64, P(CsrOut), P(C.c_int32), P(C.c_int64)]),
         "msgemm_destroy": (None, [vp]),
     }
     for name, (res, args) in sigs.items():
@@ -375,3 +376,15 @@ def msgemm_bc(h: Handle, A: DeviceCsr, sources: torch.Tensor):
     h.check(h.lib.msgemm_bc(h.h, C.byref(a), src.data_ptr() if src.numel() else None, int(src.numel()),
                             out.data_ptr(), C.byref(lv)))
     return out[:A.nrows], int(lv.value)
+
+
+def msgemm_ktruss(h: Handle, A: DeviceCsr, k: int):
+    """k-truss of a symmetric pattern: (Result with each edge's support as
+    int64 values, rounds, products kept over all rounds)."""
+    h.bind_stream()
+    a = A.abi()
+    out = CsrOut()
+    it = C.c_int32(0)
+    prod = C.c_int64(0)
+    h.check(h.lib.msgemm_ktruss(h.h, C.byref(a), int(k), C.byref(out), C.byref(it), C.byref(prod)))
+    return h.result(out, torch.int64), int(it.value), int(prod.value)

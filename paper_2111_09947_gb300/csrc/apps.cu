@@ -1,8 +1,9 @@
-// Elementwise kernels of batched betweenness centrality (msgemm_bc in
-// capi.cu): the masked products of each level run through the library's
-// pipeline; these kernels build the first frontier, the visited pattern of
-// every level (a row-major bitmap turned into CSR for the complemented mask),
-// the backward weights and the dependency sums.
+// Elementwise kernels of the graph applications built on the library's masked
+// products (capi.cu): batched betweenness centrality (msgemm_bc) -- the first
+// frontier, the visited pattern of every level (a row-major bitmap turned
+// into CSR for the complemented mask), the backward weights and the
+// dependency sums -- and k-truss (msgemm_ktruss) -- the entry filter that
+// drops self loops and edges below the support threshold.
 #include "launch.h"
 
 namespace msg {
@@ -88,6 +89,43 @@ __global__ void __launch_bounds__(256) k_bc_accum(const int *ci, const long long
     }
 }
 
+// k-truss filter: entry e of row i is kept iff ci[e] != i and (no support
+// array, or support[e] >= thr).  Counts per row, then the kept entries
+// (and their supports) in order at the scanned row pointers; a warp per row.
+__global__ void __launch_bounds__(256) k_filter_counts(const int *rp, const int *ci, int nrows, const long long *sup,
+                                                       long long thr, int *cnt) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = gw; i < nrows; i += nw) {
+        int c = 0;
+        for (int t = rp[i] + lane; t < rp[i + 1]; t += 32) c += (ci[t] != i && (!sup || sup[t] >= thr)) ? 1 : 0;
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+        if (lane == 0) cnt[i] = c;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_filter_write(const int *rp, const int *ci, int nrows, const long long *sup,
+                                                      long long thr, const int *nrp, int *nci, long long *nsup) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+    for (long long i = gw; i < nrows; i += nw) {
+        int base = nrp[i];
+        for (int t0 = rp[i]; t0 < rp[i + 1]; t0 += 32) {
+            const int t = t0 + lane;
+            const bool k = t < rp[i + 1] && ci[t] != i && (!sup || sup[t] >= thr);
+            const unsigned bal = __ballot_sync(FULL, k);
+            if (k) {
+                const int o = base + __popc(bal & ((1u << lane) - 1u));
+                nci[o] = ci[t];
+                if (nsup) nsup[o] = sup ? sup[t] : 0;
+            }
+            base += __popc(bal);
+        }
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(256) k_fill(T *p, long long n, T v) {
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
@@ -131,6 +169,18 @@ cudaError_t launch_bc_accum(const int *ci, const long long *sigma, const float *
                             cudaStream_t st, int nsm) {
     if (nnz == 0) return cudaSuccess;
     k_bc_accum<<<blocks_for(nnz, nsm, 16), 256, 0, st>>>(ci, sigma, T, nnz, bc);
+    return counted(cudaGetLastError());
+}
+cudaError_t launch_filter_counts(const int *rp, const int *ci, int nrows, const long long *sup, long long thr, int *cnt,
+                                 cudaStream_t st, int nsm) {
+    if (nrows == 0) return cudaSuccess;
+    k_filter_counts<<<blocks_for((long long)nrows * 32, nsm, 16), 256, 0, st>>>(rp, ci, nrows, sup, thr, cnt);
+    return counted(cudaGetLastError());
+}
+cudaError_t launch_filter_write(const int *rp, const int *ci, int nrows, const long long *sup, long long thr,
+                                const int *nrp, int *nci, long long *nsup, cudaStream_t st, int nsm) {
+    if (nrows == 0) return cudaSuccess;
+    k_filter_write<<<blocks_for((long long)nrows * 32, nsm, 16), 256, 0, st>>>(rp, ci, nrows, sup, thr, nrp, nci, nsup);
     return counted(cudaGetLastError());
 }
 cudaError_t launch_fill_i64(long long *p, long long n, long long v, cudaStream_t st, int nsm) {

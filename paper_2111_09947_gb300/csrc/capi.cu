@@ -1372,6 +1372,119 @@ msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *so
     return MSGEMM_OK;
 }
 
+msgemm_status msgemm_ktruss(msgemm_handle *h, const msgemm_csr *A, int64_t k, msgemm_csr_out *T, int32_t *iterations,
+                            int64_t *products) {
+    if (!h || !T) return fail(h, MSGEMM_ERR_INVALID, "NULL handle or output");
+    h->nprof = 0;
+    CKS(check_csr(h, A, "A", false));
+    if (A->nrows != A->ncols) return fail(h, MSGEMM_ERR_SHAPE, "A is %dx%d, not square", A->nrows, A->ncols);
+    if (k < 0) return fail(h, MSGEMM_ERR_INVALID, "k must be >= 0");
+    if (h->validate) CKS(validate_inputs(h, {A}));
+    cudaStream_t st = h->stream;
+    const int n = A->nrows;
+    std::vector<void *> owned;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = dev_alloc(h, bytes);
+        if (p) owned.push_back(p);
+        return p;
+    };
+    struct Guard {
+        msgemm_handle *h;
+        std::vector<void *> &v;
+        ~Guard() {
+            for (void *p : v) dev_free(h, p);
+        }
+    } guard{h, owned};
+    int *cnt = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
+    long long *tb = static_cast<long long *>(take(sizeof(long long) * ((size_t)n / STILE + 4)));
+    long long *dsm = static_cast<long long *>(take(2 * sizeof(long long)));   // [nnz, sum]
+    if (!cnt || !tb || !dsm) return fail(h, MSGEMM_ERR_OOM, "k-truss workspace allocation failed");
+    struct G {
+        int *rp = nullptr, *ci = nullptr;
+        long long *sup = nullptr;
+        long long nnz = 0;
+    };
+    // entries of X kept by the filter (no self loops; support >= thr when given)
+    auto filter = [&](const G &X, long long thr, G &out) -> msgemm_status {
+        out.rp = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
+        if (!out.rp) return fail(h, MSGEMM_ERR_OOM, "k-truss workspace allocation failed");
+        CK(launch_filter_counts(X.rp, X.ci, n, X.sup, thr, cnt, st, h->nsm));
+        CK(launch_excl_scan_int(cnt, n, out.rp, tb, st, h->nsm));
+        int tot = 0;
+        CK(cudaMemcpyAsync(&tot, out.rp + n, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        out.nnz = tot;
+        out.ci = static_cast<int *>(take(sizeof(int) * (size_t)std::max(tot, 1)));
+        if (X.sup) out.sup = static_cast<long long *>(take(sizeof(long long) * (size_t)std::max(tot, 1)));
+        if (!out.ci || (X.sup && !out.sup)) return fail(h, MSGEMM_ERR_OOM, "k-truss workspace allocation failed");
+        CK(launch_filter_write(X.rp, X.ci, n, X.sup, thr, out.rp, out.ci, out.sup, st, h->nsm));
+        return MSGEMM_OK;
+    };
+    G cur;
+    if (n > 0) {
+        G in0;
+        in0.rp = const_cast<int *>(A->rowptr);
+        in0.ci = const_cast<int *>(A->colidx);
+        in0.nnz = A->nnz;
+        CKS(filter(in0, 0, cur));   // self loops never belong to a truss
+    }
+    long long prod = 0;
+    int it = 0;
+    long long *sup = nullptr;
+    while (n > 0) {
+        ++it;
+        // support of every edge: A .* (A A) on plus-pair, at each entry's own slot
+        sup = static_cast<long long *>(take(sizeof(long long) * (size_t)std::max(cur.nnz, 1LL)));
+        if (!sup) return fail(h, MSGEMM_ERR_OOM, "k-truss workspace allocation failed");
+        CK(cudaMemsetAsync(sup, 0, sizeof(long long) * (size_t)std::max(cur.nnz, 1LL), st));
+        if (cur.nnz > 0) {
+            const msgemm_csr X{n, n, cur.nnz, cur.rp, cur.ci, nullptr};
+            std::vector<ProdIn> in(1);
+            in[0].M = &X; in[0].A = &X; in[0].B = &X; in[0].comp = 0;
+            in[0].aligned_out = sup;
+            CKS(run_pipeline(h, in, MSGEMM_PLUS_PAIR_I64, true, false));
+            // products kept by the mask = the sum of the supports
+            CK(cudaMemcpyAsync(dsm, &cur.nnz, sizeof(long long), cudaMemcpyHostToDevice, st));
+            CK(launch_reduce_sum(MSGEMM_PLUS_PAIR_I64, sup, dsm, dsm + 1, st, h->nsm));
+            long long sum = 0;
+            CK(cudaMemcpyAsync(&sum, dsm + 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            prod += sum;
+        }
+        G next;
+        cur.sup = sup;
+        CKS(filter(cur, k - 2, next));
+        if (next.nnz == cur.nnz) break;   // nothing pruned: cur is the k-truss, sup its supports
+        cur = next;
+        cur.sup = nullptr;
+    }
+    // output: the truss's pattern with each edge's support
+    memset(T, 0, sizeof *T);
+    T->nrows = n;
+    T->ncols = n;
+    T->capacity = cur.nnz;
+    T->rowptr = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * ((size_t)n + 1)));
+    T->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max(cur.nnz, 1LL)));
+    T->values = dev_alloc(h, sizeof(long long) * (size_t)std::max(cur.nnz, 1LL));
+    T->d_nnz = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t)));
+    if (!T->rowptr || !T->colidx || !T->values || !T->d_nnz) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+    if (n > 0) {
+        CK(cudaMemcpyAsync(T->rowptr, cur.rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
+        if (cur.nnz > 0) {
+            CK(cudaMemcpyAsync(T->colidx, cur.ci, sizeof(int) * (size_t)cur.nnz, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(T->values, sup, sizeof(long long) * (size_t)cur.nnz, cudaMemcpyDeviceToDevice, st));
+        }
+    } else {
+        CK(cudaMemsetAsync(T->rowptr, 0, sizeof(int), st));
+    }
+    const long long tn = cur.nnz;
+    CK(cudaMemcpyAsync(T->d_nnz, &tn, sizeof tn, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));   // host sources above; the workspace is released after this
+    if (iterations) *iterations = it;
+    if (products) *products = prod;
+    return MSGEMM_OK;
+}
+
 msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_bytes, int sorted, msgemm_csr_out *At) {
     if (!h || !At) return MSGEMM_ERR_INVALID;
     CKS(check_csr(h, A, "A", value_bytes > 0));

@@ -83,7 +83,7 @@ cudaError_t launch_tile_bounds(const int *rp, const int *ci, int nrows, int T, i
 cudaError_t launch_segsort(const int *rp, int *ci, void *v, int vbytes, int nrows, int *scratch, cudaStream_t,
                            int nsm);
 
-// bc.cu: elementwise steps of batched betweenness centrality
+// apps.cu: elementwise steps of batched betweenness centrality and k-truss
 cudaError_t launch_bc_sources(const int *src, int nsrc, int *rp, int *ci, long long *v, cudaStream_t, int nsm);
 cudaError_t launch_bitmap_or(const int *rp, const int *ci, int nrows, long long wpr, unsigned *bm, cudaStream_t,
                              int nsm);
@@ -93,6 +93,10 @@ cudaError_t launch_bitmap_cols(const unsigned *bm, int nrows, long long wpr, con
 cudaError_t launch_bc_weight(const long long *sigma, const float *T, long long nnz, float *W, cudaStream_t, int nsm);
 cudaError_t launch_bc_accum(const int *ci, const long long *sigma, const float *T, long long nnz, double *bc,
                             cudaStream_t, int nsm);
+cudaError_t launch_filter_counts(const int *rp, const int *ci, int nrows, const long long *sup, long long thr, int *cnt,
+                                 cudaStream_t, int nsm);
+cudaError_t launch_filter_write(const int *rp, const int *ci, int nrows, const long long *sup, long long thr,
+                                const int *nrp, int *nci, long long *nsup, cudaStream_t, int nsm);
 cudaError_t launch_fill_i64(long long *p, long long n, long long v, cudaStream_t, int nsm);
 cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t, int nsm);
 
