@@ -15,6 +15,8 @@ Other workloads (also reported under "forms" of the default run):
   autograd  forward + backward of the differentiable form (R-MAT scale 18)
   bc        (form only) betweenness centrality from 512 sources, R-MAT scale
             20, reported in TEPS
+  ktruss    (form only) 5-truss of the R-MAT scale-20 graph, masked flops of
+            all rounds / time
 
 --impl reference times the CPU oracle (the plain C program under oracle/)
 on bounded row samples of the same workload.
@@ -480,6 +482,37 @@ def bc_form(torch, _lib, synth, dev, stream, flush, steps, warmup, scale=20, nsr
             "gteps": round(nsrc * edges / (ms * 1e-3) / 1e9, 3)}
 
 
+def ktruss_form(torch, _lib, synth, dev, stream, flush, steps, warmup, scale=20, k=5, autotune=True):
+    """5-truss of the R-MAT scale-20 graph (Sec. 8.2): rounds of supports
+    A .* (A A) on plus-pair and pruning until stable; metric = masked flops of
+    all rounds / total time, the paper's.  The policy is tuned (untimed) on
+    the first round's product."""
+    g = synth.rmat_graph(scale, 16, synth.BASE_SEED, synth.S_A)
+    h = _lib.Handle(dev)
+    A = _lib.DeviceCsr.from_host(synth.Csr(g.nrows, g.ncols, g.rowptr, g.colidx), device=dev)
+    tune_s = None
+    if autotune:
+        t0 = time.perf_counter()
+        _lib.msgemm_autotune(h, [A], [A], [A], "plus_pair_i64")
+        torch.cuda.synchronize()
+        tune_s = round(time.perf_counter() - t0, 2)
+    out = {}
+
+    def step():
+        out["r"] = _lib.msgemm_ktruss(h, A, k)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    times = timed_steps(torch, step, steps, flush, stream)
+    h.close()
+    ms = statistics.median(times)
+    res, rounds, prods = out["r"]
+    return {"config": f"{k}-truss, R-MAT scale {scale} ef 16 symmetrised: rounds of supports A .* (A A) on "
+                      "plus-pair and pruning until no edge drops",
+            "ms_per_step": round(ms, 3), "rounds": rounds, "masked_products": prods, "truss_edges": res.nnz() // 2,
+            "masked_gflops": round(2 * prods / (ms * 1e-3) / 1e9, 3), "autotune_s": tune_s}
+
+
 def roofline_of(_lib, wl, meas):
     """Roofline of the dominant accumulator kernel (single-product workloads):
     its compulsory bytes (rows of A and M it processes, distinct rows of B
@@ -638,6 +671,9 @@ def run_ours(args):
             torch.cuda.empty_cache()
         log("form: bc")
         forms["bc"] = bc_form(torch, _lib, synth, dev, stream, flush, 3, 2)
+        torch.cuda.empty_cache()
+        log("form: ktruss")
+        forms["ktruss"] = ktruss_form(torch, _lib, synth, dev, stream, flush, 2, 1, autotune=not args.no_autotune)
         torch.cuda.empty_cache()
         line["forms"] = forms
 

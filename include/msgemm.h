@@ -99,8 +99,9 @@ typedef enum {
     MSGEMM_OPT_GRID_MIN_FLOPS = 8 /* value >= 0 (default 2^20): plain-mask rows with at least
                                      this many push products, in products wider than one
                                      column tile, are processed as (row, tile) items over the
-                                     whole GPU (at most 4096 such rows per call; the rest and
-                                     every lighter row keep one CTA or warp per row) */
+                                     whole GPU (at most 4096 to 65536 such rows per call, by
+                                     the product's width; the rest and every lighter row keep
+                                     one CTA or warp per row) */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

@@ -94,7 +94,7 @@ __device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra
     const int mnz = m1 - m0;
     const bool index_ok = P.tpos != nullptr || P.n <= pol.tileT[1];
     int kind = choose_kind<SR>(pol, f, mnz, a1 - a0, P.n, P.complement != 0, pull, dot_ok, index_ok);
-    if (kind == K_MSA_G && atomicAdd(ra.gplain, 1) >= GRID_PLAIN_CAP) kind = K_MSA_T;   // piece tables are full
+    if (kind == K_MSA_G && atomicAdd(ra.gplain, 1) >= pol.grid_cap) kind = K_MSA_T;   // piece tables are full
     ra.flops[r] = f;
     ra.kind[r] = (unsigned char)kind;
     ra.cnt[r] = 0;

@@ -451,18 +451,22 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     }
 
     // ---- MSA_G piece tables: sized by the row cap (binning assigns at most
-    // GRID_PLAIN_CAP rows to the kind), so no host synchronisation is needed
+    // Policy.grid_cap rows to the kind), so no host synchronisation is needed
     {
         bool plain_wide = false;
         for (int p = 0; p < P; ++p) plain_wide |= !in[p].comp && dp[p].n > pl.pol.tileT[0];
+        pl.pol.grid_cap = 0;
         if (plain_wide && h->grid > 0) {
-            const size_t slots = (size_t)GRID_PLAIN_CAP * pl.gnt;
-            CKS(grow(h, h->gpbuf, carve_size<int>(slots) * 2 + carve_size<int>(GRID_PLAIN_CAP)));
+            const int cap = (int)std::max<long long>(GRID_CAP_MIN, std::min<long long>(GRID_CAP_MAX,
+                                                                        GRID_TABLE_SLOTS / std::max(pl.gnt, 1)));
+            const size_t slots = (size_t)cap * pl.gnt;
+            CKS(grow(h, h->gpbuf, carve_size<int>(slots) * 2 + carve_size<int>(cap)));
             Carver cg(h->gpbuf.p);
             pl.L.g[0].cnt = cg.take<int>(slots);
             pl.L.g[0].off = cg.take<int>(slots);
-            pl.L.g[0].done = cg.take<int>(GRID_PLAIN_CAP);
-            pl.gp_done_bytes = sizeof(int) * (size_t)GRID_PLAIN_CAP;
+            pl.L.g[0].done = cg.take<int>(cap);
+            pl.gp_done_bytes = sizeof(int) * (size_t)cap;
+            pl.pol.grid_cap = cap;
         }
     }
 

@@ -97,7 +97,7 @@ struct RowArrays {
     long long *bound_total; // complemented: total temporary room
     int *any_dot;           // set when a row picked the pull kernel
     int *nlong;             // binning: rows listed for the one-CTA-per-row pass
-    int *gplain;            // MSA_G rows assigned so far (capped at GRID_PLAIN_CAP)
+    int *gplain;            // MSA_G rows assigned so far (capped at Policy.grid_cap)
     int *sub_count;         // [NKIND * NCLS_FLOPS] rows per (kind, flops class)
     int *sub_fill;          // [NKIND * NCLS_FLOPS] scatter cursors
     unsigned *err;          // device error word
@@ -118,9 +118,11 @@ __device__ __forceinline__ int flops_sub(long long f) {
     return NCLS_FLOPS - 1 - min(NCLS_FLOPS - 1, lg);
 }
 
-// Most MSA_G rows per call: their piece tables are sized on the host before
-// binning, by this cap (rows beyond it take MSA_T).
-constexpr int GRID_PLAIN_CAP = 4096;
+// Most MSA_G rows per call (Policy.grid_cap): their piece tables are sized on
+// the host before binning, by the cap (rows beyond it take MSA_T); the cap is
+// GRID_TABLE_SLOTS / tiles per row, within [GRID_CAP_MIN, GRID_CAP_MAX].
+constexpr long long GRID_TABLE_SLOTS = 1LL << 24;
+constexpr int GRID_CAP_MIN = 4096, GRID_CAP_MAX = 65536;
 // Most column tiles of a product for the grid kinds (beyond: one CTA per row).
 constexpr int GRID_MAX_TILES = 4096;
 
@@ -135,6 +137,7 @@ struct Policy {
     int tileT[2];                 // MSA_T tile width for [plain, complemented]
     int grid;                     // grid kinds: 0 off, 1 by the rules below, 2 for every heavy row
     long long grid_min_flops;     // MSA_G: CTA rows with at least this much push work (grid 1)
+    int grid_cap;                 // MSA_G: most rows per call
     unsigned char pref[NCLASS][4];  // families in preference order (F_AUTO = end)
 };
 
