@@ -60,6 +60,9 @@ def parse_args(argv=None):
     ap.add_argument("--no-forms", action="store_true", help="skip the other workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="time the default policy (no untimed tuning first)")
+    ap.add_argument("--sweep", choices=["er", "rmat"], default=None,
+                    help="policy sweeps instead of the benchmark line: Erdos-Renyi n x degrees with every "
+                         "accumulator forced vs AUTO, or triangle counting over R-MAT scales")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     return ap.parse_args(argv)
 
@@ -735,10 +738,70 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweep(args):
+    """Sweeps of the policy (one JSON line per point, then a summary line).
+    er: plain fp32 products of independent Erdos-Renyi A, B, M (n x n) over
+    n, the input degree and the mask degree (the density study of Sec. 8.1),
+    each timed with every accumulator family forced and with AUTO; AUTO's
+    time over the best forced one says how well the binning picks.  rmat:
+    triangle counting over R-MAT scales (the scaling study of Sec. 8.2)."""
+    import torch
+    from paper_2111_09947_gb300 import _lib, synth
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    h = _lib.Handle(dev)
+    rows = []
+    if args.sweep == "er":
+        for lg in (12, 14, 16, 18, 20):
+            n = 1 << lg
+            for din in (4, 16, 64):
+                for dm in (1, 16, 256):
+                    if n * max(din, dm) > (1 << 28):
+                        continue
+                    p = synth.random_problem(n, n, n, float(din), float(din), float(dm), synth.BASE_SEED + lg, "f32")
+                    d = {k: _lib.DeviceCsr.from_host(p[k], device=dev) for k in ("M", "A", "B")}
+                    d["M"].values = None
+                    t = {}
+                    for force in ("auto", "msa", "hash", "mca", "dot"):
+                        h.force(force)
+                        fn = lambda: _lib.msgemm_run(h, d["M"], d["A"], d["B"], "plus_times_f32")  # noqa: E731
+                        for _ in range(2):
+                            fn()
+                        torch.cuda.synchronize()
+                        t[force] = round(statistics.median(timed_steps(torch, fn, 5, flush, stream)), 4)
+                    h.force("auto")
+                    best = min(v for k, v in t.items() if k != "auto")
+                    row = {"n": n, "d_in": din, "d_mask": dm, "ms": t,
+                           "best": min((v, k) for k, v in t.items() if k != "auto")[1],
+                           "auto_over_best": round(t["auto"] / best, 3)}
+                    rows.append(row)
+                    print(json.dumps(row), flush=True)
+                    del d
+        r = np.array([x["auto_over_best"] for x in rows])
+        print(json.dumps({"sweep": "er", "points": len(rows), "auto_over_best_median": round(float(np.median(r)), 3),
+                          "auto_over_best_max": round(float(r.max()), 3),
+                          "auto_within_10pct": int((r <= 1.10).sum())}), flush=True)
+    else:
+        for scale in range(8, 21, 2):
+            wl = build_workload("tc", scale, synth.BASE_SEED)
+            meas = measure(torch, _lib, synth, h, wl, dev, stream, flush, 5, 3, None, autotune=not args.no_autotune)
+            ms = statistics.mean(meas["times"])
+            row = {"scale": scale, "nnz_L": wl.config["nnz_L"], "masked_products": wl.kept, "ms": round(ms, 4),
+                   "masked_gflops": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3)}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+        print(json.dumps({"sweep": "rmat", "points": len(rows)}), flush=True)
+    h.close()
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count()))
     run_ours(args)

@@ -160,11 +160,17 @@ int acc_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_I64 ? 8 : 4; 
 int in_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_F32 ? 4 : sr == MSGEMM_PLUS_TIMES_I64 ? 8 : 0; }
 int out_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_F32 ? 4 : 8; }
 
+// Default family order per row class (flops band fb = c / 4, mask band
+// mb = c % 4).  MCA first for small masks, and for rows with few products
+// (fb <= 1: at most 8192) and masks up to 512 entries, whose cost is mostly
+// the accumulator's setup -- copying the mask row is cheaper than building a
+// hash table (an Erdos-Renyi sweep of n 2^12..2^20 and degrees 4..64 x 1..256
+// had MCA ahead of hash on nearly every such point, by up to 4x); hash first
+// for heavier rows.
 void default_pref(unsigned char pref[NCLASS][4]) {
     for (int c = 0; c < NCLASS; ++c) {
-        const int mb = c % 4;
-        // small mask rows: rank by binary search is cheapest; otherwise hash
-        if (mb == 0) { pref[c][0] = F_MSA; pref[c][1] = F_MCA; pref[c][2] = F_HASH; }
+        const int fb = c / 4, mb = c % 4;
+        if (mb == 0 || (fb <= 1 && mb <= 2)) { pref[c][0] = F_MSA; pref[c][1] = F_MCA; pref[c][2] = F_HASH; }
         else { pref[c][0] = F_MSA; pref[c][1] = F_HASH; pref[c][2] = F_MCA; }
         pref[c][3] = F_AUTO;
     }
@@ -350,8 +356,9 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     // ---- B^T for the pull kernel: row pointers in the front of the sequence,
     // entries only if some row picked it.  Building B^T costs a pass over B;
     // for one product it pays only where the pull work (mask entries x
-    // average column length of B) is well below the push work (entries of A
-    // x average row length of B), or when DOT is forced.  Batches always get
+    // average column length of B) is below half the push work (entries of A
+    // x average row length of B) and the push work is at least 32x B's
+    // entries (thresholds from an Erdos-Renyi sweep), or when DOT is forced.  Batches always get
     // the row pointers (one pass over all their B's together): averages miss
     // the skew of graphs whose hubs are shared by A's columns and B's rows,
     // where push work per row far exceeds the estimate, and the binning's
@@ -362,7 +369,9 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         const double bnz = (double)x.B->nnz;
         const double push = (double)x.A->nnz * bnz / std::max(1, x.B->nrows);
         const double pull = (double)x.M->nnz * bnz / std::max(1, x.B->ncols);
-        return pull * 4.0 < push;
+        // B^T costs passes over B: only products with far more push work
+        // than B's entries amortise it
+        return pull * 2.0 < push && push >= 32.0 * bnz;
     };
     if (build_bt && h->allow_dot && (h->force == F_AUTO || h->force == F_DOT)) {
         for (int p = 0; p < P; ++p) {
