@@ -72,3 +72,18 @@ def test_sharded_product_one_rank_group():
         h.close()
     finally:
         dist.destroy_process_group()
+
+
+def test_torch_sparse_csr_interface():
+    """masked_spgemm_csr: torch.sparse_csr tensors in and out."""
+    import paper_2111_09947_gb300 as pkg
+    p = synth.random_problem(400, 300, 500, 6.0, 8.0, 30.0, 99, "f32")
+
+    def t(x, vals=True):
+        v = torch.from_numpy(x.values if vals else np.ones(x.nnz, np.float32)).cuda()
+        return torch.sparse_csr_tensor(torch.from_numpy(x.rowptr).cuda(), torch.from_numpy(x.colidx).cuda(), v,
+                                       size=(x.nrows, x.ncols))
+    C = pkg.masked_spgemm_csr(t(p["M"], False), t(p["A"]), t(p["B"]))
+    assert C.layout == torch.sparse_csr and tuple(C.shape) == (400, 500)
+    res = _lib.DeviceCsr(400, 500, C.crow_indices(), C.col_indices(), C.values())
+    assert_parity(res, O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32"), "plus_times_f32")
