@@ -347,6 +347,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     pl.L.g[0].next = cs.take<unsigned long long>(1);
     pl.L.g[1].next = cs.take<unsigned long long>(1);
     ra.gplain = cs.take<int>(1);
+    pl.L.spec_off = cs.take<int>(1);
     pl.L.gnt = pl.gnt;
     pl.zero_bytes = (size_t)(cs.base + cs.off - pl.zero_begin);
     h->last_kind_count = ra.kind_count;

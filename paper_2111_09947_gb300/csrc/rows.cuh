@@ -40,6 +40,7 @@ struct RowLaunch {
     // int64 tiled kinds: high words, tileT per CTA (CTA b at tile_hi + b * tileT)
     unsigned *tile_hi;
     int tile_hi_slots;
+    int *spec_off;     // grid kinds: raised by the first unsafe tile of a launch
 };
 
 // This CTA's high-word array of the tiled kinds (null unless split int64);
@@ -962,8 +963,20 @@ __global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet 
 // Insertion of product (j, a*b) into a grid item's tile.  Column state bits:
 // bit 0 the mask (ALLOWED for a plain mask, NOTALLOWED when complemented),
 // bit 1 SET; two bits per column in one word array, so a product reads one
-// word to learn both.  A product is added when the mask allows it, and marks
-// its column SET on the column's first product.
+// word to learn both.  A product is added when the mask allows it.
+// TRACK: its column is marked SET on the column's first product.  Without
+// TRACK nothing is marked, and *unsafe is raised by any product that could
+// make a column's sum zero although the column is SET (a value not in
+// (0, 2^31) -- for int64, also any carry into the high word): while no
+// product does, SET <=> the column's sum is non-zero, and the gather reads the
+// values instead of the bits.
+template <int SR>
+__device__ __forceinline__ bool grid_safe(typename Sr<SR>::acc_t v) {
+    if constexpr (SR == MSGEMM_PLUS_TIMES_F32) return v > 0.0f;   // false for 0, negatives, NaN
+    else if constexpr (SR == MSGEMM_PLUS_TIMES_I64) return (long long)v > 0 && v < (1ULL << 31);
+    else return true;                                              // plus-pair: counts >= 1
+}
+
 template <int SR, bool COMP>
 struct GridIns {
     using S = Sr<SR>;
@@ -974,7 +987,9 @@ struct GridIns {
     unsigned *st;
     unsigned *hi;
     unsigned *err;
+    int *unsafe;
     int c0, T;
+    bool track;   // uniform over the CTA
     __device__ __forceinline__ void operator()(int, in_t a, int j, in_t b) const {
         const int jj = j - c0;
         if ((unsigned)jj >= (unsigned)T) {   // only an unsorted row of B gets here
@@ -983,18 +998,34 @@ struct GridIns {
         }
         const unsigned w = st[jj >> 4] >> (2 * (jj & 15));
         if ((w & 1u) != (COMP ? 1u : 0u)) {
-            TA::add(vals, hi, jj, S::mul(a, b));
-            if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
+            const typename S::acc_t v = S::mul(a, b);
+            if (track) {
+                TA::add(vals, hi, jj, v);
+                if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
+            } else if constexpr (TA::split) {
+                // int64: the low word only; a carry would need the high word
+                const unsigned l = (unsigned)v;
+                const unsigned old = atomicAdd(&vals[jj], l);
+                if (!grid_safe<SR>(v) || old + l < old) *unsafe = 1;
+            } else {
+                TA::add(vals, hi, jj, v);
+                if (!grid_safe<SR>(v)) *unsafe = 1;
+            }
         }
     }
 };
 
 // One item.  Entries are written ascending from obase; in the gradient form
 // (aligned, plain masks) values go to their mask entry's own slot instead.
-// Returns the entries written.
+// For a dense tile (the row's push work per tile at least 8x the tile width,
+// so reading every column's value at the gather is cheap) the products first
+// run without SET bits; if any was unsafe (see GridIns) the tile's values are
+// cleared and the products run again with them, and the launch stops
+// speculating (values with signs, say).  Returns the entries written.
 template <int SR, bool COMP>
 __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab,
-                                         int *scratch, int tile, int ntiles, int mq0, int mq1, long long obase) {
+                                         int *scratch, int *s_unsafe, int *s_spec, int tile, int ntiles, int mq0,
+                                         int mq1, long long obase) {
     using S = Sr<SR>;
     using out_t = typename S::out_t;
     using TA = TileAcc<SR>;
@@ -1005,38 +1036,71 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
     unsigned *st = reinterpret_cast<unsigned *>(slab + align8((long long)T * sizeof(lo_t)));   // T / 16 words
     unsigned *hi = tile_hi_of<SR>(L);   // checked by the caller
     const int c0 = tile * T, c1 = min(c.n, c0 + T);
+    if (threadIdx.x == 0) {
+        *s_unsafe = 0;
+        *s_spec = *(volatile int *)L.spec_off == 0;   // one read, shared by the CTA after the barrier
+    }
     for (int q = mq0 + team.tid(); q < mq1; q += team.size()) {
         const int jj = __ldg(P.m_ci + q) - c0;
         if ((unsigned)jj < (unsigned)T) atomicOr(&st[jj >> 4], 1u << (2 * (jj & 15)));
         else atomicOr(L.ra.err, ERR_INTERNAL);
     }
     cta_sync();
-    GridIns<SR, COMP> ins{vals, st, hi, L.ra.err, c0, T};
-    if (ntiles == 1) {
-        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
-    } else {
-        const TileSeg seg{P.tpos, P.tstride, tile};
-        enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, ins);
+    const bool dense = c.flops / ntiles >= 8LL * T;
+    const bool speculate = dense && *s_spec;   // uniform over the CTA
+    GridIns<SR, COMP> ins{vals, st, hi, L.ra.err, s_unsafe, c0, T, !speculate};
+    bool tracked = !speculate;
+    for (int pass = 0; pass < 2; ++pass) {   // pass 1 only after an unsafe product
+        if (ntiles == 1) {
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+        } else {
+            const TileSeg seg{P.tpos, P.tstride, tile};
+            enum_products<SR, true, true>(c.a0, c.a1, P.a_ci, P.a_v, seg, P.b_ci, P.b_v, ins);
+        }
+        cta_sync();
+        if (tracked || *s_unsafe == 0) break;   // uniform over the CTA
+        if (threadIdx.x == 0) *(volatile int *)L.spec_off = 1;
+        // clear the tile's values (low and high words) and run again with SET bits
+        for (int x = team.tid(); x < c1 - c0; x += team.size()) {
+            vals[x] = 0;
+            if constexpr (TA::split) hi[x] = 0;
+        }
+        cta_sync();
+        tracked = true;
+        ins.track = true;
     }
-    cta_sync();
     // gather the SET columns in ascending order; each thread owns a run of
     // state words (16 columns each), and clears them
+    auto set_bits = [&](int w) -> unsigned {   // bit 2b + 1 set for SET column 16 w + b
+        if (tracked) return (st[w] >> 1) & 0x55555555u;
+        unsigned m = 0;
+        const int cend = min(16, (c1 - c0) - 16 * w);
+        for (int b = 0; b < cend; ++b)
+            if (vals[16 * w + b] != 0) m |= 1u << (2 * b);
+        return m;
+    };
     const int nwords = (c1 - c0 + 15) >> 4;
     const int per = (nwords + team.size() - 1) / team.size();
     const int w0 = min(nwords, team.tid() * per), w1 = min(nwords, w0 + per);
     int cw = 0;
-    for (int w = w0; w < w1; ++w) cw += __popc((st[w] >> 1) & 0x55555555u);
+    for (int w = w0; w < w1; ++w) cw += __popc(set_bits(w));
     int total;
     const int off = block_excl_scan(cw, scratch, &total);
     long long o = obase + off;
     out_t *tv = static_cast<out_t *>(L.tmp.v);
     for (int w = w0; w < w1; ++w) {
-        unsigned bits = (st[w] >> 1) & 0x55555555u;
+        unsigned bits = set_bits(w);
         while (bits) {
             const int b = __ffs(bits) - 1;
             bits &= bits - 1;
             const int jj = w * 16 + (b >> 1);
-            const out_t v = S::out(TA::take(vals, hi, jj));
+            out_t v;
+            if (tracked) {
+                v = S::out(TA::take(vals, hi, jj));
+            } else {   // no carry reached the high word: the low word is the value
+                v = S::out((typename S::acc_t)vals[jj]);
+                vals[jj] = 0;
+            }
             if (!COMP && L.aligned) {
                 // the column's rank in the mask row (SET columns are mask columns)
                 int lo = mq0, up = mq1;
@@ -1098,6 +1162,7 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
     __shared__ long long s_item;
     __shared__ int s_mq[2];
     __shared__ int s_last;
+    __shared__ int s_unsafe, s_spec;
     constexpr int KIND = COMP ? K_CMSA_G : K_MSA_G;
     const GridTab &G = L.g[COMP ? 1 : 0];
     const int count = L.ra.kind_count[KIND];
@@ -1140,7 +1205,8 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
         // the piece's offset in the row: mask entries before the tile (plain),
         // or columns before the tile the mask leaves open (complemented)
         const long long rel = COMP ? (long long)c0 - (mq0 - c.m0) : (long long)(mq0 - c.m0);
-        const int cnt = grid_tile<SR, COMP>(P, c, L, smem, scratch, tile, ntiles, mq0, mq1, c.tmp + rel);
+        const int cnt = grid_tile<SR, COMP>(P, c, L, smem, scratch, &s_unsafe, &s_spec, tile, ntiles, mq0, mq1,
+                                            c.tmp + rel);
         __threadfence();   // this item's entries, before the row's completion count
         cta_sync();
         if (threadIdx.x == 0) {
