@@ -313,3 +313,37 @@ def test_backward_through_grid_rows(tmp_path):
     SA, SB = O.grad(Aabs, Babs, Gabs)
     assert np.all(np.abs(dA.cpu().numpy() - dA_ref) <= 1e-5 * SA + 1e-30)
     assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
+
+
+@pytest.mark.parametrize("complement", [True, False])
+@pytest.mark.parametrize("values", ["small_positive", "carry", "f32_positive"])
+def test_grid_speculation_paths(handle, complement, values):
+    """Dense grid tiles (push work per tile >= 8x the tile width) first run
+    without SET bits: small positive values stay on that path; a value that
+    carries into the int64 high word forces the tracked rerun (and stops
+    speculation for the launch); positive fp32 stays speculative."""
+    semiring = "plus_times_f32" if values == "f32_positive" else "plus_times_i64"
+    gen = "f32" if values == "f32_positive" else "i64"
+    q = _varied_rows(16, 4000, 130000, (3900,), (0, 3000, 60000), 91, gen)
+    rng = np.random.default_rng(92)
+    if gen == "i64":
+        q["A"] = q["A"].with_values(rng.integers(1, 4, q["A"].nnz).astype(np.int64))
+        q["B"] = q["B"].with_values(rng.integers(1, 4, q["B"].nnz).astype(np.int64))
+        if values == "carry":
+            va = q["A"].values.copy()
+            va[len(va) // 2] = np.int64(1) << np.int64(40)
+            q["A"] = q["A"].with_values(va)
+    else:
+        q["A"] = q["A"].with_values(rng.uniform(0.5, 1.5, q["A"].nnz).astype(np.float32))
+        q["B"] = q["B"].with_values(rng.uniform(0.5, 1.5, q["B"].nnz).astype(np.float32))
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring, complement=complement,
+                          method=O.ESC if complement else O.MERGE)
+    handle.set_option(_lib.OPT_GRID, 2)
+    try:
+        dq = to_dev(q, semiring)
+        res = _lib.msgemm_run(handle, dq["M"], dq["A"], dq["B"], semiring, complement=complement).trimmed()
+        handle.sync_status()
+        assert handle.bin_counts()["cmsa_g" if complement else "msa_g"] > 0
+        assert_parity(res, ref, semiring, ctx=f"{values} complement={complement}")
+    finally:
+        handle.set_option(_lib.OPT_GRID, 1)
