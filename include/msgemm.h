@@ -63,7 +63,12 @@ typedef enum {
     MSGEMM_ACC_MSA = 1,   /* masked sparse accumulator: dense states + values (Sec. 5.2) */
     MSGEMM_ACC_HASH = 2,  /* hash table keyed by the mask's columns (Sec. 5.3) */
     MSGEMM_ACC_MCA = 3,   /* mask-compressed accumulator indexed by rank in the mask row (Sec. 5.4) */
-    MSGEMM_ACC_DOT = 4    /* pull: masked inner products A_i* . B_*j (Sec. 4.1) */
+    MSGEMM_ACC_DOT = 4,   /* pull: masked inner products A_i* . B_*j (Sec. 4.1) */
+    MSGEMM_ACC_HEAP = 5,  /* multiway merge of the rows of B with the mask row (Sec. 5.5,
+                             Alg. 4 and 5), NInspect = 1; rows with at most 128 stored
+                             entries in A_i*.  Complemented: NInspect = 0 */
+    MSGEMM_ACC_HEAPDOT = 6 /* the same with NInspect unbounded (each row iterator walks to
+                             its next mask column before it is queued) */
 } msgemm_accumulator;
 
 /* Options for msgemm_set_option. */
@@ -96,12 +101,22 @@ typedef enum {
     MSGEMM_OPT_WARP_SLAB = 7,     /* value 1024..24576, a multiple of 16 (default 4608): shared
                                      bytes per warp of the one-warp row kinds (hash, MCA, pull);
                                      rows whose table does not fit go to the one-CTA kinds */
-    MSGEMM_OPT_GRID_MIN_FLOPS = 8 /* value >= 0 (default 2^20): plain-mask rows with at least
+    MSGEMM_OPT_GRID_MIN_FLOPS = 8, /* value >= 0 (default 2^20): plain-mask rows with at least
                                      this many push products, in products wider than one
                                      column tile, are processed as (row, tile) items over the
                                      whole GPU (at most 4096 to 65536 such rows per call, by
                                      the product's width; the rest and every lighter row keep
                                      one CTA or warp per row) */
+    MSGEMM_OPT_PHASES = 9         /* value 1/2 (default 1), for msgemm_run, msgemm_run_batched
+                                     and msgemm_autotune (Sec. 6).  1: one phase -- rows write
+                                     to a temporary the size of the mask (plain) or of the
+                                     per-row bounds (complemented), then a compaction copies
+                                     them into C.  2: a symbolic pass counts each row's entries
+                                     from the indices alone, C is allocated to its exact size
+                                     (capacity == nnz; the call synchronises once more), and a
+                                     numeric pass writes each row in place: no temporary, more
+                                     work.  Two phases never use the (row, tile) grid kinds
+                                     nor a CUDA graph (use_graph is ignored). */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

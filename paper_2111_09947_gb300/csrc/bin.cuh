@@ -36,6 +36,11 @@ __device__ __forceinline__ int pick_family(const Policy &pol, int fam, bool warp
         if (warp && pol.slab[K_MCA_W] > 0 && mca_bytes(mnz, acc, sb) <= pol.slab[K_MCA_W]) return K_MCA_W;
         if (pol.slab[K_MCA_B] > 0 && mca_bytes(mnz, acc, sb) <= pol.slab[K_MCA_B]) return K_MCA_B;
         return -1;
+    case F_HEAP:
+    case F_HEAPDOT:
+        // iterators live in registers: at most HEAP_MAX_ITERS stored entries in A_i*
+        if ((warp || forced) && anz <= HEAP_MAX_ITERS) return fam == F_HEAP ? K_HEAP_W : K_HEAPDOT_W;
+        return -1;
     case F_DOT:
         if (!dot_ok) return -1;
         if (warp && pol.slab[K_DOT_W] > 0 && dot_bytes(anz, mnz, in, acc, sb) <= pol.slab[K_DOT_W]) return K_DOT_W;
@@ -60,6 +65,8 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
         const int heavy = (pol.grid > 0 && index_ok && (n + pol.tileT[1] - 1) / pol.tileT[1] <= GRID_MAX_TILES &&
                            (pol.grid == 2 || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
         if (pol.force == F_MSA) return heavy;
+        if (pol.force == F_HEAP || pol.force == F_HEAPDOT)   // NInspect is 0 under a complement
+            return anz <= HEAP_MAX_ITERS ? K_CHEAP_W : heavy;
         if (warp && pol.slab[K_CHASH_W] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_W])) return K_CHASH_W;
         if (pol.slab[K_CHASH_B] > 0 && chash_slots(bound, mnz, acc, pol.slab[K_CHASH_B])) return K_CHASH_B;
         return heavy;

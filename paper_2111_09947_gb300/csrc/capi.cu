@@ -37,6 +37,7 @@ struct msgemm_handle {
     Buf rows, small, tmp, bt, cur, prods, tix, gbuf, thi, gpbuf;
     unsigned *d_err = nullptr;   // in `small`, persistent
     int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
+    int phases = 1;   // 1: one-phase, 2: symbolic + numeric (MSGEMM_OPT_PHASES)
     long long tile_index_budget = 4LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
@@ -138,7 +139,8 @@ struct PScope {
 
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
-                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g"};
+                                       "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g",
+                                       "heap_w", "heapdot_w", "cheap_w"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -270,7 +272,7 @@ struct Plan {
 };
 
 msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
-                           bool by_value, Plan &pl) {
+                           bool by_value, Plan &pl, bool two_phase = false) {
     const int P = (int)in.size();
     pl.P = P;
     pl.sr = sr;
@@ -310,6 +312,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     const long long R = pl.R, ntiles = pl.ntiles;
     if (R >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "total rows >= 2^31");
     pl.pol = make_policy(h, sr, max_n);
+    if (two_phase) pl.pol.grid = 0;   // grid pieces need a temporary's room
 
     // ---- per-row workspace
     const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 2 + carve_size<unsigned char>(R) +
@@ -413,7 +416,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (pl.aligned) {
         pl.L.tmp.ci = nullptr;
         pl.L.tmp.v = in[0].aligned_out;   // one product in gradient form
-    } else if (!pl.any_comp) {
+    } else if (!pl.any_comp && !two_phase) {
         const int ob = out_bytes(sr);
         CKS(grow(h, h->tmp, carve_size<int>(pl.tmpn) + carve_size<char>((size_t)pl.tmpn * ob)));
         Carver ct(h->tmp.p);
@@ -466,7 +469,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         bool plain_wide = false;
         for (int p = 0; p < P; ++p) plain_wide |= !in[p].comp && dp[p].n > pl.pol.tileT[0];
         pl.pol.grid_cap = 0;
-        if (plain_wide && h->grid > 0) {
+        if (plain_wide && pl.pol.grid > 0) {
             const int cap = (int)std::max<long long>(GRID_CAP_MIN, std::min<long long>(GRID_CAP_MAX,
                                                                         GRID_TABLE_SLOTS / std::max(pl.gnt, 1)));
             const size_t slots = (size_t)cap * pl.gnt;
@@ -480,19 +483,33 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         }
     }
 
-    // ---- accumulator kinds to launch
+    // ---- accumulator kinds to launch (the heap kinds only when the policy
+    // can pick them: forced, or in a class's preference list)
     bool any_plain = false;
     for (int p = 0; p < P; ++p) any_plain |= !in[p].comp;
+    auto uses = [&](int fam) {
+        if (h->force == fam) return true;
+        for (int c = 0; c < NCLASS; ++c)
+            for (int x = 0; x < 4 && pl.pol.pref[c][x] != F_AUTO; ++x)
+                if (pl.pol.pref[c][x] == fam) return h->force == F_AUTO;
+        return false;
+    };
     if (any_plain) {
         if (pl.pol.slab[K_MSA_W]) pl.kinds.push_back(K_MSA_W);
         pl.kinds.insert(pl.kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
         if (!pl.bd.empty() ||
             std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
             pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
+        if (uses(F_HEAP)) pl.kinds.push_back(K_HEAP_W);
+        if (uses(F_HEAPDOT)) pl.kinds.push_back(K_HEAPDOT_W);
         pl.kinds.push_back(K_MSA_T);
         if (pl.L.g[0].cnt) pl.kinds.push_back(K_MSA_G);
     }
-    if (pl.any_comp) pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T, K_CMSA_G});
+    if (pl.any_comp) {
+        pl.kinds.insert(pl.kinds.end(), {K_CHASH_W, K_CHASH_B, K_CMSA_T});
+        if (pl.pol.grid > 0) pl.kinds.push_back(K_CMSA_G);
+        if (h->force == F_HEAP || h->force == F_HEAPDOT) pl.kinds.push_back(K_CHEAP_W);
+    }
 
     // ---- products table
     pl.ps.P = P;
@@ -565,7 +582,7 @@ msgemm_status comp_room(msgemm_handle *h, Plan &pl) {
 
 // Device sequence, middle: B^T entries, tile index, one persistent kernel per
 // kind, per-tile output counts.
-msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
+msgemm_status seq_rows_prep(msgemm_handle *h, Plan &pl) {
     cudaStream_t st = h->stream;
     const RowArrays &ra = pl.L.ra;
     if (!pl.bd.empty()) {
@@ -585,21 +602,35 @@ msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
                                   ra.kind_count, st, h->nsm));
         }
     }
-    RowLaunch L = pl.L;
+    return MSGEMM_OK;
+}
+
+// One persistent kernel per kind, in the instantiation of semiring sr (the
+// two-phase symbolic launch passes plus-pair); heavy buckets sorted first.
+msgemm_status launch_kinds(msgemm_handle *h, Plan &pl, RowLaunch L, msgemm_semiring sr, bool sort) {
+    cudaStream_t st = h->stream;
     for (int kd : pl.kinds) {
-        if (kd == K_MSA_T || kd == K_CMSA_T || kd == K_CMSA_G || kd == K_MSA_G) {
+        if (sort && (kd == K_MSA_T || kd == K_CMSA_T || kd == K_CMSA_G || kd == K_MSA_G)) {
             PScope ph(h, "sort_heavy");
-            CK(launch_sort_heavy(ra, kd, st));
+            CK(launch_sort_heavy(pl.L.ra, kd, st));
         }
         PScope ph(h, kind_name(kd));
         L.slab = pl.pol.slab[kd];
         L.tileT = pl.pol.tileT[(kd == K_CMSA_T || kd == K_CMSA_G) ? 1 : 0];
-        switch (pl.sr) {
+        switch (sr) {
         case MSGEMM_PLUS_TIMES_F32: CK(launch_kind_f32(kd, pl.ps, L, st, h->nsm)); break;
         case MSGEMM_PLUS_TIMES_I64: CK(launch_kind_i64(kd, pl.ps, L, st, h->nsm)); break;
         default: CK(launch_kind_pp(kd, pl.ps, L, st, h->nsm)); break;
         }
     }
+    return MSGEMM_OK;
+}
+
+msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
+    cudaStream_t st = h->stream;
+    const RowArrays &ra = pl.L.ra;
+    CKS(seq_rows_prep(h, pl));
+    CKS(launch_kinds(h, pl, pl.L, pl.sr, true));
     if (pl.aligned) return MSGEMM_OK;
     PScope ph(h, "count");
     CK(launch_count_tiles(pl.ps, ra, pl.ntiles, pl.tile_sums, pl.tile_offs, pl.prod_tot, pl.chunk_start, st, h->nsm));
@@ -607,7 +638,7 @@ msgemm_status seq_middle(msgemm_handle *h, Plan &pl) {
 }
 
 // Complemented products: exact output sizes (synchronises), outputs allocated.
-msgemm_status comp_outputs(msgemm_handle *h, std::vector<ProdIn> &in, Plan &pl) {
+msgemm_status comp_outputs(msgemm_handle *h, std::vector<ProdIn> &in, Plan &pl, bool all = false) {
     cudaStream_t st = h->stream;
     const int P = pl.P;
     std::vector<DevProd> &dp = h->hprods;
@@ -616,7 +647,7 @@ msgemm_status comp_outputs(msgemm_handle *h, std::vector<ProdIn> &in, Plan &pl) 
     CK(cudaStreamSynchronize(st));
     const int ob = out_bytes(pl.sr);
     for (int p = 0; p < P; ++p) {
-        if (!in[p].comp) continue;
+        if (!in[p].comp && !all) continue;
         msgemm_csr_out *C = in[p].C;
         if (tot[p] >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "product %d has >= 2^31 entries", p);
         C->capacity = tot[p];
@@ -766,6 +797,55 @@ msgemm_status run_pipeline(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     return seq_compact(h, pl);
 }
 
+// Sec. 6, two-phase form.  Symbolic: every kind runs in its plus-pair
+// instantiation (indices only; its per-row state is never larger than the
+// other semirings', so the binning's choices fit) and counts each row's
+// entries without writing any.  The counts give C's row pointers; C is then
+// allocated to its exact size (synchronises).  Numeric: every kind runs again
+// in the call's semiring and writes each row straight to its final place.
+// No temporary output and no compaction; the (row, tile) grid kinds are not
+// used (their pieces need a temporary's room), nor the CUDA graph.
+msgemm_status run_two_phase(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool build_bt,
+                            bool validate) {
+    Plan pl;
+    CKS(plan_prepare(h, in, sr, build_bt, true, pl, true));
+    CKS(plan_upload(h, pl));
+    if (validate) {
+        PScope ph(h, "validate");
+        std::vector<const msgemm_csr *> mats;
+        for (const ProdIn &x : in) mats.insert(mats.end(), {x.M, x.A, x.B});
+        CKS(validate_inputs(h, mats));
+    }
+    cudaStream_t st = h->stream;
+    CKS(seq_front(h, pl));
+    CKS(seq_rows_prep(h, pl));
+    RowLaunch L = pl.L;
+    L.count_only = 1;
+    {
+        PScope ph(h, "symbolic");
+        CKS(launch_kinds(h, pl, L, MSGEMM_PLUS_PAIR_I64, true));
+        CK(launch_count_tiles(pl.ps, pl.L.ra, pl.ntiles, pl.tile_sums, pl.tile_offs, pl.prod_tot, pl.chunk_start, st,
+                              h->nsm));
+    }
+    CKS(comp_outputs(h, in, pl, true));
+    {
+        PScope ph(h, "row_offsets");
+        CK(launch_row_offsets(pl.ps, pl.L.ra, pl.ntiles, pl.tile_offs, st, h->nsm));
+        CK(cudaMemsetAsync(pl.L.ra.kind_next, 0, sizeof(int) * NKIND, st));
+    }
+    L = pl.L;
+    L.direct = 1;
+    PScope ph(h, "numeric");
+    return launch_kinds(h, pl, L, sr, false);
+}
+
+// One-phase or two-phase, by the handle's option.
+msgemm_status run_products(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_semiring sr, bool validate,
+                           bool use_graph) {
+    if (h->phases == 2) return run_two_phase(h, in, sr, true, validate);
+    return run_pipeline(h, in, sr, true, validate, use_graph);
+}
+
 msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_semiring sr, msgemm_csr_out *C) {
     memset(C, 0, sizeof *C);
     C->nrows = M->nrows;
@@ -859,7 +939,7 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
         for (int c = 0; c < NCLASS; ++c)
             for (int x = 0; x < 4; ++x) {
                 const double v = num[4 + c * 4 + x];
-                ok &= v >= F_AUTO && v <= F_DOT && v == (int)v;
+                ok &= v >= F_AUTO && v <= F_HEAPDOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
         if (ok) out[key] = t;
@@ -911,11 +991,11 @@ struct Tuner {
         msgemm_status rs = MSGEMM_OK;
         for (int p = 0; p < P && rs == MSGEMM_OK; ++p) {
             const int c = comp ? comp[p] != 0 : 0;
-            rs = alloc_out(h, &M[p], c, sr, &C[p]);
+            rs = alloc_out(h, &M[p], c || h->phases == 2, sr, &C[p]);
             in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = c; in[p].C = &C[p];
         }
         if (rs == MSGEMM_OK && cudaEventRecord(ea, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
-        if (rs == MSGEMM_OK) rs = run_pipeline(h, in, sr, true, false);
+        if (rs == MSGEMM_OK) rs = run_products(h, in, sr, false, false);
         if (rs == MSGEMM_OK && cudaEventRecord(eb, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
         if (rs == MSGEMM_OK && (cudaEventSynchronize(eb) != cudaSuccess || cudaEventElapsedTime(ms, ea, eb) != cudaSuccess))
             rs = fail(h, MSGEMM_ERR_CUDA, "autotune timing failed");
@@ -972,7 +1052,7 @@ struct Tuner {
             memcpy(base, h->pref[c], 4);
             unsigned char best_pref[4];
             memcpy(best_pref, base, 4);
-            for (int fam : {F_MSA, F_HASH, F_MCA}) {
+            for (int fam : {F_MSA, F_HASH, F_MCA, F_HEAP, F_HEAPDOT}) {
                 if (base[0] == fam) continue;
                 unsigned char cand[4] = {(unsigned char)fam, 0, 0, 0};
                 int n = 1;
@@ -1084,7 +1164,7 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     if (!h) return MSGEMM_ERR_INVALID;
     switch (opt) {
     case MSGEMM_OPT_FORCE_ACCUM:
-        if (value < MSGEMM_ACC_AUTO || value > MSGEMM_ACC_DOT) return fail(h, MSGEMM_ERR_INVALID, "bad accumulator");
+        if (value < MSGEMM_ACC_AUTO || value > MSGEMM_ACC_HEAPDOT) return fail(h, MSGEMM_ERR_INVALID, "bad accumulator");
         h->force = (int)value;
         return MSGEMM_OK;
     case MSGEMM_OPT_VALIDATE: h->validate = value != 0; return MSGEMM_OK;
@@ -1103,6 +1183,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
         if (value < 0 || value > 2) return fail(h, MSGEMM_ERR_INVALID, "grid mode is 0, 1 or 2");
         h->grid = (int)value;
         return MSGEMM_OK;
+    case MSGEMM_OPT_PHASES:
+        if (value != 1 && value != 2) return fail(h, MSGEMM_ERR_INVALID, "phases is 1 or 2");
+        h->phases = (int)value;
+        return MSGEMM_OK;
     default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
     }
 }
@@ -1113,10 +1197,10 @@ msgemm_status msgemm_run(msgemm_handle *h, const msgemm_csr *M, int complement, 
     h->nprof = 0;
     CKS(check_product(h, M, A, B, sr));
     const int comp = complement != 0;
-    CKS(alloc_out(h, M, comp, sr, C));
+    CKS(alloc_out(h, M, comp || h->phases == 2, sr, C));
     std::vector<ProdIn> in(1);
     in[0].M = M; in[0].A = A; in[0].B = B; in[0].comp = comp; in[0].C = C;
-    return run_pipeline(h, in, sr, true, h->validate);
+    return run_products(h, in, sr, h->validate, false);
 }
 
 msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
@@ -1214,10 +1298,10 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
     for (int p = 0; p < nprod; ++p) {
         CKS(check_product(h, &M[p], &A[p], &B[p], sr));
         const int comp = complement ? complement[p] != 0 : 0;
-        CKS(alloc_out(h, &M[p], comp, sr, &C[p]));
+        CKS(alloc_out(h, &M[p], comp || h->phases == 2, sr, &C[p]));
         in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = comp; in[p].C = &C[p];
     }
-    return run_pipeline(h, in, sr, true, h->validate, use_graph != 0);
+    return run_products(h, in, sr, h->validate, use_graph != 0);
 }
 
 msgemm_status msgemm_autotune(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,

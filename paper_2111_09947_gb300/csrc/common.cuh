@@ -33,11 +33,21 @@ enum Kind : int {
     K_CMSA_T,      // complemented: MSA with NOTALLOWED default flipped, tiled
     K_CMSA_G,      // complemented, dense output: (row, tile) items over the whole grid, tile-major
     K_MSA_G,       // plain, heaviest rows of wide products: (row, tile) items, tile-major
+    K_HEAP_W,      // plain: multiway merge of B rows (Sec. 5.5), NInspect = 1
+    K_HEAPDOT_W,   // plain: the same with NInspect unbounded
+    K_CHEAP_W,     // complemented: multiway merge, NInspect = 0
     NKIND
 };
 
 // Families (msgemm_accumulator) for preference lists.
-enum Family : int { F_AUTO = 0, F_MSA = 1, F_HASH = 2, F_MCA = 3, F_DOT = 4 };
+enum Family : int { F_AUTO = 0, F_MSA = 1, F_HASH = 2, F_MCA = 3, F_DOT = 4, F_HEAP = 5, F_HEAPDOT = 6 };
+
+// Heap kinds: one warp per row, each lane holding up to HEAP_PER_LANE row
+// iterators of B in registers; rows with more stored entries of A take
+// another kind.
+constexpr int HEAP_PER_LANE = 4;
+constexpr int HEAP_MAX_ITERS = 32 * HEAP_PER_LANE;
+constexpr int HEAP_INSPECT_ALL = 0x7fffffff;   // NInspect = infinity
 
 // One product of a (possibly batched) call.  All pointers are device pointers.
 struct DevProd {

@@ -36,7 +36,8 @@ inline int kind_threads(int kind) {
     }
 }
 inline bool kind_is_warp(int kind) {
-    return kind == K_MSA_W || kind == K_HASH_W || kind == K_MCA_W || kind == K_DOT_W || kind == K_CHASH_W;
+    return kind == K_MSA_W || kind == K_HASH_W || kind == K_MCA_W || kind == K_DOT_W || kind == K_CHASH_W ||
+           kind == K_HEAP_W || kind == K_HEAPDOT_W || kind == K_CHEAP_W;
 }
 // Dynamic shared memory of a kind's launch for a given slab.
 inline size_t kind_smem(int kind, int slab) {
@@ -53,6 +54,8 @@ cudaError_t launch_count_tiles(const ProdSet &, const RowArrays &, long long nti
 cudaError_t launch_compact(const ProdSet &, const RowArrays &, const TmpOut &, long long ntiles,
                            const long long *tile_offs, const long long *chunk_start, long long max_chunks,
                            int out_bytes, cudaStream_t, int nsm);
+cudaError_t launch_row_offsets(const ProdSet &, const RowArrays &, long long ntiles, const long long *tile_offs,
+                               cudaStream_t, int nsm);
 cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t, int nsm);
 cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t, int nsm);
 cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows,

@@ -317,6 +317,51 @@ cudaError_t launch_compact(const ProdSet &ps, const RowArrays &ra, const TmpOut 
     return cudaGetLastError();
 }
 
+// Two-phase form (Sec. 6): after the symbolic launch, the row pointers of C
+// and each row's final offset, from the per-row counts and the tiles' scanned
+// offsets (one CTA per tile of CTILE rows).
+__global__ void __launch_bounds__(256) k_row_offsets(const __grid_constant__ ProdSet ps,
+                                                     const __grid_constant__ RowArrays ra, long long ntiles,
+                                                     const long long *offs) {
+    __shared__ long long sh[33];
+    constexpr int PER = CTILE / 256;
+    for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const DevProd &P = prod_at(ps, prod_of_tile(ps, t));
+        const long long lt = t - P.tile0;
+        const int i0 = (int)(lt * CTILE);
+        const int i1 = (int)std::min<long long>(P.m, (lt + 1) * CTILE);
+        int c[PER];
+        long long s = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = i0 + threadIdx.x * PER + u;
+            c[u] = i < i1 ? ra.cnt[P.row0 + i] : 0;
+            s += c[u];
+        }
+        long long tot;
+        long long ex = block_excl_scan_ll(s, sh, &tot);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int i = i0 + threadIdx.x * PER + u;
+            if (i < i1) {
+                const long long o = offs[t] + ex;
+                P.c_rp[i] = (int)o;
+                ra.tmpoff[P.row0 + i] = o;
+            }
+            ex += c[u];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_row_offsets(const ProdSet &ps, const RowArrays &ra, long long ntiles, const long long *tile_offs,
+                               cudaStream_t st, int nsm) {
+    if (ntiles == 0) return cudaSuccess;
+    k_row_offsets<<<grid_cap(ntiles, nsm, 8), 256, 0, st>>>(ps, ra, ntiles, tile_offs);
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------ transpose
 __global__ void __launch_bounds__(256) k_col_counts(const int *ci, long long nnz, int *counts) {
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x)

@@ -41,7 +41,18 @@ struct RowLaunch {
     unsigned *tile_hi;
     int tile_hi_slots;
     int *spec_off;     // grid kinds: raised by the first unsafe tile of a launch
+    // two-phase form (Sec. 6): the symbolic launch counts each row's entries
+    // and writes none (count_only); the numeric launch writes them straight
+    // into the product's output arrays at the row's final offset (direct)
+    int count_only;
+    int direct;
 };
+
+// Where a row's entries go: the shared temporary output, or (two-phase
+// numeric launch) the product's own output arrays.
+__device__ __forceinline__ TmpOut out_of(const DevProd &P, const RowLaunch &L) {
+    return L.direct ? TmpOut{P.c_ci, P.c_v} : L.tmp;
+}
 
 // This CTA's high-word array of the tiled kinds (null unless split int64);
 // a grid larger than the workspace flags an error and gets null.
@@ -240,7 +251,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
 template <int SR, bool CTA>
 __device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const typename Sr<SR>::acc_t *acc,
                                               const unsigned *sb, long long tmp, const TmpOut &T,
-                                              int *cnt_slot, int *scratch, int aligned) {
+                                              int *cnt_slot, int *scratch, int aligned, bool write) {
     using S = Sr<SR>;
     using out_t = typename S::out_t;
     Team<CTA> team;
@@ -261,7 +272,7 @@ __device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const t
             const int q = r0 + lane;
             const bool keep = q < mnz && kept(q);
             const unsigned bal = __ballot_sync(FULL, keep);
-            if (keep) {
+            if (keep && write) {
                 const long long o = tmp + base + __popc(bal & lanemask_lt());
                 T.ci[o] = mcols[q];
                 tv[o] = S::out(acc[q]);
@@ -285,7 +296,7 @@ __device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const t
             const int q = r0 + lane;
             const bool keep = q < s1 && kept(q);
             const unsigned bal = __ballot_sync(FULL, keep);
-            if (keep) {
+            if (keep && write) {
                 const long long o = tmp + base + __popc(bal & lanemask_lt());
                 T.ci[o] = mcols[q];
                 tv[o] = S::out(acc[q]);
@@ -366,7 +377,8 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
     };
     enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     team.sync();
-    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned,
+                           !L.count_only);
     team.sync();
 }
 
@@ -403,7 +415,8 @@ __device__ __forceinline__ void row_mca(const DevProd &P, const RowCtx &c, const
     };
     enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     team.sync();
-    gather_ranked<SR, CTA>(mcol, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    gather_ranked<SR, CTA>(mcol, mnz, acc, sb, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned,
+                           !L.count_only);
     team.sync();
 }
 
@@ -448,7 +461,8 @@ __device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const
     };
     enum_products<SR, CTA, false>(c.m0, c.m1, P.m_ci, nullptr, RowSeg{P.bt_rp}, P.bt_ci, P.bt_v, ins);
     team.sync();
-    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, L.tmp, L.ra.cnt + c.r, scratch, L.aligned);
+    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned,
+                           !L.count_only);
     team.sync();
 }
 
@@ -482,7 +496,8 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
     enum_products<SR, false, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     __threadfence_block();
     __syncwarp();
-    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    const TmpOut T = out_of(P, L);
+    out_t *tv = static_cast<out_t *>(T.v);
     int base = 0;
     if (L.aligned) {
         for (int q = c.m0 + lane; q < c.m1; q += 32) {
@@ -503,9 +518,9 @@ __device__ __forceinline__ void row_msa_w(const DevProd &P, const RowCtx &c, con
             else keep = test_bit(setw, j);
         }
         const unsigned bal = __ballot_sync(FULL, keep);
-        if (keep) {
+        if (keep && !L.count_only) {
             const long long o = c.tmp + base + __popc(bal & lanemask_lt());
-            L.tmp.ci[o] = j;
+            T.ci[o] = j;
             tv[o] = S::out(vals[j]);
         }
         base += __popc(bal);
@@ -592,13 +607,16 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
         }
     }
     // occupied slots form a sorted prefix; write it out
-    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    const TmpOut T = out_of(P, L);
+    out_t *tv = static_cast<out_t *>(T.v);
     int cntl = 0;
     for (long long x = team.tid(); x < H; x += team.size()) {
         const unsigned k = keys[x];
         if (k != EMPTY32) {
-            L.tmp.ci[c.tmp + x] = (int)k;
-            tv[c.tmp + x] = S::out(vals[x]);
+            if (!L.count_only) {
+                T.ci[c.tmp + x] = (int)k;
+                tv[c.tmp + x] = S::out(vals[x]);
+            }
             ++cntl;
         }
     }
@@ -618,6 +636,119 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
         if (threadIdx.x == 0) L.ra.cnt[c.r] = red;
     }
     team.sync();
+}
+
+// --------------------------------------------------------------- HEAP rows
+// Sec. 5.5, Alg. 4 and 5: the row is the multiway merge of the rows B_k*
+// (k in A_i*), consumed in ascending column order and intersected with the
+// sorted mask row (or, complemented, with its complement) by a two-way merge.
+// The priority queue of row iterators becomes a warp-wide tournament: lane l
+// holds the iterators of stored entries l, l + 32, ... of A_i* in registers,
+// and a warp minimum over their current columns is the queue's top.  All
+// iterators at the top column are popped together; their products form the
+// column's sum, and each is advanced and re-inserted by Alg. 5's procedure.
+// NI is NInspect: 0 inserts at once; otherwise the iterator first walks
+// towards the current mask entry, giving up after NI mask entries passed
+// (Heap: 1, HeapDot: unbounded).  Complemented rows use NI = 0.  Output comes
+// out ascending and compact.
+template <int SR>
+__device__ __forceinline__ typename Sr<SR>::acc_t warp_sum_acc(typename Sr<SR>::acc_t v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+    return v;
+}
+
+template <int SR, int NI, bool COMP>
+__device__ __forceinline__ void row_heap(const DevProd &P, const RowCtx &c, const RowLaunch &L) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    const int lane = lane_id();
+    const int m1 = c.m1;
+    int pos[HEAP_PER_LANE], end[HEAP_PER_LANE], col[HEAP_PER_LANE];
+    in_t av[HEAP_PER_LANE];
+    int mq = c.m0;   // the mask iterator (warp-uniform)
+    // Alg. 5 for iterator x: its column, or INT_MAX when it leaves the queue
+    auto insert = [&](int x) {
+        int p = pos[x];
+        const int e = end[x];
+        int cc = INT_MAX;
+        if constexpr (NI == 0) {
+            if (p < e) cc = __ldg(P.b_ci + p);
+        } else {
+            int mi = mq, left = NI;
+            while (p < e && mi < m1) {
+                const int bc = __ldg(P.b_ci + p), mc = __ldg(P.m_ci + mi);
+                if (bc == mc) { cc = bc; break; }
+                if (bc < mc) {
+                    ++p;
+                } else {
+                    ++mi;
+                    if (--left == 0) { cc = bc; break; }
+                }
+            }
+        }
+        pos[x] = p;
+        col[x] = cc;
+    };
+#pragma unroll
+    for (int x = 0; x < HEAP_PER_LANE; ++x) {
+        const int t = c.a0 + lane + 32 * x;
+        pos[x] = end[x] = 0;
+        col[x] = INT_MAX;
+        av[x] = in_t{};
+        if (t < c.a1) {
+            const int k = __ldg(P.a_ci + t);
+            pos[x] = __ldg(P.b_rp + k);
+            end[x] = __ldg(P.b_rp + k + 1);
+            if constexpr (S::vals) av[x] = load_val<SR>(P.a_v, t);
+            insert(x);
+        }
+    }
+    const TmpOut T = out_of(P, L);
+    out_t *tv = static_cast<out_t *>(T.v);
+    int o = 0;
+    for (;;) {
+        int lm = INT_MAX;
+#pragma unroll
+        for (int x = 0; x < HEAP_PER_LANE; ++x) lm = min(lm, col[x]);
+        const int top = __reduce_min_sync(FULL, lm);
+        if (top == INT_MAX) break;   // queue empty
+        // advance the mask iterator to its first entry >= top, 32 entries a step
+        while (mq < m1 && __ldg(P.m_ci + mq) < top) {
+            const int q = mq + lane;
+            const int v = q < m1 ? __ldg(P.m_ci + q) : INT_MAX;
+            const unsigned bal = __ballot_sync(FULL, v >= top);
+            mq = bal ? mq + __ffs(bal) - 1 : min(m1, mq + 32);
+        }
+        if (!COMP && mq >= m1) break;   // mask exhausted: nothing more can be kept
+        const bool in_mask = mq < m1 && __ldg(P.m_ci + mq) == top;
+        const bool keep = COMP ? !in_mask : in_mask;
+        acc_t s = 0;
+#pragma unroll
+        for (int x = 0; x < HEAP_PER_LANE; ++x) {
+            if (col[x] == top) {
+                if (keep) s += S::mul(av[x], load_val<SR>(P.b_v, pos[x]));
+                ++pos[x];
+                insert(x);
+            }
+        }
+        if (keep) {
+            s = warp_sum_acc<SR>(s);
+            if (lane == 0 && !L.count_only) {
+                if (!COMP && L.aligned) {
+                    tv[c.tmp + (mq - c.m0)] = S::out(s);
+                } else {
+                    T.ci[c.tmp + o] = top;
+                    tv[c.tmp + o] = S::out(s);
+                }
+            }
+            ++o;
+        }
+    }
+    if (lane == 0) L.ra.cnt[c.r] = o;
+    __syncwarp();
 }
 
 // --------------------------------------------------------------- _T rows
@@ -655,7 +786,8 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
     // cursor of stored entry t of A (product-local index) is cursors[abase + t].
     const bool use_index = P.tpos != nullptr;
     int4 *cur = L.cursors + P.abase;
-    out_t *tv = static_cast<out_t *>(L.tmp.v);
+    const TmpOut Tout = out_of(P, L);
+    out_t *tv = static_cast<out_t *>(Tout.v);
     __shared__ int s_out;    // entries written so far in this row
     __shared__ int s_mpos;   // mask cursor
     if (threadIdx.x == 0) { s_out = 0; s_mpos = c.m0; }
@@ -814,9 +946,9 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                     keep = kept(j - c0);
                 }
                 const unsigned bal = __ballot_sync(FULL, keep);
-                if (keep && !L.aligned) {
+                if (keep && !L.aligned && !L.count_only) {
                     const long long o = c.tmp + base + __popc(bal & lanemask_lt());
-                    L.tmp.ci[o] = j;
+                    Tout.ci[o] = j;
                     tv[o] = S::out(TA::get(vals, hi, j - c0));
                 }
                 base += __popc(bal);
@@ -846,8 +978,11 @@ __device__ __forceinline__ void row_msa_t(const DevProd &P, const RowCtx &c, con
                     const int b = __ffs(bits) - 1;
                     bits &= bits - 1;
                     const int jj = w * 32 + b;
-                    L.tmp.ci[o] = c0 + jj;
-                    tv[o] = S::out(TA::take(vals, hi, jj));
+                    const auto v = S::out(TA::take(vals, hi, jj));
+                    if (!L.count_only) {
+                        Tout.ci[o] = c0 + jj;
+                        tv[o] = v;
+                    }
                     ++o;
                 }
                 setw[w] = 0;
@@ -892,6 +1027,9 @@ __global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet 
         else if (KIND == K_DOT_W) row_dot<SR, false>(P, c, L, slab, nullptr);
         else if (KIND == K_MSA_W) row_msa_w<SR>(P, c, L, slab);
         else if (KIND == K_CHASH_W) row_chash<SR, false>(P, c, L, slab);
+        else if (KIND == K_HEAP_W) row_heap<SR, 1, false>(P, c, L);
+        else if (KIND == K_HEAPDOT_W) row_heap<SR, HEAP_INSPECT_ALL, false>(P, c, L);
+        else if (KIND == K_CHEAP_W) row_heap<SR, 0, true>(P, c, L);
     }
 }
 
@@ -1168,7 +1306,8 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
     const int count = L.ra.kind_count[KIND];
     const int off = L.ra.kind_off[KIND];
     const int T = L.tileT;
-    if (TileAcc<SR>::split && !tile_hi_of<SR>(L)) {   // uniform over the CTA
+    // pieces need the temporary's room: never part of the two-phase form
+    if ((TileAcc<SR>::split && !tile_hi_of<SR>(L)) || L.count_only || L.direct) {   // uniform over the CTA
         if (threadIdx.x == 0 && count > 0) atomicOr(L.ra.err, ERR_INTERNAL);
         return;
     }

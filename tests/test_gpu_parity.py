@@ -16,7 +16,7 @@ from gpu_util import assert_parity, to_dev
 pytestmark = pytest.mark.gpu
 
 SEMIRINGS = ["plus_times_f32", "plus_times_i64", "plus_pair_i64"]
-FORCES = ["auto", "msa", "hash", "mca", "dot"]
+FORCES = ["auto", "msa", "hash", "mca", "dot", "heap", "heapdot"]
 GEN = {"plus_times_f32": "f32", "plus_times_i64": "i64", "plus_pair_i64": "pair"}
 
 
