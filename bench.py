@@ -663,6 +663,9 @@ def run_ours(args):
 
     if rank == 0 and not args.no_forms:
         forms = {}
+        if len(wl.mats) == 1 and not wl.mats[0][3] and wl.name != "autograd":
+            log("form: two_phase")
+            forms["two_phase"] = two_phase_form(torch, _lib, meas["run"], flush, stream, wl, ms_per_step)
         for name in WORKLOADS:
             if name == args.workload:
                 continue
@@ -686,6 +689,29 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def two_phase_form(torch, _lib, run, flush, stream, wl, ms_one):
+    """A workload of one plain product in the two-phase form (Sec. 6) on the
+    same (tuned) handle: a symbolic pass counts, C is allocated exactly, a
+    numeric pass writes in place.  Output memory: one phase holds a temporary
+    and C, both of the mask's size; two phases hold C alone, of its own size."""
+    h = run.h
+    h.set_option(_lib.OPT_PHASES, 2)
+    try:
+        for _ in range(2):
+            run.step()
+        torch.cuda.synchronize()
+        t = statistics.median(timed_steps(torch, run.step, 5, flush, stream))
+    finally:
+        h.set_option(_lib.OPT_PHASES, 1)
+    M = wl.mats[0][0]
+    ent = 4 + (4 if wl.semiring == "plus_times_f32" else 8)   # column index + value
+    return {"config": "the main workload in the two-phase form: symbolic count, exact allocation, numeric pass "
+                      "in place (same tuned policy; the (row, tile) grid kinds are not used)",
+            "ms_per_step": round(t, 4), "one_phase_ms": round(ms_one, 4),
+            "masked_gflops_2p": round(2 * wl.kept / (t * 1e-3) / 1e9, 3),
+            "output_bytes_one_phase": 2 * M.nnz * ent, "output_bytes_two_phase": wl.nnz_c * ent}
 
 
 # ----------------------------------------------------------------- reference arm
@@ -763,25 +789,49 @@ def run_sweep(args):
                     d = {k: _lib.DeviceCsr.from_host(p[k], device=dev) for k in ("M", "A", "B")}
                     d["M"].values = None
                     t = {}
-                    for force in ("auto", "msa", "hash", "mca", "dot"):
-                        h.force(force)
+                    # every family forced (one phase), AUTO, and AUTO in two phases (Sec. 6)
+                    for force in ("auto", "msa", "hash", "mca", "dot", "heap", "heapdot", "auto_2p"):
+                        h.force("auto" if force == "auto_2p" else force)
+                        h.set_option(_lib.OPT_PHASES, 2 if force == "auto_2p" else 1)
                         fn = lambda: _lib.msgemm_run(h, d["M"], d["A"], d["B"], "plus_times_f32")  # noqa: E731
                         for _ in range(2):
                             fn()
                         torch.cuda.synchronize()
                         t[force] = round(statistics.median(timed_steps(torch, fn, 5, flush, stream)), 4)
                     h.force("auto")
-                    best = min(v for k, v in t.items() if k != "auto")
+                    h.set_option(_lib.OPT_PHASES, 1)
+                    # the autotuner on this product (fresh handle, no cache), then timed
+                    ht = _lib.Handle(dev)
+                    _lib.msgemm_autotune(ht, [d["M"]], [d["A"]], [d["B"]], "plus_times_f32")
+                    fn = lambda: _lib.msgemm_run(ht, d["M"], d["A"], d["B"], "plus_times_f32")  # noqa: E731
+                    for _ in range(2):
+                        fn()
+                    torch.cuda.synchronize()
+                    t["tuned"] = round(statistics.median(timed_steps(torch, fn, 5, flush, stream)), 4)
+                    ht.close()
+                    forced = {k: v for k, v in t.items() if k not in ("auto", "auto_2p", "tuned")}
+                    best = min(forced.values())
                     row = {"n": n, "d_in": din, "d_mask": dm, "ms": t,
-                           "best": min((v, k) for k, v in t.items() if k != "auto")[1],
-                           "auto_over_best": round(t["auto"] / best, 3)}
+                           "best": min((v, k) for k, v in forced.items())[1],
+                           "auto_over_best": round(t["auto"] / best, 3),
+                           "tuned_over_best": round(t["tuned"] / best, 3),
+                           "two_phase_over_one": round(t["auto_2p"] / t["auto"], 3)}
                     rows.append(row)
                     print(json.dumps(row), flush=True)
                     del d
         r = np.array([x["auto_over_best"] for x in rows])
+        r2 = np.array([x["two_phase_over_one"] for x in rows])
+        rt = np.array([x["tuned_over_best"] for x in rows])
+        wins = {}
+        for x in rows:
+            wins[x["best"]] = wins.get(x["best"], 0) + 1
         print(json.dumps({"sweep": "er", "points": len(rows), "auto_over_best_median": round(float(np.median(r)), 3),
                           "auto_over_best_max": round(float(r.max()), 3),
-                          "auto_within_10pct": int((r <= 1.10).sum())}), flush=True)
+                          "auto_within_10pct": int((r <= 1.10).sum()), "best_family_counts": wins,
+                          "tuned_over_best_median": round(float(np.median(rt)), 3),
+                          "tuned_over_best_max": round(float(rt.max()), 3),
+                          "tuned_within_10pct": int((rt <= 1.10).sum()),
+                          "two_phase_over_one_median": round(float(np.median(r2)), 3)}), flush=True)
     else:
         for scale in range(8, 21, 2):
             wl = build_workload("tc", scale, synth.BASE_SEED)
@@ -789,6 +839,8 @@ def run_sweep(args):
             ms = statistics.mean(meas["times"])
             row = {"scale": scale, "nnz_L": wl.config["nnz_L"], "masked_products": wl.kept, "ms": round(ms, 4),
                    "masked_gflops": round(2 * wl.kept / (ms * 1e-3) / 1e9, 3)}
+            row.update(two_phase_form(torch, _lib, meas["run"], flush, stream, wl, ms))
+            row.pop("config")
             rows.append(row)
             print(json.dumps(row), flush=True)
         print(json.dumps({"sweep": "rmat", "points": len(rows)}), flush=True)

@@ -1038,6 +1038,15 @@ struct Tuner {
         CK(cudaEventCreate(&eb));
         float best;
         CKS(measure(&best));
+        const Tuned start = current_tuned(h);
+        const float best_start = best;
+        // The class lists are searched with pull off, so that the rows pull
+        // would take meet every family too; pull comes back in the ratio
+        // search at the end, and the start wins if nothing beats it.
+        if (h->allow_dot) {
+            h->dot_ratio = 1e6f;
+            CKS(measure(&best));
+        }
         std::vector<double> work;
         CKS(class_work(work));
         double total = 0;
@@ -1111,6 +1120,7 @@ struct Tuner {
             }
             h->dot_ratio = dbest;
         }
+        if (best > best_start) apply_tuned(h, start);
         return MSGEMM_OK;
     }
 };
