@@ -152,8 +152,10 @@ __device__ __forceinline__ long long warp_len_sum(const int *idx, const int *rp,
 constexpr int SHORT_ROW = 32;
 constexpr int LONG_ROW = 1024;
 
+// (At most 64 registers: four CTAs per SM.  With the compiler's own choice
+// the per-row policy code spilled, and the pass ran 40% slower.)
 template <int SR>
-__global__ void __launch_bounds__(256) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
+__global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ ProdSet ps, const __grid_constant__ RowArrays ra,
                                                    const __grid_constant__ Policy pol, long long *room) {
     __shared__ int hist[NKIND];
     __shared__ int hsub[NKIND * NCLS_FLOPS];

@@ -1057,8 +1057,10 @@ __global__ void __launch_bounds__(256) k_rows_b(const __grid_constant__ ProdSet 
     }
 }
 
+// One CTA per SM (the slab takes the SM's shared memory), so every thread may
+// hold up to 128 registers.
 template <int SR, bool COMP>
-__global__ void __launch_bounds__(512) k_rows_t(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+__global__ void __launch_bounds__(512, 1) k_rows_t(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int scratch[40];
     __shared__ int s_row;
