@@ -25,6 +25,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -172,14 +173,23 @@ def kernel_bytes(kinds, kind_id, M, A, B, C_rp, vb_in, vb_out) -> int:
     return q
 
 
+def code_only(src: str) -> str:
+    """C/CUDA source without comments and blank lines (what the compiler sees
+    of it, up to layout), so that comment edits do not count as changes."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def source_hash() -> str:
+    """Hash of the kernel sources (comments excluded)."""
     h = hashlib.sha1()
     cdir = os.path.join(REPO, "paper_2111_09947_gb300", "csrc")
     for name in sorted(os.listdir(cdir)):
         if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(cdir, name), "rb") as f:
+            with open(os.path.join(cdir, name), encoding="utf-8") as f:
                 h.update(name.encode())
-                h.update(f.read())
+                h.update(code_only(f.read()).encode())
     return h.hexdigest()[:12]
 
 

@@ -246,8 +246,8 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
 
 // ------------------------------------------------------------------ gather
 // Ordered output of rank-indexed accumulators (HASH, MCA, DOT): entries of
-// the mask row in mask order whose state is SET (Sec. 5.2: "gathered in the
-// same order as they are ordered in the mask", stable and sorted).
+// the mask row in mask order whose state is SET (Sec. 5.2 collects the
+// output in the mask's own order, so it comes out sorted).
 template <int SR, bool CTA>
 __device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const typename Sr<SR>::acc_t *acc,
                                               const unsigned *sb, long long tmp, const TmpOut &T,
