@@ -143,6 +143,30 @@ __device__ __forceinline__ long long warp_len_sum(const int *idx, const int *rp,
     return warp_sum_ll(acc);
 }
 
+// Pull work of a row is only compared with its push work f (pull is picked
+// when pull * ratio < f), so its sum may stop once pull * ratio >= f: the
+// partial sum then gives the same decision.  Chunks of 128 as above.
+__device__ __forceinline__ long long warp_len_sum_until(const int *idx, const int *rp, int q0, int q1, double ratio,
+                                                        long long f) {
+    const int lane = lane_id();
+    long long total = 0;
+    for (int b = q0; b < q1; b += 128) {
+        int c[4];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            const int q = b + x * 32 + lane;
+            c[x] = q < q1 ? __ldg(idx + q) : -1;
+        }
+        long long acc = 0;
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+            if (c[x] >= 0) acc += __ldg(rp + c[x] + 1) - __ldg(rp + c[x]);
+        total += warp_sum_ll(acc);
+        if ((double)total * ratio >= (double)f) break;   // warp-uniform
+    }
+    return total;
+}
+
 // Flops, pull work, kind and temporary room of every row.  A warp takes up
 // to 32 consecutive rows, one per lane: rows whose A row and (when pull is
 // possible) mask row have at most SHORT_ROW entries are summed by their own
@@ -192,6 +216,7 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
                 for (int q = m0; q < m1; ++q) {
                     const int j = __ldg(P.m_ci + q);
                     pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
+                    if ((double)pull * pol.dot_ratio >= (double)f) break;   // decided: no pull
                 }
         }
         if (valid && is_huge) ra.perm[atomicAdd(ra.nlong, 1)] = (int)r;   // to k_bin_long
@@ -204,7 +229,7 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
             const int um0 = __shfl_sync(FULL, m0, u), um1 = __shfl_sync(FULL, m1, u);
             const bool udot = __shfl_sync(FULL, dot_ok, u);
             const long long fu = warp_len_sum(Q.a_ci, Q.b_rp, ua0, ua1);
-            const long long pu = udot ? warp_len_sum(Q.m_ci, Q.bt_rp, um0, um1) : 0;
+            const long long pu = udot ? warp_len_sum_until(Q.m_ci, Q.bt_rp, um0, um1, pol.dot_ratio, fu) : 0;
             if (lane == u) {
                 f = fu;
                 pull = pu;
@@ -225,6 +250,7 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
     __shared__ int hist[NKIND];
     __shared__ int hsub[NKIND * NCLS_FLOPS];
     __shared__ long long part[2][8];
+    __shared__ long long s_f;
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
     for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x) hsub[x] = 0;
     __syncthreads();
@@ -245,22 +271,25 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
         int s0, s1;
         share(a0, a1, s0, s1);
         const long long f = warp_len_sum(P.a_ci, P.b_rp, s0, s1);
-        long long pull = 0;
-        if (dot_ok) {
-            share(m0, m1, s0, s1);
-            pull = warp_len_sum(P.m_ci, P.bt_rp, s0, s1);
-        }
-        if (lane_id() == 0) {
-            part[0][w] = f;
-            part[1][w] = pull;
-        }
+        if (lane_id() == 0) part[0][w] = f;
         __syncthreads();
         if (threadIdx.x == 0) {
-            long long ft = 0, pt = 0;
-            for (int q = 0; q < nwarp; ++q) {
-                ft += part[0][q];
-                pt += part[1][q];
-            }
+            long long ft = 0;
+            for (int q = 0; q < nwarp; ++q) ft += part[0][q];
+            s_f = ft;
+        }
+        __syncthreads();
+        const long long ft = s_f;
+        long long pull = 0;
+        if (dot_ok) {   // a warp whose share alone decides against pull stops early
+            share(m0, m1, s0, s1);
+            pull = warp_len_sum_until(P.m_ci, P.bt_rp, s0, s1, pol.dot_ratio, ft);
+        }
+        if (lane_id() == 0) part[1][w] = pull;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long pt = 0;
+            for (int q = 0; q < nwarp; ++q) pt += part[1][q];
             finish_row<SR>(P, ra, pol, room, hist, hsub, r, a0, a1, m0, m1, dot_ok, ft, pt);
         }
         __syncthreads();

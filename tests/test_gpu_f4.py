@@ -191,3 +191,25 @@ def test_two_phase_empty_and_errors(handle):
     assert int(res.nnz()) == 0 and res.rowptr.numel() == 1
     with pytest.raises(_lib.MsgemmError):
         handle.set_option(_lib.OPT_PHASES, 3)
+
+
+@pytest.mark.parametrize("force", ["heap", "heapdot"])
+def test_heap_gradient_form(handle, force):
+    """Backward (values written at each mask entry's own slot) through the heap
+    kinds: dA and dB against the oracle's closed forms."""
+    m, k, n = 300, 400, 500
+    p = synth.random_problem(m, k, n, 6.0, 5.0, 30.0, 4500, "f32")
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    G = synth.Csr(m, n, ref["rowptr"].astype(np.int32), ref["colidx"], synth.upstream_grad(len(ref["colidx"]), 4))
+    dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+    d = to_dev(p, "plus_times_f32")
+    handle.force(force)
+    dA, dB = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G))
+    handle.sync_status()
+    assert handle.bin_counts()[{"heap": "heap_w", "heapdot": "heapdot_w"}[force]] > 100
+    Aabs = p["A"].with_values(np.abs(p["A"].values))
+    Babs = p["B"].with_values(np.abs(p["B"].values))
+    Gabs = G.with_values(np.abs(G.values))
+    SA, SB = O.grad(Aabs, Babs, Gabs)
+    assert np.all(np.abs(dA.cpu().numpy() - dA_ref) <= 1e-5 * SA + 1e-30)
+    assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
