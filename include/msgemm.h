@@ -131,7 +131,13 @@ typedef struct {
 /* Output CSR matrix.  The library fills every field; the arrays come from the
  * handle's allocation callback and belong to the caller afterwards.
  * capacity is the room of colidx/values; the true entry count is *d_nnz
- * (a device int64) and rowptr[nrows] (device). */
+ * (a device int64) and rowptr[nrows] (device).  A call allocates each array
+ * kind (row pointers, entry counts, and columns and values once for the
+ * outputs sized by their mask and once for those sized after counting) in ONE
+ * callback allocation for all its products, carved in 16-byte-aligned
+ * slices: an array either is such an allocation (its callback's return
+ * value: the first product it serves) or lies inside one.  The caller frees
+ * exactly the pointers its callback returned. */
 typedef struct {
     int32_t nrows, ncols;
     int32_t *rowptr;
@@ -199,9 +205,10 @@ msgemm_status msgemm_backward(msgemm_handle *handle, const msgemm_csr *A, const 
  * graph on first use and replayed while the arguments stay the same (the
  * same input pointers and sizes, the same handle options and workspace);
  * outputs may differ between replays: they are passed through a device table
- * uploaded before each replay.  Anything else runs eagerly.  Each C[p] is
- * allocated as in msgemm_run; a complemented product synchronises the host as
- * msgemm_run does. */
+ * uploaded before each replay.  Anything else runs eagerly.  The C[p] share
+ * allocations (see msgemm_csr_out): four callback calls for a batch of plain
+ * masks however many products it holds, two more when some mask is
+ * complemented (those synchronise the host as in msgemm_run). */
 msgemm_status msgemm_run_batched(msgemm_handle *handle, int nprod, const msgemm_csr *M,
                                  const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                                  msgemm_semiring semiring, msgemm_csr_out *C, int use_graph);

@@ -7,8 +7,10 @@ back into tensors.  A missing library is an error: there is no CPU fallback.
 """
 from __future__ import annotations
 
+import bisect
 import ctypes as C
 import os
+from collections.abc import Sequence
 from dataclasses import dataclass
 from typing import Optional
 
@@ -121,13 +123,20 @@ class DeviceCsr:
         return int(self.colidx.numel())
 
     def abi(self) -> Csr:
+        # the checked struct is kept while the fields hold the same objects
+        sig = (self.nrows, self.ncols, id(self.rowptr), id(self.colidx), id(self.values))
+        memo = self.__dict__.get("_abi")
+        if memo is not None and memo[0] == sig:
+            return memo[1]
         for t in (self.rowptr, self.colidx):
             assert t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()
         v = self.values
         if v is not None:
             assert v.is_cuda and v.is_contiguous() and v.numel() == self.nnz
-        return Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(),
-                   self.colidx.data_ptr() if self.nnz else 0, v.data_ptr() if v is not None and self.nnz else 0)
+        c = Csr(self.nrows, self.ncols, self.nnz, self.rowptr.data_ptr(),
+                self.colidx.data_ptr() if self.nnz else 0, v.data_ptr() if v is not None and self.nnz else 0)
+        self.__dict__["_abi"] = (sig, c)
+        return c
 
     @staticmethod
     def from_host(m, device="cuda", values_dtype=None) -> "DeviceCsr":
@@ -141,6 +150,61 @@ class DeviceCsr:
                 v = v.to(values_dtype)
             v = v.to(device)
         return DeviceCsr(m.nrows, m.ncols, rp.contiguous(), ci.contiguous(), v)
+
+
+class _Blocks:
+    """Output allocations taken over from the library; product arrays are
+    views into them."""
+
+    def __init__(self):
+        self.base: list[int] = []
+        self.mem: list[torch.Tensor] = []
+
+    def add(self, ptr: int, t: torch.Tensor):
+        i = bisect.bisect(self.base, ptr)
+        self.base.insert(i, ptr)
+        self.mem.insert(i, t)
+
+    def view(self, ptr: int, dtype: torch.dtype, count: int) -> torch.Tensor:
+        i = bisect.bisect(self.base, ptr) - 1
+        if i < 0:
+            raise KeyError("pointer outside the output allocations")
+        off = ptr - self.base[i]
+        nb = count * torch.empty((), dtype=dtype).element_size()
+        raw = self.mem[i]
+        if off + nb > raw.numel():
+            raise KeyError("array outside its allocation")
+        return raw[off:off + nb].view(dtype)
+
+    def result(self, out: CsrOut, out_dtype: torch.dtype) -> "Result":
+        cap = out.capacity
+        return Result(out.nrows, out.ncols, self.view(out.rowptr, torch.int32, out.nrows + 1),
+                      self.view(out.colidx, torch.int32, cap), self.view(out.values, out_dtype, cap),
+                      self.view(out.d_nnz, torch.int64, 1))
+
+
+class BatchResult(Sequence):
+    """Outputs of msgemm_run_batched; each product's Result is made on first
+    access (views into the batch's shared allocations)."""
+
+    def __init__(self, blocks: _Blocks, outs, out_dtype: torch.dtype):
+        self._blocks, self._outs, self._dt = blocks, outs, out_dtype
+        self._cache: dict[int, "Result"] = {}
+
+    def __len__(self):
+        return len(self._outs)
+
+    def __getitem__(self, p):
+        if isinstance(p, slice):
+            return [self[i] for i in range(*p.indices(len(self)))]
+        if p < 0:
+            p += len(self)
+        if not 0 <= p < len(self):
+            raise IndexError(p)
+        r = self._cache.get(p)
+        if r is None:
+            r = self._cache[p] = self._blocks.result(self._outs[p], self._dt)
+        return r
 
 
 @dataclass
@@ -215,13 +279,20 @@ class Handle:
         raw = self._live.pop(ptr)
         return raw.view(dtype)[:count] if count else raw.view(dtype)[:0]
 
+    def claim(self, outs) -> "_Blocks":
+        """Takes ownership of the allocations that hold these outputs' arrays
+        (a batch carves each array kind of all its products from one
+        allocation whose base is the first product's array)."""
+        blocks = _Blocks()
+        live = self._live
+        for o in outs:
+            for ptr in (o.rowptr, o.colidx, o.values, o.d_nnz):
+                if ptr and ptr in live:
+                    blocks.add(ptr, live.pop(ptr))
+        return blocks
+
     def result(self, out: CsrOut, out_dtype: torch.dtype) -> Result:
-        rp = self.adopt(out.rowptr, torch.int32, out.nrows + 1)
-        cap = out.capacity
-        ci = self.adopt(out.colidx, torch.int32, cap)
-        v = self.adopt(out.values, out_dtype, cap)
-        nz = self.adopt(out.d_nnz, torch.int64, 1)
-        return Result(out.nrows, out.ncols, rp, ci, v, nz)
+        return self.claim([out]).result(out, out_dtype)
 
     def sync_status(self):
         self.check(self.lib.msgemm_sync_status(self.h))
@@ -304,7 +375,7 @@ def msgemm_run_batched(h: Handle, Ms, As, Bs, semiring="plus_times_f32", complem
     if complement is not None:
         comp = (C.c_int * n)(*[int(bool(c)) for c in complement])
     h.check(h.lib.msgemm_run_batched(h.h, n, marr, comp, aarr, barr, sr, outs, int(bool(use_graph))))
-    return [h.result(outs[p], out_dtype(sr)) for p in range(n)]
+    return BatchResult(h.claim(outs), outs, out_dtype(sr))
 
 
 def msgemm_autotune(h: Handle, Ms, As, Bs, semiring="plus_times_f32", complement=None, cache_path=None):

@@ -60,6 +60,8 @@ struct msgemm_handle {
     cudaGraphExec_t gexec = nullptr;
     std::string gkey;
     long long gkernels = 0, gcaptures = 0;
+    // output allocations of the current call (the autotuner frees them)
+    std::vector<void *> out_allocs;
 };
 
 namespace {
@@ -105,6 +107,25 @@ void dev_free(msgemm_handle *h, void *p) {
     if (!p) return;
     if (h->free_fn) h->free_fn(p, h->ctx);
     else cudaFree(p);
+}
+
+// Output arrays of several products from ONE allocation: slices of the given
+// byte sizes (each at least one byte, 16-byte aligned) of a single callback
+// allocation, whose base is the first slice.  All null if it failed.
+std::vector<char *> carve_alloc(msgemm_handle *h, const std::vector<size_t> &sizes) {
+    std::vector<char *> out(sizes.size(), nullptr);
+    if (sizes.empty()) return out;
+    std::vector<size_t> off(sizes.size());
+    size_t total = 0;
+    for (size_t i = 0; i < sizes.size(); ++i) {
+        off[i] = total;
+        total += (std::max<size_t>(sizes[i], 1) + 15) & ~size_t(15);
+    }
+    char *base = static_cast<char *>(dev_alloc(h, total));
+    if (!base) return out;
+    h->out_allocs.push_back(base);
+    for (size_t i = 0; i < sizes.size(); ++i) out[i] = base + off[i];
+    return out;
 }
 
 msgemm_status grow(msgemm_handle *h, Buf &b, size_t bytes) {
@@ -646,14 +667,24 @@ msgemm_status comp_outputs(msgemm_handle *h, std::vector<ProdIn> &in, Plan &pl, 
     CK(cudaMemcpyAsync(tot.data(), pl.prod_tot + P, sizeof(long long) * P, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     const int ob = out_bytes(pl.sr);
+    std::vector<int> who;
+    std::vector<size_t> ci_sz, v_sz;
     for (int p = 0; p < P; ++p) {
         if (!in[p].comp && !all) continue;
-        msgemm_csr_out *C = in[p].C;
         if (tot[p] >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "product %d has >= 2^31 entries", p);
+        who.push_back(p);
+        ci_sz.push_back(sizeof(int) * (size_t)tot[p]);
+        v_sz.push_back((size_t)ob * (size_t)tot[p]);
+    }
+    // one allocation for the columns of all these products, one for the values
+    const std::vector<char *> ci = carve_alloc(h, ci_sz), v = carve_alloc(h, v_sz);
+    for (size_t x = 0; x < who.size(); ++x) {
+        const int p = who[x];
+        msgemm_csr_out *C = in[p].C;
+        if (!ci[x] || !v[x]) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
         C->capacity = tot[p];
-        C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(tot[p], 1)));
-        C->values = dev_alloc(h, (size_t)ob * (size_t)std::max<long long>(tot[p], 1));
-        if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+        C->colidx = reinterpret_cast<int32_t *>(ci[x]);
+        C->values = v[x];
         dp[p].c_ci = C->colidx;
         dp[p].c_v = C->values;
         pl.cap += tot[p];
@@ -846,20 +877,43 @@ msgemm_status run_products(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     return run_pipeline(h, in, sr, true, validate, use_graph);
 }
 
-msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_semiring sr, msgemm_csr_out *C) {
-    memset(C, 0, sizeof *C);
-    C->nrows = M->nrows;
-    C->ncols = M->ncols;
-    C->rowptr = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * ((size_t)M->nrows + 1)));
-    C->d_nnz = static_cast<int64_t *>(dev_alloc(h, sizeof(int64_t)));
-    if (!C->rowptr || !C->d_nnz) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
-    if (!comp) {
-        C->capacity = M->nnz;
-        C->colidx = static_cast<int32_t *>(dev_alloc(h, sizeof(int) * (size_t)std::max<long long>(M->nnz, 1)));
-        C->values = dev_alloc(h, (size_t)out_bytes(sr) * (size_t)std::max<long long>(M->nnz, 1));
-        if (!C->colidx || !C->values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+// Outputs of n products: row pointers and entry counts, and for products
+// sized by their mask (no_room[p] == 0: plain, one phase) columns and values
+// of the mask's size; the rest get columns and values once their exact size
+// is known.  One allocation per array kind for all n products.
+msgemm_status alloc_outs(msgemm_handle *h, int n, const msgemm_csr *M, const int *no_room, msgemm_semiring sr,
+                         msgemm_csr_out *C) {
+    std::vector<size_t> rp_sz(n), nz_sz(n, sizeof(int64_t)), ci_sz, v_sz;
+    for (int p = 0; p < n; ++p) {
+        memset(&C[p], 0, sizeof C[p]);
+        C[p].nrows = M[p].nrows;
+        C[p].ncols = M[p].ncols;
+        rp_sz[p] = sizeof(int) * ((size_t)M[p].nrows + 1);
+        if (!no_room[p]) {
+            ci_sz.push_back(sizeof(int) * (size_t)M[p].nnz);
+            v_sz.push_back((size_t)out_bytes(sr) * (size_t)M[p].nnz);
+        }
+    }
+    const std::vector<char *> rp = carve_alloc(h, rp_sz), nz = carve_alloc(h, nz_sz);
+    const std::vector<char *> ci = carve_alloc(h, ci_sz), v = carve_alloc(h, v_sz);
+    size_t x = 0;
+    for (int p = 0; p < n; ++p) {
+        C[p].rowptr = reinterpret_cast<int32_t *>(rp[p]);
+        C[p].d_nnz = reinterpret_cast<int64_t *>(nz[p]);
+        if (!C[p].rowptr || !C[p].d_nnz) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+        if (!no_room[p]) {
+            C[p].capacity = M[p].nnz;
+            C[p].colidx = reinterpret_cast<int32_t *>(ci[x]);
+            C[p].values = v[x];
+            ++x;
+            if (!C[p].colidx || !C[p].values) return fail(h, MSGEMM_ERR_OOM, "output allocation failed");
+        }
     }
     return MSGEMM_OK;
+}
+
+msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_semiring sr, msgemm_csr_out *C) {
+    return alloc_outs(h, 1, M, &comp, sr, C);
 }
 
 msgemm_status check_product(msgemm_handle *h, const msgemm_csr *M, const msgemm_csr *A, const msgemm_csr *B,
@@ -988,20 +1042,22 @@ struct Tuner {
     msgemm_status run_once(float *ms) {
         std::vector<msgemm_csr_out> C(P);
         std::vector<ProdIn> in(P);
-        msgemm_status rs = MSGEMM_OK;
-        for (int p = 0; p < P && rs == MSGEMM_OK; ++p) {
+        std::vector<int> no_room(P);
+        h->out_allocs.clear();
+        for (int p = 0; p < P; ++p) {
             const int c = comp ? comp[p] != 0 : 0;
-            rs = alloc_out(h, &M[p], c || h->phases == 2, sr, &C[p]);
+            no_room[p] = c || h->phases == 2;
             in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = c; in[p].C = &C[p];
         }
+        msgemm_status rs = alloc_outs(h, P, M, no_room.data(), sr, C.data());
         if (rs == MSGEMM_OK && cudaEventRecord(ea, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
         if (rs == MSGEMM_OK) rs = run_products(h, in, sr, false, false);
         if (rs == MSGEMM_OK && cudaEventRecord(eb, h->stream) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
         if (rs == MSGEMM_OK && (cudaEventSynchronize(eb) != cudaSuccess || cudaEventElapsedTime(ms, ea, eb) != cudaSuccess))
             rs = fail(h, MSGEMM_ERR_CUDA, "autotune timing failed");
         cudaStreamSynchronize(h->stream);
-        for (msgemm_csr_out &c : C)
-            for (void *ptr : {(void *)c.rowptr, (void *)c.colidx, c.values, (void *)c.d_nnz}) dev_free(h, ptr);
+        for (void *ptr : h->out_allocs) dev_free(h, ptr);
+        h->out_allocs.clear();
         return rs;
     }
 
@@ -1207,6 +1263,7 @@ msgemm_status msgemm_run(msgemm_handle *h, const msgemm_csr *M, int complement, 
     h->nprof = 0;
     CKS(check_product(h, M, A, B, sr));
     const int comp = complement != 0;
+    h->out_allocs.clear();
     CKS(alloc_out(h, M, comp || h->phases == 2, sr, C));
     std::vector<ProdIn> in(1);
     in[0].M = M; in[0].A = A; in[0].B = B; in[0].comp = comp; in[0].C = C;
@@ -1305,12 +1362,15 @@ msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *
     h->nprof = 0;
     if (nprod == 0) return MSGEMM_OK;
     std::vector<ProdIn> in(nprod);
+    std::vector<int> no_room(nprod);
     for (int p = 0; p < nprod; ++p) {
         CKS(check_product(h, &M[p], &A[p], &B[p], sr));
         const int comp = complement ? complement[p] != 0 : 0;
-        CKS(alloc_out(h, &M[p], comp || h->phases == 2, sr, &C[p]));
+        no_room[p] = comp || h->phases == 2;
         in[p].M = &M[p]; in[p].A = &A[p]; in[p].B = &B[p]; in[p].comp = comp; in[p].C = &C[p];
     }
+    h->out_allocs.clear();
+    CKS(alloc_outs(h, nprod, M, no_room.data(), sr, C));
     return run_products(h, in, sr, h->validate, use_graph != 0);
 }
 
