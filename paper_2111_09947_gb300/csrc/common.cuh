@@ -347,6 +347,26 @@ template <bool CTA> struct Team {
     }
 };
 
+// Staging of a CSR row segment (n elements of E = 4 or 8 bytes) from global
+// into shared memory by asynchronous copies (cp.async, one element per thread
+// and step, so any start of the row is fine): the loads stay in flight while
+// the team clears its accumulators.  Each thread then waits for its own
+// copies with stage_wait(); the team barrier that follows publishes them.
+template <int E, bool CTA>
+__device__ __forceinline__ void stage_async(void *dst, const void *src, int n) {
+    Team<CTA> team;
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    const char *s = static_cast<const char *>(src);
+    for (int q = team.tid(); q < n; q += team.size()) {
+        if constexpr (E == 4)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d + 4u * q), "l"(s + 4LL * q) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d + 8u * q), "l"(s + 8LL * q) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void cta_sync() {
     __threadfence_block();
     __syncthreads();

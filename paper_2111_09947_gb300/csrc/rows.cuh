@@ -395,12 +395,11 @@ __device__ __forceinline__ void row_mca(const DevProd &P, const RowCtx &c, const
     int *mcol = reinterpret_cast<int *>(slab);
     acc_t *acc = reinterpret_cast<acc_t *>(slab + align8(4LL * mnz));
     unsigned *sb = reinterpret_cast<unsigned *>(slab + align8(4LL * mnz) + align8((long long)mnz * sizeof(acc_t)));
-    for (int q = team.tid(); q < mnz; q += team.size()) {
-        mcol[q] = __ldg(P.m_ci + c.m0 + q);
-        acc[q] = 0;
-    }
+    stage_async<4, CTA>(mcol, P.m_ci + c.m0, mnz);   // the mask row, in flight while the arrays clear
+    for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
     if constexpr (SrSizes<SR>::setbits)
         for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
+    stage_wait();
     team.sync();
     auto ins = [&](int, in_t a, int j, in_t b) {
         int lo = 0, hi = mnz;
@@ -436,13 +435,14 @@ __device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const
     const long long avb = Sr<SR>::vals ? align8((long long)anz * sizeof(in_t)) : 0;
     acc_t *acc = reinterpret_cast<acc_t *>(slab + align8(4LL * anz) + avb);
     unsigned *sb = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(acc) + align8((long long)mnz * sizeof(acc_t)));
-    for (int q = team.tid(); q < anz; q += team.size()) {
-        acol[q] = __ldg(P.a_ci + c.a0 + q);
-        if constexpr (Sr<SR>::vals) aval[q] = load_val<SR>(P.a_v, c.a0 + q);
-    }
+    // the row A_i* (columns and values), in flight while the arrays clear
+    stage_async<4, CTA>(acol, P.a_ci + c.a0, anz);
+    if constexpr (Sr<SR>::vals)
+        stage_async<(int)sizeof(in_t), CTA>(aval, static_cast<const in_t *>(P.a_v) + c.a0, anz);
     for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
     if constexpr (SrSizes<SR>::setbits)
         for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
+    stage_wait();
     team.sync();
     const int m0 = c.m0;
     auto ins = [&](int t, in_t, int k, in_t b) {
@@ -560,11 +560,12 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
     unsigned *keys = reinterpret_cast<unsigned *>(slab);
     acc_t *vals = reinterpret_cast<acc_t *>(slab + align8(4 * H));
     int *mcol = reinterpret_cast<int *>(slab + align8(4 * H) + align8(H * (long long)sizeof(acc_t)));
+    stage_async<4, CTA>(mcol, P.m_ci + c.m0, mnz);   // the mask row, in flight while the table clears
     for (long long h = team.tid(); h < H; h += team.size()) {
         keys[h] = EMPTY32;
         vals[h] = 0;
     }
-    for (int q = team.tid(); q < mnz; q += team.size()) mcol[q] = __ldg(P.m_ci + c.m0 + q);
+    stage_wait();
     team.sync();
     auto ins = [&](int, in_t a, int j, in_t b) {
         int lo = 0, hi = mnz;
