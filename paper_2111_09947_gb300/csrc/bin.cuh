@@ -195,7 +195,18 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
     for (long long r0 = gw * W; r0 < ra.R; r0 += nw * W) {
         const long long r = r0 + lane;
         const bool valid = lane < W && r < ra.R;
-        const int p = valid ? prod_of_row(ps, r) : 0;
+        // the warp's rows are consecutive: when its first and last rows share
+        // a product, so do all (two searches instead of one per lane); the
+        // row kernels read the recorded product instead of searching again
+        int p = 0;
+        if (ps.P > 1) {
+            const long long rl = min(r0 + W, ra.R) - 1;
+            int pe = 0;
+            if (lane < 2) pe = prod_of_row(ps, lane ? rl : r0);
+            const int pf = __shfl_sync(FULL, pe, 0), pl = __shfl_sync(FULL, pe, 1);
+            p = pf == pl ? pf : (valid ? prod_of_row(ps, r) : 0);
+            if (valid && ra.prod) ra.prod[r] = p;
+        }
         const DevProd &P = prod_at(ps, p);
         int a0 = 0, a1 = 0, m0 = 0, m1 = 0;
         if (valid) {
@@ -258,7 +269,7 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
     const int w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int x = blockIdx.x; x < nlong; x += gridDim.x) {
         const long long r = ra.perm[x];
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const DevProd &P = prod_at(ps, row_prod(ps, ra.prod, r));
         const int i = (int)(r - P.row0);
         const int a0 = __ldg(P.a_rp + i), a1 = __ldg(P.a_rp + i + 1);
         const int m0 = __ldg(P.m_rp + i), m1 = __ldg(P.m_rp + i + 1);

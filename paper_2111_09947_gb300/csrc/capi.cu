@@ -336,7 +336,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (two_phase) pl.pol.grid = 0;   // grid pieces need a temporary's room
 
     // ---- per-row workspace
-    const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 2 + carve_size<unsigned char>(R) +
+    const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 3 + carve_size<unsigned char>(R) +
                               carve_size<long long>(ntiles) * 3 + 256 + carve_size<long long>(2 * (size_t)P) +
                               carve_size<long long>((R + STILE - 1) / STILE + 2) + carve_size<DevProd>(P) + 4096;
     CKS(grow(h, h->rows, rows_bytes));
@@ -348,6 +348,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     pl.room = cv.take<long long>(R);
     ra.cnt = cv.take<int>(R);
     ra.perm = cv.take<int>(R);
+    ra.prod = P > 1 ? cv.take<int>(R) : nullptr;
     ra.kind = cv.take<unsigned char>(R);
     pl.tile_sums = cv.take<long long>(ntiles);
     pl.tile_offs = cv.take<long long>(ntiles);

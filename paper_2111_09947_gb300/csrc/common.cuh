@@ -92,6 +92,12 @@ __device__ __forceinline__ int prod_of_row(const ProdSet &ps, long long r) {
     return lo;
 }
 
+// Product of global row r: recorded by the binning pass for batched calls
+// (one load instead of a search of the product table), else searched.
+__device__ __forceinline__ int row_prod(const ProdSet &ps, const int *prod, long long r) {
+    return prod ? prod[r] : prod_of_row(ps, r);
+}
+
 // Per-row arrays of one pipeline run (workspace).
 struct RowArrays {
     long long R;            // total rows over all products
@@ -100,6 +106,7 @@ struct RowArrays {
     int *cnt;               // entries kept in the row
     unsigned char *kind;    // Kind of the row
     int *perm;              // rows grouped by kind
+    int *prod;              // product of each row (batched calls; null for one product)
     int *kind_count;        // [NKIND] rows per kind
     int *kind_off;          // [NKIND + 1] exclusive offsets into perm
     int *kind_fill;         // [NKIND] scatter cursors

@@ -1021,7 +1021,7 @@ __global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet 
         x = __shfl_sync(FULL, x, 0);
         if (x >= count) break;
         const long long r = L.ra.perm[off + x];
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const DevProd &P = prod_at(ps, row_prod(ps, L.ra.prod, r));
         const RowCtx c = row_ctx(P, r, L.ra);
         if (KIND == K_HASH_W) row_hash<SR, false>(P, c, L, slab, nullptr);
         else if (KIND == K_MCA_W) row_mca<SR, false>(P, c, L, slab, nullptr);
@@ -1049,7 +1049,7 @@ __global__ void __launch_bounds__(256) k_rows_b(const __grid_constant__ ProdSet 
         const int x = s_row;
         if (x >= count) break;
         const long long r = L.ra.perm[off + x];
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const DevProd &P = prod_at(ps, row_prod(ps, L.ra.prod, r));
         const RowCtx c = row_ctx(P, r, L.ra);
         if (KIND == K_HASH_B) row_hash<SR, true>(P, c, L, smem, scratch);
         else if (KIND == K_MCA_B) row_mca<SR, true>(P, c, L, smem, scratch);
@@ -1079,7 +1079,7 @@ __global__ void __launch_bounds__(512, 1) k_rows_t(const __grid_constant__ ProdS
         const int x = s_row;
         if (x >= count) break;
         const long long r = L.ra.perm[off + x];
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const DevProd &P = prod_at(ps, row_prod(ps, L.ra.prod, r));
         const RowCtx c = row_ctx(P, r, L.ra);
         row_msa_t<SR, COMP>(P, c, L, smem, scratch);
     }
@@ -1328,7 +1328,7 @@ __global__ void __launch_bounds__(1024, 1) k_rows_g(const __grid_constant__ Prod
         if (item >= nitems) break;
         const int tile = (int)(item / count), x = (int)(item % count);
         const long long r = L.ra.perm[off + x];
-        const DevProd &P = prod_at(ps, prod_of_row(ps, r));
+        const DevProd &P = prod_at(ps, row_prod(ps, L.ra.prod, r));
         const RowCtx c = row_ctx(P, r, L.ra);
         const int ntiles = (c.n + T - 1) / T;
         if (tile >= ntiles) continue;
