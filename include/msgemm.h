@@ -214,11 +214,13 @@ msgemm_status msgemm_run_batched(msgemm_handle *handle, int nprod, const msgemm_
                                  msgemm_semiring semiring, msgemm_csr_out *C, int use_graph);
 
 /* Tunes the handle's binning policy on the given batch by timing it
- * (synchronises; every candidate computes the same result): for each row
- * class carrying work (4 push-flop bands x 4 mask-row bands), the
- * accumulator family tried first (MSA, hash or MCA), then the flop bound
- * between warp and CTA rows, then the pull/push ratio above which rows take
- * the pull kernel.  With cache_path != NULL the tuned policy is stored there
+ * (synchronises; every candidate computes the same result).  Starting with
+ * the pull kernel off: for each row class carrying work (4 push-flop bands x
+ * 4 mask-row bands), the accumulator family tried first (MSA, hash, MCA,
+ * Heap or HeapDot), then the flop bound between warp and CTA rows, the warp
+ * slab, the flop bound of the (row, tile) grid rows, and last the pull/push
+ * ratio below which rows take the pull kernel (or pull kept off).  The
+ * starting policy is kept when no candidate beats it.  With cache_path != NULL the tuned policy is stored there
  * as JSON keyed by device name and semiring, and read back instead of
  * timing when the file already holds that key (a malformed entry is
  * ignored).  nprod == 0 only loads the cache. */
