@@ -220,10 +220,11 @@ msgemm_status msgemm_run_batched(msgemm_handle *handle, int nprod, const msgemm_
  * Heap or HeapDot), then the flop bound between warp and CTA rows, the warp
  * slab, the flop bound of the (row, tile) grid rows, and last the pull/push
  * ratio below which rows take the pull kernel (or pull kept off).  The
- * starting policy is kept when no candidate beats it.  With cache_path != NULL the tuned policy is stored there
- * as JSON keyed by device name and semiring, and read back instead of
- * timing when the file already holds that key (a malformed entry is
- * ignored).  nprod == 0 only loads the cache. */
+ * starting policy is kept when no candidate beats it.  With cache_path !=
+ * NULL the tuned policy is stored there as JSON keyed by device name and
+ * semiring, and read back instead of timing when the file already holds
+ * that key (a malformed entry is ignored).  nprod == 0 only loads the
+ * cache. */
 msgemm_status msgemm_autotune(msgemm_handle *handle, int nprod, const msgemm_csr *M,
                               const int *complement, const msgemm_csr *A, const msgemm_csr *B,
                               msgemm_semiring semiring, const char *cache_path);
