@@ -385,6 +385,25 @@ def oracle_sample_rate(M, A, B, semiring, complement, target_s, rng_seed=7, kept
     return total_f / total_t / 1e9, total_t, total_rows
 
 
+def oracle_threads_form(wl, seconds=1.5):
+    """The oracle on one host core and on all of them, on row samples of a
+    one-product workload (its first product), as masked GFLOP/s."""
+    from oracle import oracle as O
+    M, A, B, comp = wl.mats[0]
+    kfn = kept_from_oracle(M, A, B, comp)
+    cores = os.cpu_count()
+    out = {"unit": "GFLOP/s", "kind": "oracle", "cores": cores}
+    try:
+        for label, n in (("threads_1", 1), ("threads_all", cores)):
+            O.set_threads(n)
+            rate, secs, rows = oracle_sample_rate(M, A, B, wl.semiring, comp, seconds, kept_fn=kfn)
+            out[label] = round(rate, 5)
+            out[label + "_sample"] = f"{rows} of {M.nrows} rows, {secs:.2f} s"
+    finally:
+        O.set_threads(cores)
+    return out
+
+
 def kept_from_oracle(M, A, B, complement):
     """kept_fn for oracle samples: products kept in the sampled rows, counted
     by the oracle in plus-pair (not part of the timed oracle call)."""
@@ -683,6 +702,9 @@ def run_ours(args):
             fw = build_workload(name, None, synth.BASE_SEED)
             fm = measure(torch, _lib, synth, h, fw, dev, stream, flush, 5, 2, None, autotune=not args.no_autotune)
             forms[name] = dict(config=fw.config["workload"], **form_summary(fw, fm))
+            if name in ("er", "autograd") and world == 1:
+                # the CPU oracle on one core and on all (the forward product for autograd)
+                forms[name]["cpu_oracle"] = oracle_threads_form(fw)
             del fm
             torch.cuda.empty_cache()
         log("form: bc")

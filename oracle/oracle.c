@@ -42,6 +42,19 @@
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Threads of the parallel loops below from now on (n >= 1); the oracle's
+ * results do not depend on it.  Used to time the oracle on one core. */
+void oracle_set_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
 
 enum { ORACLE_PT_F32 = 0, ORACLE_PT_I64 = 1, ORACLE_PP_I64 = 2 };
 enum { ORACLE_MERGE = 0, ORACLE_ESC = 1 };

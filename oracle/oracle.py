@@ -52,8 +52,16 @@ def _load() -> C.CDLL:
         lib.oracle_ktruss.argtypes = [i64, vp, vp, i64, vp, vp, vp]
         lib.oracle_ktruss.restype = i32
         lib.oracle_bc.restype = i32
+        lib.oracle_set_threads.restype = None
+        lib.oracle_set_threads.argtypes = [i32]
         _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (results do not
+    depend on it)."""
+    _load().oracle_set_threads(int(n))
 
 
 def _arr(a, dtype):
