@@ -704,7 +704,10 @@ def run_ours(args):
             forms[name] = dict(config=fw.config["workload"], **form_summary(fw, fm))
             if name in ("er", "autograd") and world == 1:
                 # the CPU oracle on one core and on all (the forward product for autograd)
-                forms[name]["cpu_oracle"] = oracle_threads_form(fw)
+                try:
+                    forms[name]["cpu_oracle"] = oracle_threads_form(fw)
+                except Exception as e:   # a side figure: never lose the line for it
+                    forms[name]["cpu_oracle"] = {"error": repr(e)[:200]}
             del fm
             torch.cuda.empty_cache()
         log("form: bc")
