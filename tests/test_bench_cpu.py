@@ -45,3 +45,21 @@ def test_reference_arm_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == "masked GFLOP/s"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_oracle_threads_form_and_thread_independence():
+    """The one-core / all-core oracle figure runs, and the oracle's result does
+    not depend on its thread count."""
+    from oracle import oracle as O
+    wl = bench.build_workload("er", None, synth.BASE_SEED)
+    out = bench.oracle_threads_form(wl, seconds=0.05)
+    assert out["threads_1"] > 0 and out["threads_all"] > 0 and out["cores"] == os.cpu_count()
+    M, A, B, _ = wl.mats[0]
+    try:
+        O.set_threads(1)
+        one = O.masked_spgemm(M, A, B, "plus_times_f32")
+    finally:
+        O.set_threads(os.cpu_count())
+    many = O.masked_spgemm(M, A, B, "plus_times_f32")
+    for k in ("rowptr", "colidx", "values", "S"):
+        assert np.array_equal(one[k], many[k])
