@@ -152,6 +152,16 @@ class DeviceCsr:
         return DeviceCsr(m.nrows, m.ncols, rp.contiguous(), ci.contiguous(), v)
 
 
+_ESIZE: dict = {}
+
+
+def _esize(dtype: torch.dtype) -> int:
+    n = _ESIZE.get(dtype)
+    if n is None:
+        n = _ESIZE[dtype] = torch.empty((), dtype=dtype).element_size()
+    return n
+
+
 class _Blocks:
     """Output allocations taken over from the library; product arrays are
     views into them."""
@@ -170,7 +180,7 @@ class _Blocks:
         if i < 0:
             raise KeyError("pointer outside the output allocations")
         off = ptr - self.base[i]
-        nb = count * torch.empty((), dtype=dtype).element_size()
+        nb = count * _esize(dtype)
         raw = self.mem[i]
         if off + nb > raw.numel():
             raise KeyError("array outside its allocation")
