@@ -213,3 +213,39 @@ def test_heap_gradient_form(handle, force):
     SA, SB = O.grad(Aabs, Babs, Gabs)
     assert np.all(np.abs(dA.cpu().numpy() - dA_ref) <= 1e-5 * SA + 1e-30)
     assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
+
+
+@pytest.mark.parametrize("complement", [False, True])
+def test_heap_register_limit(handle, complement):
+    """A row with exactly 128 stored entries in A_i* fits the heap's registers
+    (4 iterators per lane); one with 129 takes the tiled MSA; both exact."""
+    rng = np.random.default_rng(46)
+    m, k, n = 6, 400, 300
+    rows = [128, 129, 1, 127, 0, 5]
+    rp = np.concatenate([[0], np.cumsum(rows)]).astype(np.int32)
+    ci = np.concatenate([np.sort(rng.choice(k, size=r, replace=False)) for r in rows]).astype(np.int32)
+    A = synth.Csr(m, k, rp, ci, rng.integers(-9, 9, len(ci)).astype(np.int64))
+    p = synth.random_problem(m, k, n, 4.0, 3.0, 40.0, 4600, "i64")
+    p["A"] = A
+    handle.force("heap")
+    res = _run(handle, p, "plus_times_i64", complement)
+    kinds = handle.row_kinds(m)
+    assert_parity(res.trimmed(), _ref(p, "plus_times_i64", complement), "plus_times_i64")
+    heap = _lib.KIND_NAMES.index("cheap_w" if complement else "heap_w")
+    assert kinds[0] == heap and kinds[3] == heap and kinds[1] != heap
+
+
+def test_two_phase_rejects_invalid_input(handle):
+    """Validation runs before the symbolic pass: an unsorted row is refused."""
+    p = synth.random_problem(40, 30, 50, 4.0, 4.0, 6.0, 4700, "f32")
+    A = p["A"]
+    ci = A.colidx.copy()
+    r = next(i for i in range(A.nrows) if A.rowptr[i + 1] - A.rowptr[i] >= 2)
+    ci[A.rowptr[r]], ci[A.rowptr[r] + 1] = ci[A.rowptr[r] + 1], ci[A.rowptr[r]]
+    p["A"] = synth.Csr(A.nrows, A.ncols, A.rowptr, ci, A.values)
+    handle.set_option(_lib.OPT_PHASES, 2)
+    d = to_dev(p, "plus_times_f32")
+    with pytest.raises(_lib.MsgemmError) as e:
+        _lib.msgemm_run(handle, d["M"], d["A"], d["B"], "plus_times_f32")
+    assert e.value.status == 3
+    handle.sync_status()
