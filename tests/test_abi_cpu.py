@@ -39,3 +39,17 @@ def test_binding_loads(libpath):
 
 def test_sm103a_only_build_flags():
     assert _build.ARCH_FLAGS == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_handle_fails_loudly_without_a_gpu(libpath):
+    """With no CUDA device the library refuses to make a handle and says so:
+    the product path has no CPU fallback."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(Exception):
+        _lib.Handle(torch.device("cuda", 0))
+    lib = _lib.load()
+    h = ctypes.c_void_p()
+    status = lib.msgemm_create(ctypes.byref(h), None, _lib.ALLOC_FN(), _lib.FREE_FN(), None)
+    assert status == 7 and not h.value   # MSGEMM_ERR_CUDA, no handle
