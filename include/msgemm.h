@@ -281,8 +281,14 @@ msgemm_status msgemm_transpose(msgemm_handle *handle, const msgemm_csr *A, int v
  * MSGEMM_ERR_OVERFLOW before any work.  The first call on a device looks up
  * the array's device address with that device current; make that first call
  * before any stream capture.  Every call shares the array, which keeps the
- * previous call's contents (each call clears what it needs), so calls that
- * overlap on the GPU race: serialise them (one stream, or events). */
+ * previous call's contents (each call clears what it needs; the sort pass
+ * reuses the cursor area for its list of long rows), so calls that overlap on
+ * the GPU race: serialise them (one stream, or events).  The call returns
+ * before the GPU work is done: the outputs are valid once `stream` reaches
+ * this point, so synchronise the stream, or record an event on it and wait
+ * for that, before reading them from another stream or from the host.
+ * Entries whose column index lies outside [0, ncols(A)) are skipped (never
+ * written anywhere); At_rowptr then counts only the entries in range. */
 msgemm_status msgemm_transpose_noalloc(const msgemm_csr *A, int value_bytes, int sorted, int32_t *At_rowptr,
                                        int32_t *At_colidx, void *At_values, void *stream);
 

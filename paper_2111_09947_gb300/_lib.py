@@ -439,9 +439,12 @@ def msgemm_transpose_noalloc(A: DeviceCsr, value_bytes: int, sorted_rows: bool =
     dt = {0: None, 4: torch.float32, 8: torch.int64}[value_bytes]
     v = torch.empty(max(A.nnz, 1), dtype=dt, device=dev) if dt is not None else None
     a = A.abi()
-    st = lib.msgemm_transpose_noalloc(C.byref(a), int(value_bytes), int(bool(sorted_rows)), rp.data_ptr(),
-                                      ci.data_ptr(), v.data_ptr() if v is not None else None,
-                                      torch.cuda.current_stream(dev).cuda_stream)
+    # the entry point takes its scratch and SM count from the current device:
+    # make A's device current for the call
+    with torch.cuda.device(dev):
+        st = lib.msgemm_transpose_noalloc(C.byref(a), int(value_bytes), int(bool(sorted_rows)), rp.data_ptr(),
+                                          ci.data_ptr(), v.data_ptr() if v is not None else None,
+                                          torch.cuda.current_stream(dev).cuda_stream)
     if st != 0:
         raise MsgemmError(st, "msgemm_transpose_noalloc")
     return rp, ci[:A.nnz], (v[:A.nnz] if v is not None else None)

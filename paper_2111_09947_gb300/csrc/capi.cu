@@ -1312,7 +1312,7 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
         CK(launch_col_counts(X->colidx, X->nnz, X->ncols, t.cur, st, h->nsm));
         CK(launch_excl_scan_int(t.cur, X->ncols, t.rp, t.tb, st, h->nsm));
         CK(cudaMemcpyAsync(t.cur, t.rp, sizeof(int) * ((size_t)X->ncols + 1), cudaMemcpyDeviceToDevice, st));
-        CK(launch_transpose_fill(X->rowptr, X->colidx, X->values, 4, X->nrows, t.rp, t.cur, t.ci, t.v, nullptr, st,
+        CK(launch_transpose_fill(X->rowptr, X->colidx, X->values, 4, X->nrows, X->ncols, t.cur, t.ci, t.v, nullptr, st,
                                  h->nsm));
         if (sorted) CK(launch_segsort(t.rp, t.ci, t.v, 4, X->ncols, t.cur, st, h->nsm));   // cursors are free now
         return MSGEMM_OK;
@@ -1462,7 +1462,7 @@ msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *so
     CK(launch_col_counts(A->colidx, nnz, n, at_cur, st, h->nsm));
     CK(launch_excl_scan_int(at_cur, n, at_rp, tb, st, h->nsm));
     CK(cudaMemcpyAsync(at_cur, at_rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
-    CK(launch_transpose_fill(A->rowptr, A->colidx, nullptr, 0, n, at_rp, at_cur, at_ci, nullptr, nullptr, st, h->nsm));
+    CK(launch_transpose_fill(A->rowptr, A->colidx, nullptr, 0, n, n, at_cur, at_ci, nullptr, nullptr, st, h->nsm));
     CK(launch_segsort(at_rp, at_ci, nullptr, 0, n, at_cur, st, h->nsm));
     CK(cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)(nsrc * wpr), st));
     const msgemm_csr Aone{n, n, nnz, A->rowptr, A->colidx, a1};
@@ -1676,7 +1676,7 @@ msgemm_status msgemm_transpose(msgemm_handle *h, const msgemm_csr *A, int value_
     CK(launch_col_counts(A->colidx, A->nnz, A->ncols, cur, st, h->nsm));
     CK(launch_excl_scan_int(cur, A->ncols, At->rowptr, tbuf, st, h->nsm));
     CK(cudaMemcpyAsync(cur, At->rowptr, sizeof(int) * ((size_t)A->ncols + 1), cudaMemcpyDeviceToDevice, st));
-    CK(launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At->rowptr, cur, At->colidx,
+    CK(launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, A->ncols, cur, At->colidx,
                              At->values, nullptr, st, h->nsm));
     if (sorted) CK(launch_segsort(At->rowptr, At->colidx, At->values, value_bytes, A->ncols, cur, st, h->nsm));
     int64_t nnz = A->nnz;

@@ -58,8 +58,9 @@ cudaError_t launch_row_offsets(const ProdSet &, const RowArrays &, long long nti
                                cudaStream_t, int nsm);
 cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t, int nsm);
 cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long *tile_buf, cudaStream_t, int nsm);
+// Entries whose column is outside [0, ncols) are skipped (not transposed).
 cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows,
-                                  const int *trp, int *cursor, int *tci, void *tv, const int *gate,
+                                  int ncols, int *cursor, int *tci, void *tv, const int *gate,
                                   cudaStream_t, int nsm);
 cudaError_t launch_validate(const int *rp, const int *ci, int nrows, int ncols, long long nnz, unsigned *err,
                             cudaStream_t, int nsm);

@@ -77,7 +77,7 @@ extern "C" msgemm_status msgemm_transpose_noalloc(const msgemm_csr *A, int value
     if (cudaMemcpyAsync(cursor, At_rowptr, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st) !=
         cudaSuccess)
         return MSGEMM_ERR_CUDA;
-    if (launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, At_rowptr, cursor, At_colidx,
+    if (launch_transpose_fill(A->rowptr, A->colidx, A->values, value_bytes, A->nrows, n, cursor, At_colidx,
                               At_values, nullptr, st, nsm) != cudaSuccess)
         return MSGEMM_ERR_CUDA;
     // the cursors (n + 1 ints) are free after the scatter: they hold the sort's row list

@@ -363,15 +363,19 @@ cudaError_t launch_row_offsets(const ProdSet &ps, const RowArrays &ra, long long
 }
 
 // ------------------------------------------------------------ transpose
-__global__ void __launch_bounds__(256) k_col_counts(const int *ci, long long nnz, int *counts) {
-    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x)
-        atomicAdd(&counts[ci[t]], 1);
+// Column indices outside [0, ncols) are skipped here and in the fill below,
+// so a bad index never writes outside the counts/cursor array (ncols + 1).
+__global__ void __launch_bounds__(256) k_col_counts(const int *ci, long long nnz, int ncols, int *counts) {
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < nnz; t += (long long)gridDim.x * blockDim.x) {
+        const int c = ci[t];
+        if ((unsigned)c < (unsigned)ncols) atomicAdd(&counts[c], 1);
+    }
 }
 
 cudaError_t launch_col_counts(const int *ci, long long nnz, int ncols, int *counts, cudaStream_t st, int nsm) {
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * ((size_t)ncols + 1), st);
     if (e != cudaSuccess || nnz == 0) return e;
-    k_col_counts<<<grid_cap((nnz + 255) / 256, nsm, 8), 256, 0, st>>>(ci, nnz, counts); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    k_col_counts<<<grid_cap((nnz + 255) / 256, nsm, 8), 256, 0, st>>>(ci, nnz, ncols, counts); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
     return cudaGetLastError();
 }
 
@@ -425,7 +429,7 @@ cudaError_t launch_excl_scan_int(const int *in, long long n, int *out, long long
 // With gate != NULL the kernel does nothing unless *gate is set.
 template <int VB>
 __global__ void __launch_bounds__(256) k_transpose_fill(const int *rp, const int *ci, const void *v, int nrows,
-                                                        int *cursor, int *tci, void *tv, const int *gate) {
+                                                        int ncols, int *cursor, int *tci, void *tv, const int *gate) {
     if (gate && *gate == 0) return;
     using V = typename std::conditional<VB == 4, unsigned, unsigned long long>::type;
     const int lane = threadIdx.x & 31;
@@ -434,21 +438,22 @@ __global__ void __launch_bounds__(256) k_transpose_fill(const int *rp, const int
     for (long long i = gw; i < nrows; i += nw) {
         const int s = rp[i], e = rp[i + 1];
         for (int t = s + lane; t < e; t += 32) {
-            const int pos = atomicAdd(&cursor[ci[t]], 1);
+            const int c = ci[t];
+            if ((unsigned)c >= (unsigned)ncols) continue;
+            const int pos = atomicAdd(&cursor[c], 1);
             tci[pos] = (int)i;
             if (VB) static_cast<V *>(tv)[pos] = static_cast<const V *>(v)[t];
         }
     }
 }
 
-cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows, const int *trp,
+cudaError_t launch_transpose_fill(const int *rp, const int *ci, const void *v, int vbytes, int nrows, int ncols,
                                   int *cursor, int *tci, void *tv, const int *gate, cudaStream_t st, int nsm) {
     if (nrows == 0) return cudaSuccess;
-    (void)trp;
     const int g = grid_cap(((long long)nrows + 7) / 8, nsm, 16);
-    if (vbytes == 4) { k_transpose_fill<4><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
-    else if (vbytes == 8) { k_transpose_fill<8><<<g, 256, 0, st>>>(rp, ci, v, nrows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
-    else { k_transpose_fill<0><<<g, 256, 0, st>>>(rp, ci, nullptr, nrows, cursor, tci, nullptr, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    if (vbytes == 4) { k_transpose_fill<4><<<g, 256, 0, st>>>(rp, ci, v, nrows, ncols, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else if (vbytes == 8) { k_transpose_fill<8><<<g, 256, 0, st>>>(rp, ci, v, nrows, ncols, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+    else { k_transpose_fill<0><<<g, 256, 0, st>>>(rp, ci, nullptr, nrows, ncols, cursor, tci, nullptr, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     return cudaGetLastError();
 }
 
@@ -664,11 +669,18 @@ __global__ void __launch_bounds__(SEG_CTA) k_segsort_cta(const int *rp, int *ci,
 template <int VB>
 static cudaError_t segsort_t(const int *rp, int *ci, void *v, int nrows, int *list, cudaStream_t st, int nsm) {
     const size_t smem = 4 * SEG_SMEM + (VB ? (size_t)VB * SEG_SMEM : 0);
-    static bool attr = false;
-    if (!attr) {
+    // The shared-memory limit is a per-device attribute of the kernel: raised
+    // once per device (bit d of the mask; racing threads may both set it,
+    // which is harmless).
+    static std::atomic<unsigned long long> attr_set{0};
+    int dev = 0;
+    cudaError_t ed = cudaGetDevice(&dev);
+    if (ed != cudaSuccess) return ed;
+    const unsigned long long bit = dev < 64 ? 1ULL << dev : 0ULL;
+    if (!bit || !(attr_set.load(std::memory_order_acquire) & bit)) {
         cudaError_t e = cudaFuncSetAttribute(k_segsort_cta<VB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        attr = true;
+        attr_set.fetch_or(bit, std::memory_order_acq_rel);
     }
     cudaError_t e = cudaMemsetAsync(list, 0, sizeof(int), st);
     if (e != cudaSuccess) return e;

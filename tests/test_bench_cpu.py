@@ -32,9 +32,34 @@ def test_q_min_and_kernel_bytes():
 def test_oracle_sample_rate_runs():
     p = synth.triangle_counting(scale=10, ef=8, seed=1)
     L = p["M"]
-    rate, secs, rows = bench.oracle_sample_rate(L, L, L, "plus_pair_i64", False, 0.05,
-                                                kept_fn=lambda r, res: int(res["values"].sum()))
-    assert rate >= 0 and secs > 0 and rows > 0
+    kfn = bench.kept_fn_for("plus_pair_i64", L, L, L, False)
+    rate, secs, rows, res = bench.oracle_sample_rate(L, L, L, "plus_pair_i64", False, 5.0, kept_fn=kfn)
+    assert rate >= 0 and secs > 0 and rows == L.nrows      # a small C fits the budget whole
+    # the whole-C count equals the oracle's triangle count
+    from oracle import oracle as O
+    assert kfn(None, res) == int(O.masked_spgemm(L, L, L, "plus_pair_i64")["values"].sum())
+
+
+def test_oracle_plan_budget():
+    """The planner takes the whole C when it fits the budget and otherwise a
+    row sample that fits it."""
+    p = synth.triangle_counting(scale=12, ef=16, seed=1)
+    L = p["M"]
+    whole, fixed, per_row = bench.oracle_plan(L, L, L, "plus_pair_i64", False, 100.0)
+    assert whole is None and fixed >= 0 and per_row > 0
+    part, fixed, per_row = bench.oracle_plan(L, L, L, "plus_pair_i64", False, fixed + per_row * 100)
+    assert part is not None and 1 <= part < L.nrows
+
+
+def test_kept_fn_for_semirings():
+    """Kept products from an fp32 result (a plus-pair call on the same rows)
+    equal the plus-pair sum."""
+    from oracle import oracle as O
+    q = synth.random_problem(80, 60, 90, 5.0, 5.0, 9.0, 4, "f32")
+    rows = np.array([1, 5, 7, 40], np.int32)
+    res = O.masked_spgemm(q["M"], q["A"], q["B"], "plus_times_f32", rows=rows)
+    pp = O.masked_spgemm(q["M"], q["A"], q["B"], "plus_pair_i64", rows=rows)
+    assert bench.kept_fn_for("plus_times_f32", q["M"], q["A"], q["B"], False)(rows, res) == int(pp["values"].sum())
 
 
 def test_reference_arm_line():
@@ -45,6 +70,8 @@ def test_reference_arm_line():
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == "masked GFLOP/s"
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    # the same config dict as the GPU arm builds for this workload
+    assert line["config"] == bench.build_workload("tc", 10, synth.BASE_SEED).config
 
 
 def test_oracle_threads_form_and_thread_independence():

@@ -122,6 +122,31 @@ def test_autograd_problem_scale14(handle):
     assert np.all(np.abs(dB.cpu().numpy() - dB_ref) <= 1e-5 * SB + 1e-30)
 
 
+def test_autograd_problem_scale18_full(handle):
+    """The differentiable workload at its full size (R-MAT scale 18, edge
+    factor 16, fp32 N(0,1)): the forward C on every row, and dA, dB on every
+    entry, against the fp64 oracle at the per-entry bounds 1e-5 * sum |a||b|
+    (C), 1e-5 * sum |g||b| (dA) and 1e-5 * sum |a||g| (dB)."""
+    p = synth.autograd_problem(scale=18, ef=16)
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    d = to_dev(p, "plus_times_f32")
+    res = _lib.msgemm_run(handle, d["M"], d["A"], d["B"], "plus_times_f32").trimmed()
+    handle.sync_status()
+    assert_parity(res, ref, "plus_times_f32", ctx="autograd scale 18 forward")
+    G = synth.Csr(p["M"].nrows, p["M"].ncols, ref["rowptr"].astype(np.int32), ref["colidx"],
+                  synth.upstream_grad(len(ref["colidx"])))
+    dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+    SA, SB = O.grad(p["A"].with_values(np.abs(p["A"].values)), p["B"].with_values(np.abs(p["B"].values)),
+                    G.with_values(np.abs(G.values)))
+    for rep in range(2):   # the second call reuses whatever the first left in the handle
+        dA, dB = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G))
+        handle.sync_status()
+        eA = np.abs(dA.cpu().numpy().astype(np.float64) - dA_ref)
+        eB = np.abs(dB.cpu().numpy().astype(np.float64) - dB_ref)
+        assert np.all(eA <= 1e-5 * SA + 1e-30), f"dA: {(eA > 1e-5 * SA).sum()} entries outside (rep {rep})"
+        assert np.all(eB <= 1e-5 * SB + 1e-30), f"dB: {(eB > 1e-5 * SB).sum()} entries outside (rep {rep})"
+
+
 def test_batched_full_size_sampled_products(handle):
     ps = synth.batched_problems(nprod=256)
     devs = [to_dev(q, "plus_times_f32") for q in ps]
