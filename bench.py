@@ -306,11 +306,15 @@ class DeviceRun:
             return cache[key]
         self.prods = [(dv(M, False), dv(A, keep), dv(B, keep), c) for (M, A, B, c) in wl.mats]
         self.G = None
+        self.plan = None
         if wl.name == "autograd":
             M, A, B, _ = self.prods[0]
             res = _lib.msgemm_run(h, M, A, B, sr).trimmed()
             self.G = _lib.DeviceCsr(res.nrows, res.ncols, res.rowptr, res.colidx,
                                     torch.from_numpy(synth.upstream_grad(res.nnz)).to(dev))
+            # the transposed patterns, built once as the autograd function does
+            # on its first backward (patterns are fixed across steps)
+            self.plan = _lib.BackwardPlan(h, A, B)
 
     def step(self):
         """One step; returns (result object, a device scalar to read back)."""
@@ -327,7 +331,7 @@ class DeviceRun:
         M, A, B, comp = self.prods[0]
         if name == "autograd":
             r = _lib.msgemm_run(h, M, A, B, sr)
-            _lib.msgemm_backward(h, A, B, self.G)
+            _lib.msgemm_backward(h, A, B, self.G, plan=self.plan)
             return r, r.d_nnz
         r = _lib.msgemm_run(h, M, A, B, sr, comp)
         return r, r.d_nnz
@@ -535,9 +539,11 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
     if wl.name == "autograd":
         M, A, B, _ = run.prods[0]
         fwd = lambda: _lib.msgemm_run(h, M, A, B, wl.semiring)  # noqa: E731
-        bwd = lambda: _lib.msgemm_backward(h, A, B, run.G)  # noqa: E731
+        bwd = lambda: _lib.msgemm_backward(h, A, B, run.G, plan=run.plan)  # noqa: E731
+        bwd0 = lambda: _lib.msgemm_backward(h, A, B, run.G)  # noqa: E731
         out["fwd_ms"] = statistics.median(timed_steps(torch, fwd, 5, flush, stream))
         out["bwd_ms"] = statistics.median(timed_steps(torch, bwd, 5, flush, stream))
+        out["bwd_unplanned_ms"] = statistics.median(timed_steps(torch, bwd0, 5, flush, stream))
     return out
 
 
@@ -675,7 +681,7 @@ def form_summary(wl, meas):
         d["push_products"] = push_products(A, B)
     if meas["per_phase"]:
         d["phase_ms"] = {n: round(statistics.mean(v), 4) for n, v in meas["per_phase"].items()}
-    for k in ("per_product_ms", "graph_ms", "fwd_ms", "bwd_ms"):
+    for k in ("per_product_ms", "graph_ms", "fwd_ms", "bwd_ms", "bwd_unplanned_ms"):
         if k in meas:
             d[k] = round(meas[k], 3)
     if "per_product_ms" in meas:
@@ -744,7 +750,8 @@ def run_ours(args):
         line["roofline_smem"] = roof_smem
     if "push_products" in summary:
         line["push_gflops"] = round(2 * summary["push_products"] / (ms_per_step * 1e-3) / 1e9, 2)
-    for k in ("per_product_ms", "batched_speedup", "graph_ms", "graph_vs_per_product", "fwd_ms", "bwd_ms"):
+    for k in ("per_product_ms", "batched_speedup", "graph_ms", "graph_vs_per_product", "fwd_ms", "bwd_ms",
+              "bwd_unplanned_ms"):
         if k in summary:
             line[k] = summary[k]
 

@@ -107,7 +107,7 @@ typedef enum {
                                      whole GPU (at most 4096 to 65536 such rows per call, by
                                      the product's width; the rest and every lighter row keep
                                      one CTA or warp per row) */
-    MSGEMM_OPT_PHASES = 9         /* value 1/2 (default 1), for msgemm_run, msgemm_run_batched
+    MSGEMM_OPT_PHASES = 9,        /* value 1/2 (default 1), for msgemm_run, msgemm_run_batched
                                      and msgemm_autotune (Sec. 6).  1: one phase -- rows write
                                      to a temporary the size of the mask (plain) or of the
                                      per-row bounds (complemented), then a compaction copies
@@ -117,6 +117,13 @@ typedef enum {
                                      numeric pass writes each row in place: no temporary, more
                                      work.  Two phases never use the (row, tile) grid kinds
                                      nor a CUDA graph (use_graph is ignored). */
+    MSGEMM_OPT_HASH_KICKS = 10    /* value 0..4096 (default 64): the hash rows (Sec. 5.3) place
+                                     each mask column by two-choice (cuckoo) hashing, moving at
+                                     most this many keys per insertion; a row whose insertion
+                                     runs out retries with a second pair of hash functions, then
+                                     falls back to linear probing.  0 = linear probing only.
+                                     The result never depends on it (tests use 0 and 1 to run
+                                     every build path). */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */
@@ -193,6 +200,33 @@ msgemm_status msgemm_run(msgemm_handle *handle, const msgemm_csr *M, int complem
 msgemm_status msgemm_backward(msgemm_handle *handle, const msgemm_csr *A, const msgemm_csr *B,
                               const msgemm_csr *G, msgemm_semiring semiring,
                               float *dA_vals, float *dB_vals);
+
+/* A backward plan: the transposes msgemm_backward builds on every call (B^T
+ * and A^T), built once for fixed patterns of A and B -- the usual case when
+ * training values on a fixed sparsity pattern.  The plan keeps the two
+ * transposed patterns with ascending rows and, for each of their entries,
+ * the position of its value in A or B; msgemm_backward_planned then only
+ * gathers the current values by those positions (one light kernel each)
+ * before the two masked products, instead of counting, scanning, scattering
+ * and sorting.  Results equal msgemm_backward's (same products, same
+ * accumulators; the summation order inside an entry may differ, within the
+ * fp32 bound).
+ * The plan records A's and B's row-pointer and column arrays by address and
+ * their sizes: the arrays must hold the same pattern while the plan is used
+ * (planned calls with other addresses or sizes return MSGEMM_ERR_INVALID).
+ * Its memory (about 12 bytes per stored entry of A and of B, plus the row
+ * pointers) comes from the handle's allocation callback; destroy the plan
+ * with the same handle, before the handle.  Planned calls on one plan share
+ * its value arrays: run them on one stream.  Asynchronous on the handle's
+ * stream. */
+typedef struct msgemm_backward_plan msgemm_backward_plan;
+msgemm_status msgemm_backward_plan_create(msgemm_handle *handle, const msgemm_csr *A, const msgemm_csr *B,
+                                          msgemm_backward_plan **plan);
+/* dA and dB as msgemm_backward (plus-times fp32) for the plan's patterns. */
+msgemm_status msgemm_backward_planned(msgemm_handle *handle, msgemm_backward_plan *plan,
+                                      const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
+                                      float *dA_vals, float *dB_vals);
+void msgemm_backward_plan_destroy(msgemm_handle *handle, msgemm_backward_plan *plan);
 
 /* nprod independent products C[p] = M[p] .* (A[p] B[p]) (or complemented per
  * complement[p], which may be NULL for all-plain), one semiring.  Binning,

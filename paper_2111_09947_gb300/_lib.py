@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import bisect
 import ctypes as C
+import weakref
 import os
 from collections.abc import Sequence
 from dataclasses import dataclass
@@ -24,6 +25,7 @@ ACC_AUTO, ACC_MSA, ACC_HASH, ACC_MCA, ACC_DOT, ACC_HEAP, ACC_HEAPDOT = 0, 1, 2, 
 ACCUMULATORS = {"auto": 0, "msa": 1, "hash": 2, "mca": 3, "dot": 4, "heap": 5, "heapdot": 6}
 OPT_FORCE_ACCUM, OPT_VALIDATE, OPT_DOT, OPT_PROFILE, OPT_TILE_INDEX, OPT_GRID, OPT_WARP_SLAB, OPT_GRID_MIN_FLOPS = 1, 2, 3, 4, 5, 6, 7, 8
 OPT_PHASES = 9
+OPT_HASH_KICKS = 10
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_SHAPE", 3: "ERR_UNSORTED", 4: "ERR_UNSUPPORTED", 5: "ERR_OOM",
           6: "ERR_OVERFLOW", 7: "ERR_CUDA", 8: "ERR_TIMEOUT"}
 KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "dot_w", "dot_b",
@@ -34,7 +36,8 @@ EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_ru
            "msgemm_run_batched", "msgemm_autotune", "msgemm_transpose", "msgemm_reduce_sum",
            "msgemm_sync_status", "msgemm_last_error_detail", "msgemm_num_kinds", "msgemm_bin_counts",
            "msgemm_profile_count", "msgemm_profile_entry", "msgemm_last_row_kinds", "msgemm_kernel_launches",
-           "msgemm_transpose_noalloc", "msgemm_bc", "msgemm_ktruss", "msgemm_destroy"]
+           "msgemm_transpose_noalloc", "msgemm_bc", "msgemm_ktruss", "msgemm_destroy",
+           "msgemm_backward_plan_create", "msgemm_backward_planned", "msgemm_backward_plan_destroy"]
 
 
 class MsgemmError(RuntimeError):
@@ -100,6 +103,9 @@ def load(build_if_missing: bool = False) -> C.CDLL:
         "msgemm_bc": (i32, [vp, P(Csr), vp, i32, vp, P(C.c_int32)]),
         "msgemm_ktruss": (i32, [vp, P(Csr), i64, P(CsrOut), P(C.c_int32), P(C.c_int64)]),
         "msgemm_destroy": (None, [vp]),
+        "msgemm_backward_plan_create": (i32, [vp, P(Csr), P(Csr), P(vp)]),
+        "msgemm_backward_planned": (i32, [vp, vp, P(Csr), P(Csr), P(Csr), vp, vp]),
+        "msgemm_backward_plan_destroy": (None, [vp, vp]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(lib, name)
@@ -243,6 +249,7 @@ class Handle:
         self.lib = load()
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         self._live: dict[int, torch.Tensor] = {}
+        self._plans = weakref.WeakSet()   # backward plans made with this handle
         self._alloc_cb = ALLOC_FN(self._alloc)
         self._free_cb = FREE_FN(self._free)
         h = C.c_void_p()
@@ -331,6 +338,8 @@ class Handle:
 
     def close(self):
         if getattr(self, "h", None):
+            for plan in list(self._plans):   # their memory came from this handle
+                plan.close()
             self.lib.msgemm_destroy(self.h)
             self.h = None
             self._live.clear()
@@ -361,15 +370,49 @@ def msgemm_run(h: Handle, M: DeviceCsr, A: DeviceCsr, B: DeviceCsr, semiring="pl
     return h.result(out, out_dtype(sr))
 
 
-def msgemm_backward(h: Handle, A: DeviceCsr, B: DeviceCsr, G: DeviceCsr, need_dA=True, need_dB=True):
-    """(dA values aligned with A's storage, dB values aligned with B's)."""
+class BackwardPlan:
+    """Transposed patterns of A and B for repeated backward passes
+    (msgemm_backward_plan_create); keeps A, B and the handle alive and is
+    destroyed before its handle closes."""
+
+    def __init__(self, h: Handle, A: DeviceCsr, B: DeviceCsr):
+        self.h, self.A, self.B = h, A, B
+        self.p = None
+        h.bind_stream()
+        p = C.c_void_p()
+        a, b = A.abi(), B.abi()
+        h.check(h.lib.msgemm_backward_plan_create(h.h, C.byref(a), C.byref(b), C.byref(p)))
+        self.p = p
+        h._plans.add(self)
+
+    def close(self):
+        if self.p is not None and getattr(self.h, "h", None):
+            self.h.lib.msgemm_backward_plan_destroy(self.h.h, self.p)
+        self.p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def msgemm_backward(h: Handle, A: DeviceCsr, B: DeviceCsr, G: DeviceCsr, need_dA=True, need_dB=True,
+                    plan: Optional[BackwardPlan] = None):
+    """(dA values aligned with A's storage, dB values aligned with B's).
+    With a plan made for A's and B's patterns the transposes are not rebuilt."""
     h.bind_stream()
     dA = torch.empty(A.nnz, dtype=torch.float32, device=A.colidx.device) if need_dA else None
     dB = torch.empty(B.nnz, dtype=torch.float32, device=B.colidx.device) if need_dB else None
     a, b, g = A.abi(), B.abi(), G.abi()
-    h.check(h.lib.msgemm_backward(h.h, C.byref(a), C.byref(b), C.byref(g), PLUS_TIMES_F32,
-                                  dA.data_ptr() if dA is not None and dA.numel() else None,
-                                  dB.data_ptr() if dB is not None and dB.numel() else None))
+    pa = dA.data_ptr() if dA is not None and dA.numel() else None
+    pb = dB.data_ptr() if dB is not None and dB.numel() else None
+    if plan is not None:
+        if plan.p is None:
+            raise MsgemmError(1, "backward plan is closed")
+        h.check(h.lib.msgemm_backward_planned(h.h, plan.p, C.byref(a), C.byref(b), C.byref(g), pa, pb))
+    else:
+        h.check(h.lib.msgemm_backward(h.h, C.byref(a), C.byref(b), C.byref(g), PLUS_TIMES_F32, pa, pb))
     return dA, dB
 
 

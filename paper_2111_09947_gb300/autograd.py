@@ -3,14 +3,27 @@
 The loss l(C) reaches A and B through C's values only.  With G = dl/dC stored
 on C's pattern, dA = pattern(A) .* (G B^T) and dB = pattern(B) .* (A^T G);
 both are masked products run by the library's own accumulators
-(``msgemm_backward``).  Patterns are fixed; gradients flow to the value
-arrays of A and B.
+(``msgemm_backward_planned``).  Patterns are fixed; gradients flow to the
+value arrays of A and B, and the transposed patterns the backward needs are
+built once per (A, B) pattern pair and handle.
 """
 from __future__ import annotations
 
 import torch
 
-from ._lib import DeviceCsr, Handle, msgemm_backward, msgemm_run
+from ._lib import BackwardPlan, DeviceCsr, Handle, msgemm_backward, msgemm_run
+
+
+def backward_plan(handle: Handle, A: DeviceCsr, B: DeviceCsr) -> BackwardPlan:
+    """The backward plan of (A, B) on this handle, made on first use and kept
+    on A (patterns are fixed; only values change between steps)."""
+    plans = A.__dict__.setdefault("_backward_plans", {})
+    key = (id(handle), id(B))
+    plan = plans.get(key)
+    if plan is None or plan.p is None:
+        plan = BackwardPlan(handle, A, B)
+        plans[key] = plan
+    return plan
 
 
 class MaskedSpGEMM(torch.autograd.Function):
@@ -35,7 +48,8 @@ class MaskedSpGEMM(torch.autograd.Function):
         G = DeviceCsr(M.nrows, M.ncols, rp, ci, g_vals.contiguous().float())
         Ax = DeviceCsr(A.nrows, A.ncols, A.rowptr, A.colidx, a_vals.detach().contiguous())
         Bx = DeviceCsr(B.nrows, B.ncols, B.rowptr, B.colidx, b_vals.detach().contiguous())
-        dA, dB = msgemm_backward(handle, Ax, Bx, G, ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        dA, dB = msgemm_backward(handle, Ax, Bx, G, ctx.needs_input_grad[0], ctx.needs_input_grad[1],
+                                 plan=backward_plan(handle, A, B))
         return dA, dB, None, None, None, None
 
 

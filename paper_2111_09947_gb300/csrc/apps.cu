@@ -132,6 +132,20 @@ __global__ void __launch_bounds__(256) k_fill(T *p, long long n, T v) {
         p[e] = v;
 }
 
+// p[e] = e: the position of every entry, carried through a transpose as its
+// value so that the transpose's entries can later be filled by a gather.
+__global__ void __launch_bounds__(256) k_iota(int *p, long long n) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        p[e] = (int)e;
+}
+
+// dst[e] = src[perm[e]] (coalesced writes, reads through L2).
+__global__ void __launch_bounds__(256) k_gather_f32(const int *__restrict__ perm, const float *__restrict__ src,
+                                                    long long n, float *__restrict__ dst) {
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = __ldg(src + __ldg(perm + e));
+}
+
 int blocks_for(long long work, int nsm, int per_sm) {
     const long long b = (work + 255) / 256;
     return (int)std::max(1LL, std::min(b, (long long)nsm * per_sm));
@@ -186,6 +200,16 @@ cudaError_t launch_filter_write(const int *rp, const int *ci, int nrows, const l
 cudaError_t launch_fill_i64(long long *p, long long n, long long v, cudaStream_t st, int nsm) {
     if (n == 0) return cudaSuccess;
     k_fill<long long><<<blocks_for(n, nsm, 16), 256, 0, st>>>(p, n, v);
+    return counted(cudaGetLastError());
+}
+cudaError_t launch_iota_i32(int *p, long long n, cudaStream_t st, int nsm) {
+    if (n == 0) return cudaSuccess;
+    k_iota<<<blocks_for(n, nsm, 16), 256, 0, st>>>(p, n);
+    return counted(cudaGetLastError());
+}
+cudaError_t launch_gather_f32(const int *perm, const float *src, long long n, float *dst, cudaStream_t st, int nsm) {
+    if (n == 0) return cudaSuccess;
+    k_gather_f32<<<blocks_for(n, nsm, 16), 256, 0, st>>>(perm, src, n, dst);
     return counted(cudaGetLastError());
 }
 cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t st, int nsm) {

@@ -38,6 +38,7 @@ struct msgemm_handle {
     unsigned *d_err = nullptr;   // in `small`, persistent
     int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
     int phases = 1;   // 1: one-phase, 2: symbolic + numeric (MSGEMM_OPT_PHASES)
+    int hash_kicks = CUCKOO_KICKS;   // MSGEMM_OPT_HASH_KICKS
     long long tile_index_budget = 4LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
@@ -449,6 +450,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     // ---- tile index of B for every tiled product, within the memory budget;
     // products left without one walk their tiles with per-entry cursors
     pl.L.aligned = pl.aligned ? 1 : 0;
+    pl.L.hash_kicks = h->hash_kicks;
     pl.nts.assign(P, 0);
     pl.tpos.assign(P, nullptr);
     if (any_tiled) {
@@ -1254,6 +1256,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
         if (value != 1 && value != 2) return fail(h, MSGEMM_ERR_INVALID, "phases is 1 or 2");
         h->phases = (int)value;
         return MSGEMM_OK;
+    case MSGEMM_OPT_HASH_KICKS:
+        if (value < 0 || value > 4096) return fail(h, MSGEMM_ERR_INVALID, "hash kicks is 0..4096");
+        h->hash_kicks = (int)value;
+        return MSGEMM_OK;
     default: return fail(h, MSGEMM_ERR_INVALID, "unknown option %d", (int)opt);
     }
 }
@@ -1271,17 +1277,59 @@ msgemm_status msgemm_run(msgemm_handle *h, const msgemm_csr *M, int complement, 
     return run_products(h, in, sr, h->validate, false);
 }
 
+namespace {
+
+msgemm_status check_backward(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
+                             msgemm_semiring sr) {
+    if (sr != MSGEMM_PLUS_TIMES_F32) return fail(h, MSGEMM_ERR_UNSUPPORTED, "backward is defined for plus-times fp32");
+    CKS(check_csr(h, A, "A", true));
+    CKS(check_csr(h, B, "B", true));
+    if (G) {
+        CKS(check_csr(h, G, "G", true));
+        if (A->ncols != B->nrows || G->nrows != A->nrows || G->ncols != B->ncols)
+            return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: A %dx%d, B %dx%d, G %dx%d", A->nrows, A->ncols,
+                        B->nrows, B->ncols, G->nrows, G->ncols);
+    } else if (A->ncols != B->nrows) {
+        return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: A %dx%d, B %dx%d", A->nrows, A->ncols, B->nrows,
+                    B->ncols);
+    }
+    return MSGEMM_OK;
+}
+
+// dA = pattern(A) .* (G B^T): mask A, left G (m x n), right B^T (n x k)
+// given as Bt; the pull kernel reads columns of B^T, which are the rows of B.
+msgemm_status backward_dA(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
+                          const msgemm_csr &Bt, float *dA_vals) {
+    msgemm_csr Mx = *A;
+    Mx.values = nullptr;
+    std::vector<ProdIn> in(1);
+    in[0].M = &Mx; in[0].A = G; in[0].B = &Bt; in[0].comp = 0;
+    in[0].bt_rp = B->rowptr; in[0].bt_ci = B->colidx; in[0].bt_v = B->values;
+    in[0].aligned_out = dA_vals;
+    CK(cudaMemsetAsync(dA_vals, 0, sizeof(float) * (size_t)A->nnz, h->stream));
+    return A->nnz > 0 ? run_pipeline(h, in, MSGEMM_PLUS_TIMES_F32, false, false) : MSGEMM_OK;
+}
+
+// dB = pattern(B) .* (A^T G): mask B, left A^T (k x m) given as At, right G.
+msgemm_status backward_dB(msgemm_handle *h, const msgemm_csr *B, const msgemm_csr *G, const msgemm_csr &At,
+                          int at_sorted, float *dB_vals) {
+    msgemm_csr Mx = *B;
+    Mx.values = nullptr;
+    std::vector<ProdIn> in(1);
+    in[0].M = &Mx; in[0].A = &At; in[0].B = G; in[0].comp = 0;
+    in[0].a_sorted = at_sorted;
+    in[0].aligned_out = dB_vals;
+    CK(cudaMemsetAsync(dB_vals, 0, sizeof(float) * (size_t)B->nnz, h->stream));
+    return B->nnz > 0 ? run_pipeline(h, in, MSGEMM_PLUS_TIMES_F32, false, false) : MSGEMM_OK;
+}
+
+}  // namespace
+
 msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B, const msgemm_csr *G,
                               msgemm_semiring sr, float *dA_vals, float *dB_vals) {
     if (!h) return MSGEMM_ERR_INVALID;
-    if (sr != MSGEMM_PLUS_TIMES_F32) return fail(h, MSGEMM_ERR_UNSUPPORTED, "backward is defined for plus-times fp32");
     h->nprof = 0;
-    CKS(check_csr(h, A, "A", true));
-    CKS(check_csr(h, B, "B", true));
-    CKS(check_csr(h, G, "G", true));
-    if (A->ncols != B->nrows || G->nrows != A->nrows || G->ncols != B->ncols)
-        return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: A %dx%d, B %dx%d, G %dx%d", A->nrows, A->ncols,
-                    B->nrows, B->ncols, G->nrows, G->ncols);
+    CKS(check_backward(h, A, B, G, sr));
     if (h->validate) CKS(validate_inputs(h, {A, B, G}));
     cudaStream_t st = h->stream;
     // transposes B^T (n x k) and A^T (k x m), values carried, rows unsorted
@@ -1318,42 +1366,134 @@ msgemm_status msgemm_backward(msgemm_handle *h, const msgemm_csr *A, const msgem
         return MSGEMM_OK;
     };
     if (dA_vals) {
-        // dA = pattern(A) .* (G B^T): mask A, left G (m x n), right B^T (n x k);
-        // the pull kernel reads columns of B^T, which are the rows of B.
         rs = transpose(B, Bt, true);
         if (rs == MSGEMM_OK) {
-            msgemm_csr Mx = *A, Bx{};
-            Mx.values = nullptr;
-            Bx.nrows = B->ncols; Bx.ncols = B->nrows; Bx.nnz = B->nnz;
-            Bx.rowptr = Bt.rp; Bx.colidx = Bt.ci; Bx.values = Bt.v;
-            std::vector<ProdIn> in(1);
-            in[0].M = &Mx; in[0].A = G; in[0].B = &Bx; in[0].comp = 0;
-            in[0].bt_rp = B->rowptr; in[0].bt_ci = B->colidx; in[0].bt_v = B->values;
-            in[0].aligned_out = dA_vals;
-            if (cudaMemsetAsync(dA_vals, 0, sizeof(float) * (size_t)A->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
-            if (rs == MSGEMM_OK && A->nnz > 0) rs = run_pipeline(h, in, sr, false, false);
+            const msgemm_csr Bx{B->ncols, B->nrows, B->nnz, Bt.rp, Bt.ci, Bt.v};
+            rs = backward_dA(h, A, B, G, Bx, dA_vals);
         }
     }
     if (rs == MSGEMM_OK && dB_vals) {
-        // dB = pattern(B) .* (A^T G): mask B, left A^T (k x m, rows unsorted), right G
         rs = transpose(A, At, false);
         if (rs == MSGEMM_OK) {
-            msgemm_csr Mx = *B, Ax{};
-            Mx.values = nullptr;
-            Ax.nrows = A->ncols; Ax.ncols = A->nrows; Ax.nnz = A->nnz;
-            Ax.rowptr = At.rp; Ax.colidx = At.ci; Ax.values = At.v;
-            std::vector<ProdIn> in(1);
-            in[0].M = &Mx; in[0].A = &Ax; in[0].B = G; in[0].comp = 0;
-            in[0].a_sorted = 0;
-            in[0].aligned_out = dB_vals;
-            if (cudaMemsetAsync(dB_vals, 0, sizeof(float) * (size_t)B->nnz, st) != cudaSuccess) rs = MSGEMM_ERR_CUDA;
-            if (rs == MSGEMM_OK && B->nnz > 0) rs = run_pipeline(h, in, sr, false, false);
+            const msgemm_csr Ax{A->ncols, A->nrows, A->nnz, At.rp, At.ci, At.v};
+            rs = backward_dB(h, B, G, Ax, 0, dB_vals);
         }
     }
     // the transpose buffer is released in stream order (the callback's free
     // must honour stream order; cudaFree synchronises)
     dev_free(h, tb.p);
     return rs;
+}
+
+// Transposed patterns of a backward pass, built once (see msgemm.h).
+struct msgemm_backward_plan {
+    int device = 0;
+    const int32_t *a_rp = nullptr, *a_ci = nullptr, *b_rp = nullptr, *b_ci = nullptr;
+    int32_t am = 0, an = 0, bm = 0, bn = 0;
+    int64_t annz = 0, bnnz = 0;
+    void *mem = nullptr;
+    int *bt_rp = nullptr, *bt_ci = nullptr, *bt_perm = nullptr;   // B^T (n x k), rows ascending
+    int *at_rp = nullptr, *at_ci = nullptr, *at_perm = nullptr;   // A^T (k x m), rows ascending
+    float *bt_v = nullptr, *at_v = nullptr;                       // values gathered by each call
+};
+
+msgemm_status msgemm_backward_plan_create(msgemm_handle *h, const msgemm_csr *A, const msgemm_csr *B,
+                                          msgemm_backward_plan **plan) {
+    if (!h || !plan) return fail(h, MSGEMM_ERR_INVALID, "NULL handle or plan");
+    *plan = nullptr;
+    h->nprof = 0;
+    CKS(check_backward(h, A, B, nullptr, MSGEMM_PLUS_TIMES_F32));
+    if (h->validate) CKS(validate_inputs(h, {A, B}));
+    cudaStream_t st = h->stream;
+    const long long big = std::max(A->nnz, B->nnz);
+    const int wide = std::max(A->ncols, B->ncols);
+    const size_t bytes = carve_size<int>((size_t)B->ncols + 1) + 2 * carve_size<int>(B->nnz) +
+                         carve_size<float>(B->nnz) + carve_size<int>((size_t)A->ncols + 1) +
+                         2 * carve_size<int>(A->nnz) + carve_size<float>(A->nnz) +
+                         carve_size<int>((size_t)wide + 1) + carve_size<int>(big) +
+                         carve_size<long long>(wide / STILE + 4) + 1024;
+    msgemm_backward_plan *pl = new msgemm_backward_plan();
+    pl->mem = dev_alloc(h, bytes);
+    if (!pl->mem) {
+        delete pl;
+        return fail(h, MSGEMM_ERR_OOM, "backward plan allocation failed");
+    }
+    Carver cv(pl->mem);
+    pl->bt_rp = cv.take<int>((size_t)B->ncols + 1);
+    pl->bt_ci = cv.take<int>(B->nnz);
+    pl->bt_perm = cv.take<int>(B->nnz);
+    pl->bt_v = cv.take<float>(B->nnz);
+    pl->at_rp = cv.take<int>((size_t)A->ncols + 1);
+    pl->at_ci = cv.take<int>(A->nnz);
+    pl->at_perm = cv.take<int>(A->nnz);
+    pl->at_v = cv.take<float>(A->nnz);
+    int *cur = cv.take<int>((size_t)wide + 1);
+    int *iota = cv.take<int>(big);
+    long long *tiles = cv.take<long long>(wide / STILE + 4);
+    pl->device = h->device;
+    pl->a_rp = A->rowptr; pl->a_ci = A->colidx; pl->am = A->nrows; pl->an = A->ncols; pl->annz = A->nnz;
+    pl->b_rp = B->rowptr; pl->b_ci = B->colidx; pl->bm = B->nrows; pl->bn = B->ncols; pl->bnnz = B->nnz;
+    // each transpose carries the entries' positions as its values; the
+    // sorted rows then hold, per entry, where its value sits in the source
+    auto build = [&](const msgemm_csr *X, int *trp, int *tci, int *tperm) -> msgemm_status {
+        PScope ph(h, "plan transpose");
+        CK(launch_col_counts(X->colidx, X->nnz, X->ncols, cur, st, h->nsm));
+        CK(launch_excl_scan_int(cur, X->ncols, trp, tiles, st, h->nsm));
+        CK(cudaMemcpyAsync(cur, trp, sizeof(int) * ((size_t)X->ncols + 1), cudaMemcpyDeviceToDevice, st));
+        CK(launch_transpose_fill(X->rowptr, X->colidx, iota, 4, X->nrows, X->ncols, cur, tci, tperm, nullptr, st,
+                                 h->nsm));
+        CK(launch_segsort(trp, tci, tperm, 4, X->ncols, cur, st, h->nsm));
+        return MSGEMM_OK;
+    };
+    msgemm_status rs = MSGEMM_OK;
+    if (cudaSuccess != launch_iota_i32(iota, big, st, h->nsm)) rs = fail(h, MSGEMM_ERR_CUDA, "iota launch failed");
+    if (rs == MSGEMM_OK) rs = build(B, pl->bt_rp, pl->bt_ci, pl->bt_perm);
+    if (rs == MSGEMM_OK) rs = build(A, pl->at_rp, pl->at_ci, pl->at_perm);
+    if (rs != MSGEMM_OK) {
+        dev_free(h, pl->mem);
+        delete pl;
+        return rs;
+    }
+    *plan = pl;
+    return MSGEMM_OK;
+}
+
+msgemm_status msgemm_backward_planned(msgemm_handle *h, msgemm_backward_plan *pl, const msgemm_csr *A,
+                                      const msgemm_csr *B, const msgemm_csr *G, float *dA_vals, float *dB_vals) {
+    if (!h || !pl) return fail(h, MSGEMM_ERR_INVALID, "NULL handle or plan");
+    h->nprof = 0;
+    CKS(check_backward(h, A, B, G, MSGEMM_PLUS_TIMES_F32));
+    if (pl->device != h->device || A->rowptr != pl->a_rp || A->colidx != pl->a_ci || A->nrows != pl->am ||
+        A->ncols != pl->an || A->nnz != pl->annz || B->rowptr != pl->b_rp || B->colidx != pl->b_ci ||
+        B->nrows != pl->bm || B->ncols != pl->bn || B->nnz != pl->bnnz)
+        return fail(h, MSGEMM_ERR_INVALID, "A or B is not the pattern the plan was made for");
+    if (A->nnz > 0 && !A->values) return fail(h, MSGEMM_ERR_INVALID, "A has no values");
+    if (B->nnz > 0 && !B->values) return fail(h, MSGEMM_ERR_INVALID, "B has no values");
+    if (h->validate) CKS(validate_inputs(h, {A, B, G}));
+    cudaStream_t st = h->stream;
+    if (dA_vals) {
+        {
+            PScope ph(h, "gather");
+            CK(launch_gather_f32(pl->bt_perm, static_cast<const float *>(B->values), B->nnz, pl->bt_v, st, h->nsm));
+        }
+        const msgemm_csr Bx{B->ncols, B->nrows, B->nnz, pl->bt_rp, pl->bt_ci, pl->bt_v};
+        CKS(backward_dA(h, A, B, G, Bx, dA_vals));
+    }
+    if (dB_vals) {
+        {
+            PScope ph(h, "gather");
+            CK(launch_gather_f32(pl->at_perm, static_cast<const float *>(A->values), A->nnz, pl->at_v, st, h->nsm));
+        }
+        const msgemm_csr Ax{A->ncols, A->nrows, A->nnz, pl->at_rp, pl->at_ci, pl->at_v};
+        CKS(backward_dB(h, B, G, Ax, 1, dB_vals));
+    }
+    return MSGEMM_OK;
+}
+
+void msgemm_backward_plan_destroy(msgemm_handle *h, msgemm_backward_plan *pl) {
+    if (!pl) return;
+    if (h) dev_free(h, pl->mem);
+    delete pl;
 }
 
 msgemm_status msgemm_run_batched(msgemm_handle *h, int nprod, const msgemm_csr *M, const int *complement,

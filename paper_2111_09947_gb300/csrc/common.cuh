@@ -300,19 +300,41 @@ __host__ __device__ __forceinline__ long long pow2_at_least(long long x) {
 __host__ __device__ __forceinline__ long long align8(long long x) { return (x + 7) & ~7LL; }
 __host__ __device__ __forceinline__ long long words32(long long bits) { return (bits + 31) >> 5; }
 
-// Hash (mask-keyed) table: 32-bit keys and 16-bit ranks per slot.
-__host__ __device__ __forceinline__ long long hash_table_bytes(long long H) { return align8(6 * H); }
-// Table size: load factor 0.25 (Sec. 5.3) when it fits, else 0.5; ranks are
-// 16-bit, so mask rows longer than 65535 never take this form.  Returns 0 if
-// it does not fit.
-__host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc, bool setbits, long long slab) {
-    if (mnz > 65535) return 0;
-    long long extra = align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
-    long long h4 = pow2_at_least(4 * mnz), h2 = pow2_at_least(2 * mnz);
-    if (hash_table_bytes(h4) + extra <= slab) return h4;
-    if (hash_table_bytes(h2) + extra <= slab) return h2;
-    return 0;
+// Hash (mask-keyed) table: per slot a 32-bit key (the mask column; bit 31
+// marks the SET state where the semiring keeps one) and the slot's
+// accumulator.  Slots: 4 x nnz(m) (load factor 0.25, Sec. 5.3), at least 32,
+// or as many as the slab holds down to 2 x nnz(m) (load 0.5); any count, not
+// only powers of two (positions come from a multiply-high).  Returns 0 if
+// the row does not fit.
+__host__ __device__ __forceinline__ long long hash_table_bytes(long long H, int acc) {
+    return align8(4 * H) + H * acc;   // keys, then the (8-byte aligned) accumulators
 }
+__host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc, long long slab) {
+    if (mnz <= 0 || mnz > (1 << 24)) return 0;
+    long long h = 4 * mnz < 32 ? 32 : 4 * mnz;
+    const long long fit = (slab - 8) / (4 + acc);
+    if (h > fit) h = fit;
+    return h >= 2 * mnz ? h : 0;
+}
+
+// Two-choice (cuckoo) positions of key x in a table of H >= 2 slots:
+// h1 = multiply-high of x * c1 into [0, H); h2 = h1 + 1 + (a second
+// multiply-high into [0, H - 1)) mod H, so h2 != h1.  Every key of a built
+// table sits at one of its two positions, so a lookup reads exactly two
+// slots (Pagh and Rodler's cuckoo hashing; parallel insertion by atomic
+// exchange as in Alcantara et al.'s GPU hash tables).
+struct CuckooHash {
+    unsigned c1, c2, H;
+    __device__ __forceinline__ unsigned h1(unsigned x) const { return __umulhi(x * c1, H); }
+    __device__ __forceinline__ unsigned h2(unsigned x, unsigned p1) const {
+        const unsigned t = p1 + 1u + __umulhi(x * c2, H - 1u);
+        return t >= H ? t - H : t;
+    }
+};
+// Multiplier pairs of the first attempt and of the retry (odd constants).
+constexpr unsigned CUCKOO_A1 = 0x9E3779B1u, CUCKOO_A2 = 0x85EBCA77u;
+constexpr unsigned CUCKOO_B1 = 0xC2B2AE3Du, CUCKOO_B2 = 0x27D4EB2Fu;
+constexpr int CUCKOO_KICKS = 64;
 __host__ __device__ __forceinline__ long long mca_bytes(long long mnz, int acc, bool setbits) {
     return align8(4 * mnz) + align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);
 }

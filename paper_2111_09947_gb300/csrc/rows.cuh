@@ -46,6 +46,7 @@ struct RowLaunch {
     // into the product's output arrays at the row's final offset (direct)
     int count_only;
     int direct;
+    int hash_kicks;    // HASH kinds: moves allowed per cuckoo insertion; 0 = linear probing
 };
 
 // Where a row's entries go: the shared temporary output, or (two-phase
@@ -245,37 +246,37 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
 }
 
 // ------------------------------------------------------------------ gather
-// Ordered output of rank-indexed accumulators (HASH, MCA, DOT): entries of
-// the mask row in mask order whose state is SET (Sec. 5.2 collects the
-// output in the mask's own order, so it comes out sorted).
-template <int SR, bool CTA>
-__device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const typename Sr<SR>::acc_t *acc,
-                                              const unsigned *sb, long long tmp, const TmpOut &T,
-                                              int *cnt_slot, int *scratch, int aligned, bool write) {
+// Ordered output of the mask-ordered accumulators (HASH, MCA, DOT): entries
+// of the mask row, in mask order, whose state is SET (Sec. 5.2 collects the
+// output in the mask's own order, so it comes out sorted).  get(q, v)
+// returns whether mask entry q is SET and its accumulated value in v.
+template <int SR, bool CTA, class G>
+__device__ __forceinline__ void gather_by(const int *mcols, int mnz, const G &get, long long tmp, const TmpOut &T,
+                                          int *cnt_slot, int *scratch, int aligned, bool write) {
     using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
     using out_t = typename S::out_t;
     Team<CTA> team;
     const int lane = lane_id();
     out_t *tv = static_cast<out_t *>(T.v);
-    auto kept = [&](int q) -> bool {
-        if constexpr (S::count_set) return acc[q] != 0;
-        else return test_bit(sb, q);
-    };
     if (aligned) {
-        for (int q = team.tid(); q < mnz; q += team.size())
-            if (kept(q)) tv[tmp + q] = S::out(acc[q]);
+        for (int q = team.tid(); q < mnz; q += team.size()) {
+            acc_t v;
+            if (get(q, v)) tv[tmp + q] = S::out(v);
+        }
         return;
     }
     if (!CTA) {
         int base = 0;
         for (int r0 = 0; r0 < mnz; r0 += 32) {
             const int q = r0 + lane;
-            const bool keep = q < mnz && kept(q);
+            acc_t v{};
+            const bool keep = q < mnz && get(q, v);
             const unsigned bal = __ballot_sync(FULL, keep);
             if (keep && write) {
                 const long long o = tmp + base + __popc(bal & lanemask_lt());
                 T.ci[o] = mcols[q];
-                tv[o] = S::out(acc[q]);
+                tv[o] = S::out(v);
             }
             base += __popc(bal);
         }
@@ -287,24 +288,41 @@ __device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const t
         int c = 0;
         for (int r0 = s0; r0 < s1; r0 += 32) {
             const int q = r0 + lane;
-            c += __popc(__ballot_sync(FULL, q < s1 && kept(q)));
+            acc_t v{};
+            c += __popc(__ballot_sync(FULL, q < s1 && get(q, v)));
         }
         int total;
         const int off = block_excl_scan(lane == 0 ? c : 0, scratch, &total);
         int base = __shfl_sync(FULL, off, 0);
         for (int r0 = s0; r0 < s1; r0 += 32) {
             const int q = r0 + lane;
-            const bool keep = q < s1 && kept(q);
+            acc_t v{};
+            const bool keep = q < s1 && get(q, v);
             const unsigned bal = __ballot_sync(FULL, keep);
             if (keep && write) {
                 const long long o = tmp + base + __popc(bal & lanemask_lt());
                 T.ci[o] = mcols[q];
-                tv[o] = S::out(acc[q]);
+                tv[o] = S::out(v);
             }
             base += __popc(bal);
         }
         if (threadIdx.x == 0) *cnt_slot = total;
     }
+}
+
+// Rank-indexed accumulators (MCA, DOT): acc[q] and SET bit q belong to mask
+// entry q.
+template <int SR, bool CTA>
+__device__ __forceinline__ void gather_ranked(const int *mcols, int mnz, const typename Sr<SR>::acc_t *acc,
+                                              const unsigned *sb, long long tmp, const TmpOut &T,
+                                              int *cnt_slot, int *scratch, int aligned, bool write) {
+    using acc_t = typename Sr<SR>::acc_t;
+    auto get = [&](int q, acc_t &v) -> bool {
+        v = acc[q];
+        if constexpr (Sr<SR>::count_set) return v != 0;
+        else return test_bit(sb, q);
+    };
+    gather_by<SR, CTA>(mcols, mnz, get, tmp, T, cnt_slot, scratch, aligned, write);
 }
 
 // Row context.
@@ -331,54 +349,145 @@ __device__ __forceinline__ RowCtx row_ctx(const DevProd &P, long long r, const R
 
 
 // --------------------------------------------------------------- HASH rows
-// Sec. 5.3: open addressing, linear probing, no resizing, keyed by the mask's
-// columns; a slot holds (column, rank in the mask row).  Values live in a
-// rank-indexed array so the gather runs in mask order.
+// Sec. 5.3: a table keyed by the mask's columns, no resizing; a product
+// whose column is not a key is never evaluated (NOTALLOWED).  The paper's
+// table probes linearly; here every key is placed by two-choice (cuckoo)
+// hashing, so a lookup reads exactly two slots with no probe loop: on a warp,
+// a linear probe runs as long as the longest chain among its 32 lanes, which
+// made the probe loop most of the kernel's instructions.  The accumulator of
+// a key lives in the key's own slot; for semirings with a separate SET state
+// it is bit 31 of the key word (columns are below 2^31 - 1).  The gather walks
+// the mask row in order and looks each column up again.
+//
+// Building: each mask column is inserted by atomic exchange, carrying any
+// key it displaces to that key's other position (at most CUCKOO_KICKS moves
+// per key).  If an insertion runs out of moves, the table is rebuilt with the
+// second multiplier pair, and if that fails too, with linear probing (the
+// paper's form) in the same layout; every form finds every key.
+constexpr unsigned KEY_SET = 0x80000000u;
+
+// Inserts the mask row's columns; returns true on failure (team-uniform).
+template <bool CTA>
+__device__ __forceinline__ bool cuckoo_build(unsigned *key, const CuckooHash &ch, const int *mcols, int mnz,
+                                             int kicks) {
+    Team<CTA> team;
+    bool fail = false;
+    for (int q = team.tid(); q < mnz; q += team.size()) {
+        unsigned x = (unsigned)__ldg(mcols + q);
+        unsigned pos = ch.h1(x);
+        int it = 0;
+        for (; it < kicks; ++it) {
+            const unsigned y = atomicExch(&key[pos], x);
+            if (y == EMPTY32) break;
+            x = y;   // carry the displaced key to its other position
+            const unsigned a = ch.h1(y);
+            pos = pos == a ? ch.h2(y, a) : a;
+        }
+        if (it == kicks) fail = true;
+    }
+    team.sync();
+    if constexpr (CTA) return __syncthreads_or(fail) != 0;
+    else return __any_sync(FULL, fail);
+}
+
+template <bool CTA>
+__device__ __forceinline__ void linear_build(unsigned *key, const CuckooHash &ch, const int *mcols, int mnz) {
+    Team<CTA> team;
+    for (int q = team.tid(); q < mnz; q += team.size()) {
+        const unsigned x = (unsigned)__ldg(mcols + q);
+        unsigned h = ch.h1(x);
+        while (atomicCAS(&key[h], EMPTY32, x) != EMPTY32) h = h + 1 == ch.H ? 0u : h + 1;
+    }
+    team.sync();
+}
+
+template <bool CTA>
+__device__ __forceinline__ void clear_keys(unsigned *key, unsigned H) {
+    Team<CTA> team;
+    for (unsigned h = team.tid(); h < H; h += team.size()) key[h] = EMPTY32;
+    team.sync();
+}
+
 template <int SR, bool CTA>
 __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, const RowLaunch &L, unsigned char *slab, int *scratch) {
     using S = Sr<SR>;
     using acc_t = typename S::acc_t;
     using in_t = typename S::in_t;
+    constexpr bool SETB = SrSizes<SR>::setbits;
+    constexpr unsigned KMASK = SETB ? ~KEY_SET : ~0u;   // key bits of a slot word
     Team<CTA> team;
     const int mnz = c.m1 - c.m0;
-    const long long H = hash_slots(mnz, (int)sizeof(acc_t), SrSizes<SR>::setbits, L.slab);
-    const int logH = ilog2(H);
-    const unsigned hmask = (unsigned)H - 1u;
-    // slot h: key[h] (mask column or EMPTY) and rank[h] (its position in the mask row)
+    const unsigned H = (unsigned)hash_slots(mnz, (int)sizeof(acc_t), L.slab);
     unsigned *key = reinterpret_cast<unsigned *>(slab);
-    unsigned short *rank = reinterpret_cast<unsigned short *>(slab + 4 * H);
-    acc_t *acc = reinterpret_cast<acc_t *>(slab + hash_table_bytes(H));
-    unsigned *sb = reinterpret_cast<unsigned *>(slab + hash_table_bytes(H) + align8((long long)mnz * sizeof(acc_t)));
-    for (long long h = team.tid(); h < H; h += team.size()) key[h] = EMPTY32;
-    for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
-    if constexpr (SrSizes<SR>::setbits)
-        for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;
-    team.sync();
-    for (int q = team.tid(); q < mnz; q += team.size()) {   // setAllowed for every mask column
-        const unsigned j = (unsigned)__ldg(P.m_ci + c.m0 + q);
-        unsigned h = hash32(j, logH);
-        while (atomicCAS(&key[h], EMPTY32, j) != EMPTY32) h = (h + 1) & hmask;
-        rank[h] = (unsigned short)q;
+    acc_t *acc = reinterpret_cast<acc_t *>(slab + align8(4LL * H));
+    const int *mcols = P.m_ci + c.m0;
+    for (unsigned h = team.tid(); h < H; h += team.size()) {
+        key[h] = EMPTY32;
+        acc[h] = 0;
     }
     team.sync();
-    auto ins = [&](int, in_t a, int j, in_t b) {
-        unsigned h = hash32((unsigned)j, logH);
-        for (;;) {   // terminates: at least half of the slots are empty
-            const unsigned kk = key[h];
-            if (kk == (unsigned)j) {
-                const int rk = rank[h];
-                S::add(&acc[rk], S::mul(a, b));
-                if constexpr (SrSizes<SR>::setbits) set_bit_once(sb, rk);
-                return;
-            }
-            if (kk == EMPTY32) return;   // NOTALLOWED: product never evaluated
-            h = (h + 1) & hmask;
+    CuckooHash ch{CUCKOO_A1, CUCKOO_A2, H};
+    const int kicks = L.hash_kicks;
+    bool linear = kicks <= 0;
+    if (linear) {
+        linear_build<CTA>(key, ch, mcols, mnz);
+    } else if (cuckoo_build<CTA>(key, ch, mcols, mnz, kicks)) {
+        clear_keys<CTA>(key, H);
+        ch.c1 = CUCKOO_B1;
+        ch.c2 = CUCKOO_B2;
+        if (cuckoo_build<CTA>(key, ch, mcols, mnz, kicks)) {
+            clear_keys<CTA>(key, H);
+            linear_build<CTA>(key, ch, mcols, mnz);
+            linear = true;
         }
+    }
+    // a hit: add the product into the slot; mark SET once (bit 31 of the key word)
+    auto hit = [&](unsigned p, unsigned kw, in_t a, in_t b) {
+        S::add(&acc[p], S::mul(a, b));
+        if constexpr (SETB)
+            if (!(kw & KEY_SET)) atomicOr(&key[p], KEY_SET);
     };
-    enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+    // slot of a key known to be in the table
+    auto slot_of = [&](unsigned x) -> unsigned {
+        unsigned h = ch.h1(x);
+        if (!linear) {
+            return (key[h] & KMASK) == x ? h : ch.h2(x, h);
+        }
+        while ((key[h] & KMASK) != x) h = h + 1 == H ? 0u : h + 1;
+        return h;
+    };
+    if (!linear) {
+        auto ins = [&](int, in_t a, int j, in_t b) {
+            const unsigned x = (unsigned)j;
+            const unsigned p1 = ch.h1(x), p2 = ch.h2(x, p1);
+            const unsigned k1 = key[p1], k2 = key[p2];
+            const bool f1 = (k1 & KMASK) == x;
+            if (f1 || (k2 & KMASK) == x) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
+        };
+        enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+    } else {
+        auto ins = [&](int, in_t a, int j, in_t b) {
+            unsigned h = ch.h1((unsigned)j);
+            for (;;) {   // terminates: at least half of the slots are empty
+                const unsigned kk = key[h];
+                if ((kk & KMASK) == (unsigned)j) {
+                    hit(h, kk, a, b);
+                    return;
+                }
+                if (kk == EMPTY32) return;   // NOTALLOWED: product never evaluated
+                h = h + 1 == H ? 0u : h + 1;
+            }
+        };
+        enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+    }
     team.sync();
-    gather_ranked<SR, CTA>(P.m_ci + c.m0, mnz, acc, sb, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned,
-                           !L.count_only);
+    auto get = [&](int q, acc_t &v) -> bool {
+        const unsigned p = slot_of((unsigned)__ldg(mcols + q));
+        v = acc[p];
+        if constexpr (Sr<SR>::count_set) return v != 0;
+        else return (key[p] & KEY_SET) != 0;
+    };
+    gather_by<SR, CTA>(mcols, mnz, get, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned, !L.count_only);
     team.sync();
 }
 

@@ -237,3 +237,108 @@ def test_autograd_function(handle):
     err = np.abs(cv.detach().cpu().numpy().astype(np.float64) - ref["values"])
     assert np.array_equal(crp.cpu().numpy(), ref["rowptr"]) and np.array_equal(cci.cpu().numpy(), ref["colidx"])
     assert np.all(err <= 1e-5 * ref["S"])
+
+
+@pytest.mark.parametrize("kicks", [0, 1, 64])
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+def test_hash_build_paths(handle, semiring, kicks):
+    """Hash rows (Sec. 5.3) forced on every row, with the cuckoo insertion's
+    move limit at its default (64), at 1 (insertions run out often: the retry
+    with the second hash pair and the linear fallback both run) and at 0
+    (linear probing only).  Mask rows from 1 to 1500 entries put warp and CTA
+    rows at load factors from 0.25 up to 0.5; the gradient form (values at the
+    mask's slots) and the two-phase form go through the same lookups."""
+    rng = np.random.default_rng(500 + kicks)
+    m, k, n = 600, 500, 40000
+    mdeg = np.array([1, 7, 60, 140, 230, 287, 700, 1500])[np.arange(m) % 8]
+    rows, cols = [], []
+    for i in range(m):
+        c = np.sort(rng.choice(n, size=int(mdeg[i]), replace=False))
+        rows.append(np.full(len(c), i))
+        cols.append(c)
+    M = synth.coo_to_csr(m, n, np.concatenate(rows).astype(np.int32), np.concatenate(cols).astype(np.int32))
+    q = synth.random_problem(m, k, n, 12.0, 300.0, 1.0, 501 + kicks, GEN[semiring])
+    q["M"] = M
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring)
+    handle.set_option(_lib.OPT_HASH_KICKS, kicks)
+    try:
+        for phases in (1, 2):
+            handle.set_option(_lib.OPT_PHASES, phases)
+            res = run(handle, q, semiring, False, "hash")
+            assert_parity(res, ref, semiring, ctx=f"kicks={kicks} phases={phases}")
+            counts = handle.bin_counts()
+            assert counts["hash_w"] > 0 and counts["hash_b"] > 0
+    finally:
+        handle.set_option(_lib.OPT_PHASES, 1)
+        handle.set_option(_lib.OPT_HASH_KICKS, 64)
+        handle.force("auto")
+
+
+def _grad_bounds(p, G):
+    SA, SB = O.grad(p["A"].with_values(np.abs(p["A"].values)), p["B"].with_values(np.abs(p["B"].values)),
+                    G.with_values(np.abs(G.values)))
+    return SA, SB
+
+
+@pytest.mark.parametrize("force", ["auto", "hash", "mca", "msa"])
+def test_backward_plan(handle, force):
+    """The planned backward (transposed patterns built once) against the
+    oracle's gradients at the per-entry bounds, on two value sets of the same
+    pattern in a row; a plan refuses operands with another pattern."""
+    m, k, n = 700, 900, 800
+    p = synth.random_problem(m, k, n, 9.0, 7.0, 40.0, 606, "f32")
+    d = to_dev(p, "plus_times_f32")
+    handle.force(force)
+    try:
+        plan = _lib.BackwardPlan(handle, d["A"], d["B"])
+        for rep in range(2):
+            if rep:
+                p["A"] = p["A"].with_values(synth.normal_f32(p["A"].nnz, 700, 4))
+                p["B"] = p["B"].with_values(synth.normal_f32(p["B"].nnz, 700, 5))
+                d["A"].values.copy_(torch.from_numpy(p["A"].values))
+                d["B"].values.copy_(torch.from_numpy(p["B"].values))
+            ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+            G = synth.Csr(m, n, ref["rowptr"].astype(np.int32), ref["colidx"],
+                          synth.upstream_grad(len(ref["colidx"]), 60 + rep))
+            dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+            SA, SB = _grad_bounds(p, G)
+            dA, dB = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G), plan=plan)
+            handle.sync_status()
+            assert np.all(np.abs(dA.cpu().numpy().astype(np.float64) - dA_ref) <= 1e-5 * SA + 1e-30)
+            assert np.all(np.abs(dB.cpu().numpy().astype(np.float64) - dB_ref) <= 1e-5 * SB + 1e-30)
+            # only dB, then only dA
+            _, dB1 = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G), need_dA=False,
+                                          plan=plan)
+            dA1, _ = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G), need_dB=False,
+                                          plan=plan)
+            handle.sync_status()
+            assert np.all(np.abs(dA1.cpu().numpy().astype(np.float64) - dA_ref) <= 1e-5 * SA + 1e-30)
+            assert np.all(np.abs(dB1.cpu().numpy().astype(np.float64) - dB_ref) <= 1e-5 * SB + 1e-30)
+        # another pattern (a copy of A's arrays at other addresses) is refused
+        A2 = _lib.DeviceCsr(d["A"].nrows, d["A"].ncols, d["A"].rowptr.clone(), d["A"].colidx.clone(), d["A"].values)
+        with pytest.raises(_lib.MsgemmError) as e:
+            _lib.msgemm_backward(handle, A2, d["B"], _lib.DeviceCsr.from_host(G), plan=plan)
+        assert e.value.status == 1
+        plan.close()
+    finally:
+        handle.force("auto")
+
+
+def test_backward_plan_outlived_by_handle_close():
+    """Closing a handle destroys the plans made with it first (their memory
+    came from its allocator); a closed plan is refused."""
+    p = synth.random_problem(50, 40, 60, 4.0, 4.0, 6.0, 9, "f32")
+    d = to_dev(p, "plus_times_f32")
+    h = _lib.Handle()
+    plan = _lib.BackwardPlan(h, d["A"], d["B"])
+    h.close()
+    assert plan.p is None
+    h2 = _lib.Handle()
+    try:
+        ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+        G = _lib.DeviceCsr.from_host(synth.Csr(50, 60, ref["rowptr"].astype(np.int32), ref["colidx"],
+                                               synth.upstream_grad(len(ref["colidx"]), 1)))
+        with pytest.raises(_lib.MsgemmError):
+            _lib.msgemm_backward(h2, d["A"], d["B"], G, plan=plan)
+    finally:
+        h2.close()
