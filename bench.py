@@ -67,6 +67,9 @@ def parse_args(argv=None):
                     help="policy sweeps instead of the benchmark line: Erdos-Renyi n x degrees with every "
                          "accumulator forced vs AUTO, or triangle counting over R-MAT scales")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--sweep-out", default=None, help="write the sweep's table (with the kernel source hash) "
+                                                       "to this JSON file")
+    ap.add_argument("--sweep-max-log2", type=int, default=22, help="largest n = 2^x of the Erdos-Renyi sweep")
     return ap.parse_args(argv)
 
 
@@ -307,6 +310,7 @@ class DeviceRun:
         self.prods = [(dv(M, False), dv(A, keep), dv(B, keep), c) for (M, A, B, c) in wl.mats]
         self.G = None
         self.plan = None
+        self.allreduce = None
         if wl.name == "autograd":
             M, A, B, _ = self.prods[0]
             res = _lib.msgemm_run(h, M, A, B, sr).trimmed()
@@ -321,9 +325,12 @@ class DeviceRun:
         _lib, h, sr = self._lib, self.h, self.wl.semiring
         name = self.wl.name
         if name == "tc":
-            L = self.prods[0][0]
-            r = _lib.msgemm_run(h, L, L, L, sr)
-            return r, _lib.msgemm_reduce_sum(h, r, sr)
+            M, A, B, _ = self.prods[0]   # L, L, L; or a row block of L, its rows of L, and L
+            r = _lib.msgemm_run(h, M, A, B, sr)
+            cnt = _lib.msgemm_reduce_sum(h, r, sr)
+            if self.allreduce is not None:   # row-sharded: sum the partial counts over the ranks
+                self.allreduce(cnt)
+            return r, cnt
         if name == "batched":
             Ms, As, Bs = [p[0] for p in self.prods], [p[1] for p in self.prods], [p[2] for p in self.prods]
             outs = _lib.msgemm_run_batched(h, Ms, As, Bs, sr)
@@ -468,7 +475,8 @@ def kept_from_oracle(M, A, B, complement):
 
 
 # ----------------------------------------------------------------- measurement
-def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks_gpu=None, autotune=True):
+def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks_gpu=None, autotune=True,
+            allreduce=None, dist_sync=False):
     """Times `steps` steps of a workload; returns a dict of measurements.
     With autotune, a fresh handle's policy is first tuned on the workload's
     products by the library's autotuner (untimed; its duration is reported)."""
@@ -476,6 +484,7 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
         h = _lib.Handle(dev)
     run = DeviceRun(torch, _lib, synth, h, wl, dev)
     wl.kept, wl.nnz_c = run.count_kept()
+    run.allreduce = allreduce
     tune_s = None
     if autotune:
         t0 = time.perf_counter()
@@ -501,10 +510,11 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
             per_phase.setdefault(name, []).append(ms)
 
     def sync_all():
-        # every rank enters and leaves the timed region together
+        # every rank enters and leaves the timed region together (the main
+        # measurement only: the forms run on rank 0 alone)
         torch.cuda.synchronize()
-        import torch.distributed as dist
-        if dist.is_available() and dist.is_initialized():
+        if dist_sync:
+            import torch.distributed as dist
             dist.barrier()
         torch.cuda.synchronize()
     sync_all()
@@ -705,19 +715,34 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    seed = synth.BASE_SEED + 7919 * rank      # weak scaling: one instance per rank
+    # triangle counting on N ranks: one product split by rows (strong
+    # scaling, the count all-reduced every step); other workloads: one seeded
+    # instance per rank (weak scaling)
+    sharded = world > 1 and args.workload == "tc"
+    seed = synth.BASE_SEED if sharded or world == 1 else synth.BASE_SEED + 7919 * rank
     h = _lib.Handle(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     log(f"generating {args.workload} workload")
     t_gen = time.perf_counter()
     wl = build_workload(args.workload, args.scale, seed)
+    sharding = None
+    if sharded:
+        from paper_2111_09947_gb300 import shard
+        L = wl.mats[0][0]
+        b = shard.partition_rows(shard.push_work(L, L), world)
+        r0, r1 = int(b[rank]), int(b[rank + 1])
+        Lb = shard.row_block(L, r0, r1)
+        wl.mats = [(Lb, Lb, L, False)]
+        sharding = {"kind": "rows of L in contiguous blocks balanced by push work, L replicated as the right "
+                            "operand, partial counts all-reduced every step", "ranks": world}
     gen_s = time.perf_counter() - t_gen
     log("measuring")
     if world > 1:
         dist.barrier()
     meas = measure(torch, _lib, synth, h, wl, dev, stream, flush, args.steps, args.warmup, local,
-                   autotune=not args.no_autotune)
+                   autotune=not args.no_autotune, allreduce=(lambda t: dist.all_reduce(t)) if sharded else None,
+                   dist_sync=world > 1)
     total_ms = sum(meas["times"])
     flops = 2.0 * wl.kept
     if world > 1:
@@ -739,13 +764,20 @@ def run_ours(args):
     line = {
         "metric": "masked GFLOP/s", "value": round(value, 3), "unit": "GFLOP/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype,
+        "higher_is_better": True, "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+        "dtype": wl.dtype,
         "data": "synthetic (seeded R-MAT / Erdos-Renyi; the paper's SuiteSparse graphs are not used)",
         "config": cfg, "gpu_launches": int(meas["launches"]), "roofline": roof,
         "hbm_min_gbs": summary.get("hbm_min_gbs"), "phase_ms": summary.get("phase_ms"),
         "clocks": meas["clocks"], "e2e": e2e, "gen_seconds": round(gen_s, 2), "autotune_s": meas["autotune_s"],
-        "counts": {"masked_products": wl.kept, "nnz_C": wl.nnz_c, "seed_per_rank": world > 1},
+        "counts": {"masked_products": wl.kept, "nnz_C": wl.nnz_c, "seed_per_rank": world > 1 and not sharded},
     }
+    if sharding is not None:
+        # the all-reduced count of the last step, and the kept products of all blocks
+        _, cnt = meas["run"].step()
+        sharding["triangles"] = int(cnt.item())
+        sharding["masked_products_all_ranks"] = int(flops / 2)
+        line["sharding"] = sharding
     if roof_smem is not None:
         line["roofline_smem"] = roof_smem
     if "push_products" in summary:
@@ -888,7 +920,7 @@ def run_sweep(args):
     h = _lib.Handle(dev)
     rows = []
     if args.sweep == "er":
-        for lg in (12, 14, 16, 18, 20):
+        for lg in range(12, args.sweep_max_log2 + 1, 2):
             n = 1 << lg
             for din in (4, 16, 64):
                 for dm in (1, 16, 256):
@@ -898,8 +930,13 @@ def run_sweep(args):
                     d = {k: _lib.DeviceCsr.from_host(p[k], device=dev) for k in ("M", "A", "B")}
                     d["M"].values = None
                     t = {}
-                    # every family forced (one phase), AUTO, and AUTO in two phases (Sec. 6)
-                    for force in ("auto", "msa", "hash", "mca", "dot", "heap", "heapdot", "auto_2p"):
+                    # every family forced (one phase), AUTO, and AUTO in two phases (Sec. 6); the
+                    # dense MSA forced on every row is left out from n = 2^22 (at 2^20 it already
+                    # takes 0.2-0.6 s a call: every row clears and gathers n columns)
+                    fams = ["auto", "msa", "hash", "mca", "dot", "heap", "heapdot", "auto_2p"]
+                    if lg >= 22:
+                        fams.remove("msa")
+                    for force in fams:
                         h.force("auto" if force == "auto_2p" else force)
                         h.set_option(_lib.OPT_PHASES, 2 if force == "auto_2p" else 1)
                         fn = lambda: _lib.msgemm_run(h, d["M"], d["A"], d["B"], "plus_times_f32")  # noqa: E731
@@ -934,13 +971,14 @@ def run_sweep(args):
         wins = {}
         for x in rows:
             wins[x["best"]] = wins.get(x["best"], 0) + 1
-        print(json.dumps({"sweep": "er", "points": len(rows), "auto_over_best_median": round(float(np.median(r)), 3),
-                          "auto_over_best_max": round(float(r.max()), 3),
-                          "auto_within_10pct": int((r <= 1.10).sum()), "best_family_counts": wins,
-                          "tuned_over_best_median": round(float(np.median(rt)), 3),
-                          "tuned_over_best_max": round(float(rt.max()), 3),
-                          "tuned_within_10pct": int((rt <= 1.10).sum()),
-                          "two_phase_over_one_median": round(float(np.median(r2)), 3)}), flush=True)
+        summary = {"sweep": "er", "points": len(rows), "auto_over_best_median": round(float(np.median(r)), 3),
+                   "auto_over_best_max": round(float(r.max()), 3),
+                   "auto_within_10pct": int((r <= 1.10).sum()), "best_family_counts": wins,
+                   "tuned_over_best_median": round(float(np.median(rt)), 3),
+                   "tuned_over_best_max": round(float(rt.max()), 3),
+                   "tuned_within_10pct": int((rt <= 1.10).sum()),
+                   "two_phase_over_one_median": round(float(np.median(r2)), 3)}
+        print(json.dumps(summary), flush=True)
     else:
         for scale in range(8, 21, 2):
             wl = build_workload("tc", scale, synth.BASE_SEED)
@@ -952,8 +990,17 @@ def run_sweep(args):
             row.pop("config")
             rows.append(row)
             print(json.dumps(row), flush=True)
-        print(json.dumps({"sweep": "rmat", "points": len(rows)}), flush=True)
+        summary = {"sweep": "rmat", "points": len(rows)}
+        print(json.dumps(summary), flush=True)
     h.close()
+    if args.sweep_out:
+        doc = {"sweep": args.sweep, "source_sha": source_hash(), "device": torch.cuda.get_device_name(dev),
+               "when": time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime()),
+               "command": "python bench.py " + " ".join(sys.argv[1:]),
+               "timing": "median of 5 CUDA-event-timed calls after 2 untimed, L2 flushed before each (ms)",
+               "summary": summary, "rows": rows}
+        with open(args.sweep_out, "w") as f:
+            json.dump(doc, f, indent=1)
 
 
 def main(argv=None):

@@ -317,23 +317,34 @@ __host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc,
     return h >= 2 * mnz ? h : 0;
 }
 
-// Two-choice (cuckoo) positions of key x in a table of H >= 2 slots:
-// h1 = multiply-high of x * c1 into [0, H); h2 = h1 + 1 + (a second
-// multiply-high into [0, H - 1)) mod H, so h2 != h1.  Every key of a built
-// table sits at one of its two positions, so a lookup reads exactly two
-// slots (Pagh and Rodler's cuckoo hashing; parallel insertion by atomic
-// exchange as in Alcantara et al.'s GPU hash tables).
+// Two-choice (cuckoo) positions of key x in a table of H >= 32 slots: with
+// u = x * c (mod 2^32) and w = u * H (64 bits), p1 = the high word of w (a
+// multiply-high into [0, H)); the low word gives the second position,
+// p2 = p1 + 1 + (low >> sh) mod H, where sh makes the offset at most H - 2,
+// so p2 != p1.  Two multiplies per key.  Every key of a built table sits at
+// one of its two positions, so a lookup reads exactly two slots (Pagh and
+// Rodler's cuckoo hashing; parallel insertion by atomic exchange as in
+// Alcantara et al.'s GPU hash tables).
 struct CuckooHash {
-    unsigned c1, c2, H;
-    __device__ __forceinline__ unsigned h1(unsigned x) const { return __umulhi(x * c1, H); }
-    __device__ __forceinline__ unsigned h2(unsigned x, unsigned p1) const {
-        const unsigned t = p1 + 1u + __umulhi(x * c2, H - 1u);
-        return t >= H ? t - H : t;
+    unsigned c, H, sh;
+    __device__ __forceinline__ void pos(unsigned x, unsigned &p1, unsigned &p2) const {
+        const unsigned long long w = (unsigned long long)(x * c) * H;
+        p1 = (unsigned)(w >> 32);
+        const unsigned t = p1 + 1u + ((unsigned)w >> sh);
+        p2 = t >= H ? t - H : t;
+    }
+    __device__ __forceinline__ unsigned h1(unsigned x) const {
+        return (unsigned)(((unsigned long long)(x * c) * H) >> 32);
     }
 };
-// Multiplier pairs of the first attempt and of the retry (odd constants).
-constexpr unsigned CUCKOO_A1 = 0x9E3779B1u, CUCKOO_A2 = 0x85EBCA77u;
-constexpr unsigned CUCKOO_B1 = 0xC2B2AE3Du, CUCKOO_B2 = 0x27D4EB2Fu;
+// sh for a table of H slots: 32 - floor(log2(H - 1)).
+__host__ __device__ __forceinline__ unsigned cuckoo_shift(unsigned H) {
+    unsigned l = 0;
+    while ((2u << l) <= H - 1) ++l;
+    return 32u - l;
+}
+// Multipliers of the first attempt and of the retry (odd constants).
+constexpr unsigned CUCKOO_A = 0x9E3779B1u, CUCKOO_B = 0xC2B2AE3Du;
 constexpr int CUCKOO_KICKS = 64;
 __host__ __device__ __forceinline__ long long mca_bytes(long long mnz, int acc, bool setbits) {
     return align8(4 * mnz) + align8(mnz * acc) + (setbits ? 4 * words32(mnz) : 0);

@@ -117,7 +117,9 @@ constexpr int LONG_SEG = MSG_LONG_SEG;
 
 // The walk of one range [s, e) by the whole warp, chunks of 128 entries
 // (4 loads per lane in flight), from chunk c0 in steps of cstep chunks.
-template <int SR, class F>
+// With WSYNC every lane calls f for every slot (column -1: no product), so f
+// may use warp-wide votes; otherwise only lanes holding a product call it.
+template <int SR, bool WSYNC = false, class F>
 __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
                                            const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
@@ -127,16 +129,18 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
         in_t bv[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-            const long long q = q0 + x * 32 + lane;
+            // q0 < e < 2^31, so q stays below 2^32: 32-bit index arithmetic
+            const unsigned q = (unsigned)q0 + (unsigned)(x * 32 + lane);
             col[x] = -1;
-            if (q < e) {
+            bv[x] = in_t{};
+            if (q < (unsigned)e) {
                 col[x] = __ldg(ici + q);
                 bv[x] = load_val<SR>(iv, q);
             }
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
-            if (col[x] >= 0) f(t, a, col[x], bv[x]);
+            if (WSYNC || col[x] >= 0) f(t, a, col[x], bv[x]);
     }
 }
 
@@ -147,7 +151,7 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
 constexpr int BIG_SEG = 2048;
 constexpr int BIG_LIST = 128;
 
-template <int SR, bool CTA, bool OUTV, class Seg, class F>
+template <int SR, bool CTA, bool OUTV, bool WSYNC = false, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
                                               const Seg &seg, const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
@@ -192,7 +196,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             lmask &= lmask - 1;
             const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
             const in_t au = shfl_val<SR>(av, u);
-            walk_range<SR>(tbase + nw * u, au, su, eu, 0, 1, ici, iv, f);
+            walk_range<SR, WSYNC>(tbase + nw * u, au, su, eu, 0, 1, ici, iv, f);
         }
         // short ranges: load-balanced flat enumeration, two products per lane
         // per pass (both searches and both loads in flight together)
@@ -225,8 +229,8 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
                 col1 = __ldg(ici + q1);
                 b1 = load_val<SR>(iv, q1);
             }
-            if (p0 < total) f(tbase + nw * k0, a0, col0, b0);
-            if (p1 < total) f(tbase + nw * k1, a1, col1, b1);
+            if (WSYNC || p0 < total) f(tbase + nw * k0, a0, col0, b0);
+            if (WSYNC || p1 < total) f(tbase + nw * k1, a1, col1, b1);
         }
     }
     if constexpr (CTA) {
@@ -238,7 +242,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
         for (int i = 0; i < nb; ++i) {
             const int s0 = s_big[i][1], e0 = s_big[i][2];
             const int first = (int)(((long long)wq - g % nw + nw) % nw);
-            walk_range<SR>(s_big[i][0], s_biga[i], s0, e0, first, nw, ici, iv, f);
+            walk_range<SR, WSYNC>(s_big[i][0], s_biga[i], s0, e0, first, nw, ici, iv, f);
             g += (e0 - s0 + 127) / 128;
         }
         __syncthreads();   // the list is reused by the team's next call
@@ -380,8 +384,9 @@ __device__ __forceinline__ bool cuckoo_build(unsigned *key, const CuckooHash &ch
             const unsigned y = atomicExch(&key[pos], x);
             if (y == EMPTY32) break;
             x = y;   // carry the displaced key to its other position
-            const unsigned a = ch.h1(y);
-            pos = pos == a ? ch.h2(y, a) : a;
+            unsigned a, b;
+            ch.pos(y, a, b);
+            pos = pos == a ? b : a;
         }
         if (it == kicks) fail = true;
     }
@@ -426,15 +431,14 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
         acc[h] = 0;
     }
     team.sync();
-    CuckooHash ch{CUCKOO_A1, CUCKOO_A2, H};
+    CuckooHash ch{CUCKOO_A, H, cuckoo_shift(H)};
     const int kicks = L.hash_kicks;
     bool linear = kicks <= 0;
     if (linear) {
         linear_build<CTA>(key, ch, mcols, mnz);
     } else if (cuckoo_build<CTA>(key, ch, mcols, mnz, kicks)) {
         clear_keys<CTA>(key, H);
-        ch.c1 = CUCKOO_B1;
-        ch.c2 = CUCKOO_B2;
+        ch.c = CUCKOO_B;
         if (cuckoo_build<CTA>(key, ch, mcols, mnz, kicks)) {
             clear_keys<CTA>(key, H);
             linear_build<CTA>(key, ch, mcols, mnz);
@@ -449,22 +453,27 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
     };
     // slot of a key known to be in the table
     auto slot_of = [&](unsigned x) -> unsigned {
-        unsigned h = ch.h1(x);
+        unsigned h, h2;
+        ch.pos(x, h, h2);
         if (!linear) {
-            return (key[h] & KMASK) == x ? h : ch.h2(x, h);
+            return (key[h] & KMASK) == x ? h : h2;
         }
         while ((key[h] & KMASK) != x) h = h + 1 == H ? 0u : h + 1;
         return h;
     };
     if (!linear) {
+        // called on every lane for every product slot (j < 0: none), so the
+        // lookup runs without a branch around it
         auto ins = [&](int, in_t a, int j, in_t b) {
             const unsigned x = (unsigned)j;
-            const unsigned p1 = ch.h1(x), p2 = ch.h2(x, p1);
+            unsigned p1, p2;
+            ch.pos(x, p1, p2);
             const unsigned k1 = key[p1], k2 = key[p2];
-            const bool f1 = (k1 & KMASK) == x;
-            if (f1 || (k2 & KMASK) == x) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
+            const bool ok = j >= 0;
+            const bool f1 = ok & ((k1 & KMASK) == x), f2 = ok & ((k2 & KMASK) == x);
+            if (f1 | f2) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
         };
-        enum_products<SR, CTA, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+        enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     } else {
         auto ins = [&](int, in_t a, int j, in_t b) {
             unsigned h = ch.h1((unsigned)j);
@@ -1144,7 +1153,7 @@ __global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet 
 }
 
 template <int SR, int KIND>
-__global__ void __launch_bounds__(256) k_rows_b(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+__global__ void __launch_bounds__(256, 4) k_rows_b(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int scratch[40];
     __shared__ int s_row;

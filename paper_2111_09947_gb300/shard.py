@@ -110,3 +110,27 @@ def sharded_product(M, A, B, compute, rank: int, world: int, group=None, device=
     nnz = int(rp[-1]) if len(rp) else 0
     offsets = gather_row_offsets(nnz, device=device, group=group)
     return {"r0": r0, "r1": r1, "offset": int(offsets[rank]), "nnz": nnz, "result": res}
+
+
+def allreduce_sum(x, group=None):
+    """In-place sum of a tensor over the group (the one data-path exchange of
+    a row-sharded triangle count: each rank's partial count)."""
+    import torch.distributed as dist
+    dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+    return x
+
+
+def sharded_triangle_count(L, count_block, rank: int, world: int, group=None, device=None):
+    """Triangle count of the strict lower triangle L (C = L .* (L L) on
+    plus-pair, count = sum(C), Sec. 8.2) split by rows: this rank computes the
+    block of rows that partition_rows gives it by push work (L replicated as
+    the right operand), count_block(L_block, L) returns its partial count as
+    a one-element int64 tensor on `device`, and an all-reduce sums the
+    partial counts.  Returns dict(r0, r1, local, total)."""
+    b = partition_rows(push_work(L, L), world)
+    r0, r1 = int(b[rank]), int(b[rank + 1])
+    Lb = row_block(L, r0, r1)
+    part = count_block(Lb, L)
+    local = int(part.item())
+    total = allreduce_sum(part, group=group)
+    return {"r0": r0, "r1": r1, "local": local, "total": int(total.item())}

@@ -45,6 +45,52 @@ def _sharded_worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
+def _tc_worker(rank, world, port, q):
+    """Each rank counts the triangles of its row block of L with the oracle;
+    the all-reduce gives every rank the whole count."""
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import sys
+        sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        from oracle import oracle as O
+        from paper_2111_09947_gb300 import synth
+        L = synth.triangle_counting(scale=10, ef=8, seed=3)["M"]
+
+        def count_block(Lb, Lfull):
+            r = O.masked_spgemm(Lb, Lb, Lfull, "plus_pair_i64")
+            return torch.tensor([int(r["values"].sum())], dtype=torch.int64)
+        out = shard.sharded_triangle_count(L, count_block, rank, world)
+        q.put((rank, out))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_sharded_triangle_count():
+    """A triangle count split by rows over two gloo ranks: the blocks cover
+    the rows once, and the all-reduced count equals the whole product's."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    from oracle import oracle as O
+    from paper_2111_09947_gb300 import synth
+    L = synth.triangle_counting(scale=10, ef=8, seed=3)["M"]
+    want = int(O.masked_spgemm(L, L, L, "plus_pair_i64")["values"].sum())
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_tc_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert res[0]["r0"] == 0 and res[0]["r1"] == res[1]["r0"] and res[1]["r1"] == L.nrows
+    assert res[0]["local"] + res[1]["local"] == want
+    assert res[0]["total"] == res[1]["total"] == want
+    assert res[0]["local"] > 0 and res[1]["local"] > 0
+
+
 def _worker(rank, world, port, q):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
