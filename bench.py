@@ -530,8 +530,9 @@ def measure(torch, _lib, synth, h, wl, dev, stream, flush, steps, warmup, clocks
     h.set_option(_lib.OPT_PROFILE, 1)
     timed_steps(torch, run.step, max(3, min(steps, 10)), flush, stream, after=collect)
     h.set_option(_lib.OPT_PROFILE, 0)
+    kind_rows = {k: v for k, v in h.bin_counts().items() if v} if wl.name != "autograd" else None
     out = {"times": times, "launches": launches, "clocks": clk, "per_phase": per_phase, "kinds": kinds, "run": run,
-           "autotune_s": tune_s}
+           "autotune_s": tune_s, "kind_rows": kind_rows}
     if wl.name == "batched":
         run.per_product_step()
         torch.cuda.synchronize()
@@ -691,6 +692,8 @@ def form_summary(wl, meas):
         d["push_products"] = push_products(A, B)
     if meas["per_phase"]:
         d["phase_ms"] = {n: round(statistics.mean(v), 4) for n, v in meas["per_phase"].items()}
+    if meas.get("kind_rows"):
+        d["kind_rows"] = meas["kind_rows"]
     for k in ("per_product_ms", "graph_ms", "fwd_ms", "bwd_ms", "bwd_unplanned_ms"):
         if k in meas:
             d[k] = round(meas[k], 3)
@@ -769,6 +772,7 @@ def run_ours(args):
         "data": "synthetic (seeded R-MAT / Erdos-Renyi; the paper's SuiteSparse graphs are not used)",
         "config": cfg, "gpu_launches": int(meas["launches"]), "roofline": roof,
         "hbm_min_gbs": summary.get("hbm_min_gbs"), "phase_ms": summary.get("phase_ms"),
+        "kind_rows": summary.get("kind_rows"),
         "clocks": meas["clocks"], "e2e": e2e, "gen_seconds": round(gen_s, 2), "autotune_s": meas["autotune_s"],
         "counts": {"masked_products": wl.kept, "nnz_C": wl.nnz_c, "seed_per_rank": world > 1 and not sharded},
     }

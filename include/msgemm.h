@@ -117,13 +117,18 @@ typedef enum {
                                      numeric pass writes each row in place: no temporary, more
                                      work.  Two phases never use the (row, tile) grid kinds
                                      nor a CUDA graph (use_graph is ignored). */
-    MSGEMM_OPT_HASH_KICKS = 10    /* value 0..4096 (default 64): the hash rows (Sec. 5.3) place
+    MSGEMM_OPT_HASH_KICKS = 10,   /* value 0..4096 (default 64): the hash rows (Sec. 5.3) place
                                      each mask column by two-choice (cuckoo) hashing, moving at
                                      most this many keys per insertion; a row whose insertion
                                      runs out retries with a second pair of hash functions, then
                                      falls back to linear probing.  0 = linear probing only.
                                      The result never depends on it (tests use 0 and 1 to run
                                      every build path). */
+    MSGEMM_OPT_QTEAM_FLOPS = 11   /* value 0..2^20 (default 1024): plain rows with at most 8 mask
+                                     entries and at most this many push products take the
+                                     mask-compressed accumulator (Sec. 5.4) on a team of eight
+                                     lanes (four rows per warp, the mask row and its accumulators
+                                     in registers) -- under AUTO and when MCA is forced; 0 = never */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

@@ -72,6 +72,10 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
         return heavy;
     }
     if (flops == 0 || mnz == 0) return K_EMPTY;
+    // the smallest rows: MCA on a team of eight (a family choice of MCA, or AUTO)
+    if (pol.q_flops_max > 0 && mnz <= QMASK && flops <= pol.q_flops_max &&
+        (pol.force == F_AUTO || pol.force == F_MCA))
+        return K_MCA_Q;
     // heaviest rows of products wider than a tile: (row, tile) items over the GPU
     const bool grid_ok = pol.grid > 0 && !warp && index_ok && n > pol.tileT[0] &&
                          (n + pol.tileT[0] - 1) / pol.tileT[0] <= GRID_MAX_TILES;

@@ -43,6 +43,7 @@ struct msgemm_handle {
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
+    int q_flops_max = 1024;   // MSGEMM_OPT_QTEAM_FLOPS: K_MCA_Q rows (0: never)
     int warp_slab = 4608;   // shared bytes per warp of the one-warp row kinds
     long long grid_min_flops = 1LL << 20;   // MSA_G: plain CTA rows with at least this push work
     int *last_kind_count = nullptr;
@@ -162,7 +163,7 @@ struct PScope {
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
                                        "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g",
-                                       "heap_w", "heapdot_w", "cheap_w"};
+                                       "heap_w", "heapdot_w", "cheap_w", "mca_q"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -206,6 +207,7 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.allow_dot = h->allow_dot;
     p.dot_ratio = h->dot_ratio;
     p.warp_flops_max = h->warp_flops_max;
+    p.q_flops_max = h->q_flops_max;
     const int acc = acc_bytes(sr);
     const int wslab = h->warp_slab;   // default 4.5 KB: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
     const int bslab = 32 * 1024;  // per CTA-row: 7 CTAs per SM
@@ -521,6 +523,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (any_plain) {
         if (pl.pol.slab[K_MSA_W]) pl.kinds.push_back(K_MSA_W);
         pl.kinds.insert(pl.kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
+        if (pl.pol.q_flops_max > 0) pl.kinds.push_back(K_MCA_Q);
         if (!pl.bd.empty() ||
             std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
             pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
@@ -939,6 +942,7 @@ struct Tuned {
     int warp_slab = 4608;
     long long grid_min_flops = 1LL << 20;
     unsigned char pref[NCLASS][4];
+    int q_flops_max = 1024;
 };
 
 Tuned current_tuned(const msgemm_handle *h) {
@@ -948,6 +952,7 @@ Tuned current_tuned(const msgemm_handle *h) {
     t.warp_slab = h->warp_slab;
     t.grid_min_flops = h->grid_min_flops;
     memcpy(t.pref, h->pref, sizeof t.pref);
+    t.q_flops_max = h->q_flops_max;
     return t;
 }
 
@@ -957,12 +962,14 @@ void apply_tuned(msgemm_handle *h, const Tuned &t) {
     h->warp_slab = t.warp_slab;
     h->grid_min_flops = t.grid_min_flops;
     memcpy(h->pref, t.pref, sizeof t.pref);
+    h->q_flops_max = t.q_flops_max;
 }
 
 // Cache file: a JSON object, one entry per line,
 //   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "grid_min_flops": G,
-//                                "pref": [[f,f,f,f], ...]}
-// with NCLASS preference rows of accumulator families (msgemm_accumulator).
+//                                "pref": [[f,f,f,f], ...], "q_flops_max": Q}
+// with NCLASS preference rows of accumulator families (msgemm_accumulator);
+// an entry without q_flops_max (written before it existed) keeps its default.
 void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
     FILE *f = fopen(path, "r");
     if (!f) return;
@@ -983,7 +990,7 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ++c;
             }
         }
-        if (num.size() != 4 + NCLASS * 4) continue;
+        if (num.size() != 4 + NCLASS * 4 && num.size() != 5 + NCLASS * 4) continue;
         Tuned t;
         if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
         if (num[2] < 1024 || num[2] > 24576 || (int)num[2] % 16) continue;
@@ -999,6 +1006,11 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ok &= v >= F_AUTO && v <= F_HEAPDOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
+        if (num.size() == 5 + NCLASS * 4) {
+            const double q = num[4 + NCLASS * 4];
+            ok &= q >= 0 && q <= (1 << 20) && q == (int)q;
+            t.q_flops_max = (int)q;
+        }
         if (ok) out[key] = t;
     }
     fclose(f);
@@ -1016,7 +1028,7 @@ bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
                 kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab, t.grid_min_flops);
         for (int c = 0; c < NCLASS; ++c)
             fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
-        fprintf(f, "]}%s\n", ++i < m.size() ? "," : "");
+        fprintf(f, "], \"q_flops_max\": %d}%s\n", t.q_flops_max, ++i < m.size() ? "," : "");
     }
     fprintf(f, "}\n");
     const bool ok = fclose(f) == 0;
@@ -1147,6 +1159,16 @@ struct Tuner {
             if (t < best * keep) { best = t; wbest = w; }
         }
         h->warp_flops_max = wbest;
+        const int qbest0 = h->q_flops_max;
+        int qbest = qbest0;
+        for (int q : {0, 256, 1024, 4096, 16384, 65536, 1 << 20}) {
+            if (q == qbest0) continue;
+            h->q_flops_max = q;
+            float t;
+            CKS(measure(&t));
+            if (t < best * keep) { best = t; qbest = q; }
+        }
+        h->q_flops_max = qbest;
         const int sbest0 = h->warp_slab;
         int sbest = sbest0;
         for (int sl : {3072, 3584, 4096, 4608, 6144, 9216}) {
@@ -1255,6 +1277,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_PHASES:
         if (value != 1 && value != 2) return fail(h, MSGEMM_ERR_INVALID, "phases is 1 or 2");
         h->phases = (int)value;
+        return MSGEMM_OK;
+    case MSGEMM_OPT_QTEAM_FLOPS:
+        if (value < 0 || value > (1 << 20)) return fail(h, MSGEMM_ERR_INVALID, "team-of-eight flop bound is 0..2^20");
+        h->q_flops_max = (int)value;
         return MSGEMM_OK;
     case MSGEMM_OPT_HASH_KICKS:
         if (value < 0 || value > 4096) return fail(h, MSGEMM_ERR_INVALID, "hash kicks is 0..4096");

@@ -36,8 +36,13 @@ enum Kind : int {
     K_HEAP_W,      // plain: multiway merge of B rows (Sec. 5.5), NInspect = 1
     K_HEAPDOT_W,   // plain: the same with NInspect unbounded
     K_CHEAP_W,     // complemented: multiway merge, NInspect = 0
+    K_MCA_Q,       // plain, tiny rows: MCA on an eight-lane team, mask row in registers
     NKIND
 };
+
+// K_MCA_Q rows: at most QMASK mask entries and at most Policy.q_flops_max
+// push products; QTEAM lanes per row.
+constexpr int QMASK = 8, QTEAM = 8;
 
 // Families (msgemm_accumulator) for preference lists.
 enum Family : int { F_AUTO = 0, F_MSA = 1, F_HASH = 2, F_MCA = 3, F_DOT = 4, F_HEAP = 5, F_HEAPDOT = 6 };
@@ -150,6 +155,8 @@ struct Policy {
     int allow_dot;
     float dot_ratio;              // pull when pull_cost * dot_ratio < flops
     int warp_flops_max;           // rows above go to CTA-level kinds
+    int q_flops_max;              // K_MCA_Q: plain rows with <= QMASK mask entries and at most this
+                                  // many push products (0: never)
     int slab[NKIND];              // bytes per warp (_W) or per CTA (_B, _T); 0 = disabled
     int tileT[2];                 // MSA_T tile width for [plain, complemented]
     int grid;                     // grid kinds: 0 off, 1 by the rules below, 2 for every heavy row

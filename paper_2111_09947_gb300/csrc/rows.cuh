@@ -73,6 +73,16 @@ __device__ __forceinline__ typename Sr<SR>::in_t shfl_val(typename Sr<SR>::in_t 
     else return v;
 }
 
+template <int SR>
+__device__ __forceinline__ typename Sr<SR>::in_t shfl_val_mask(unsigned m, typename Sr<SR>::in_t v, int src) {
+    if constexpr (Sr<SR>::vals) return __shfl_sync(m, v, src);
+    else return v;
+}
+template <int SR>
+__device__ __forceinline__ typename Sr<SR>::acc_t shfl_xor_acc(unsigned m, typename Sr<SR>::acc_t v, int o) {
+    return __shfl_xor_sync(m, v, o);
+}
+
 __device__ __forceinline__ bool test_bit(const unsigned *w, int b) { return (w[b >> 5] >> (b & 31)) & 1u; }
 __device__ __forceinline__ void set_bit_once(unsigned *w, int b) {
     unsigned m = 1u << (b & 31);
@@ -1149,6 +1159,122 @@ __global__ void __launch_bounds__(256) k_rows_w(const __grid_constant__ ProdSet 
         else if (KIND == K_HEAP_W) row_heap<SR, 1, false>(P, c, L);
         else if (KIND == K_HEAPDOT_W) row_heap<SR, HEAP_INSPECT_ALL, false>(P, c, L);
         else if (KIND == K_CHEAP_W) row_heap<SR, 0, true>(P, c, L);
+    }
+}
+
+// --------------------------------------------------------------- MCA, team of eight
+// Sec. 5.4's mask-compressed accumulator for the smallest rows (at most QMASK
+// mask entries and few push products, the bulk of the rows of a batch of
+// small products): an eight-lane team per row, four rows per warp.  The mask
+// row m sits in registers of every lane of the team, and so do the QMASK
+// accumulators of its entries: a product's rank in m is the index of the mask
+// column equal to its column, found by comparing with all of them (after a
+// range test that rejects most products at once).  The team walks the rows of
+// B one A entry at a time, its lanes striding B_k*; afterwards it sums its
+// lanes' accumulators with shuffles and writes the SET entries in mask order.
+// No shared memory and no barrier: the per-row fixed cost of the warp kinds
+// (clearing, staging, gathering mask-sized arrays) is what dominates such rows.
+template <int SR>
+__global__ void __launch_bounds__(256) k_rows_q(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using in_t = typename S::in_t;
+    using out_t = typename S::out_t;
+    const int lane = lane_id(), g = lane >> 3, tl = lane & 7;
+    const unsigned tmask = 0xffu << (8 * g);   // the team's lanes
+    const int count = L.ra.kind_count[K_MCA_Q];
+    const int off = L.ra.kind_off[K_MCA_Q];
+    for (;;) {
+        int x = 0;
+        if (lane == 0) x = atomicAdd(&L.ra.kind_next[K_MCA_Q], 4);
+        x = __shfl_sync(FULL, x, 0);
+        if (x >= count) break;   // uniform over the warp
+        const int xr = x + g;    // this team's row (none past the bucket's end)
+        const bool have = xr < count;
+        const long long r = have ? (long long)L.ra.perm[off + xr] : 0;
+        const DevProd &P = prod_at(ps, have ? row_prod(ps, L.ra.prod, r) : 0);
+        int a0 = 0, a1 = 0, m0 = 0, mnz = 0;
+        long long tmp = 0;
+        if (have) {
+            const long long i = r - P.row0;
+            a0 = __ldg(P.a_rp + i);
+            a1 = __ldg(P.a_rp + i + 1);
+            m0 = __ldg(P.m_rp + i);
+            mnz = __ldg(P.m_rp + i + 1) - m0;
+            tmp = L.ra.tmpoff[r];
+        }
+        // the mask row in registers; -1 (never a column) past its end
+        const int mv = tl < mnz ? __ldg(P.m_ci + m0 + tl) : -1;
+        int mk[QMASK];
+#pragma unroll
+        for (int q = 0; q < QMASK; ++q) mk[q] = __shfl_sync(FULL, mv, (g << 3) + q);
+        const int mlo = mk[0];
+        const int mhi = __shfl_sync(FULL, mv, (g << 3) + max(mnz - 1, 0));
+        const unsigned mspan = (unsigned)(mhi - mlo);
+        acc_t acc[QMASK];
+#pragma unroll
+        for (int q = 0; q < QMASK; ++q) acc[q] = 0;
+        unsigned setm = 0;
+        if (mnz > 0) {   // uniform over the team
+            // A entries eight at a time: lane u holds entry a + u (its value
+            // and the range of its row of B); the team then walks each row
+            for (int a = a0; a < a1; a += QTEAM) {
+                const int t = a + tl;
+                int s = 0, e = 0;
+                in_t av{};
+                if (t < a1) {
+                    const int k = __ldg(P.a_ci + t);
+                    av = load_val<SR>(P.a_v, t);
+                    s = __ldg(P.b_rp + k);
+                    e = __ldg(P.b_rp + k + 1);
+                }
+                const int na = min(QTEAM, a1 - a);
+                for (int u = 0; u < na; ++u) {   // uniform over the team
+                    const int src = (g << 3) + u;
+                    const int su = __shfl_sync(tmask, s, src), eu = __shfl_sync(tmask, e, src);
+                    const in_t au = shfl_val_mask<SR>(tmask, av, src);
+                    for (int q = su + tl; q < eu; q += QTEAM) {
+                        const int j = __ldg(P.b_ci + q);
+                        if ((unsigned)(j - mlo) > mspan) continue;   // outside the mask row's range
+                        unsigned hitm = 0;
+#pragma unroll
+                        for (int w = 0; w < QMASK; ++w) hitm |= (j == mk[w]) ? (1u << w) : 0u;
+                        if (hitm) {
+                            const acc_t pv = S::mul(au, load_val<SR>(P.b_v, q));
+#pragma unroll
+                            for (int w = 0; w < QMASK; ++w)
+                                if (hitm & (1u << w)) acc[w] += pv;
+                            setm |= hitm;
+                        }
+                    }
+                }
+            }
+        }
+        // team sums (a fixed butterfly over the eight lanes)
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+#pragma unroll
+            for (int w = 0; w < QMASK; ++w) acc[w] += shfl_xor_acc<SR>(FULL, acc[w], o);
+            setm |= __shfl_xor_sync(FULL, setm, o);
+        }
+        acc_t v = 0;
+#pragma unroll
+        for (int w = 0; w < QMASK; ++w)
+            if (w == tl) v = acc[w];
+        const bool keep = have && tl < mnz && ((setm >> tl) & 1u);
+        const unsigned bal = (__ballot_sync(FULL, keep) >> (8 * g)) & 0xffu;
+        if (have) {
+            const TmpOut T = out_of(P, L);
+            out_t *tv = static_cast<out_t *>(T.v);
+            if (L.aligned) {
+                if (keep) tv[tmp + tl] = S::out(v);
+            } else if (!L.count_only && keep) {
+                const long long o = tmp + __popc(bal & ((1u << tl) - 1u));
+                T.ci[o] = mv;
+                tv[o] = S::out(v);
+            }
+            if (tl == 0) L.ra.cnt[r] = __popc(bal);
+        }
     }
 }
 

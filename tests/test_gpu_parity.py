@@ -342,3 +342,62 @@ def test_backward_plan_outlived_by_handle_close():
             _lib.msgemm_backward(h2, d["A"], d["B"], G, plan=plan)
     finally:
         h2.close()
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("qflops", [0, 1024, 1 << 20])
+def test_team_of_eight_mca(handle, semiring, qflops):
+    """Rows with at most 8 mask entries and at most MSGEMM_OPT_QTEAM_FLOPS
+    push products take the mask-compressed accumulator on an eight-lane team
+    (Sec. 5.4; mask row and accumulators in registers).  Mask rows of 0 to 12
+    entries, A rows of 0 to 40 entries over B rows of 1 to 300: some rows
+    qualify, some are too heavy or have too many mask entries.  AUTO and forced
+    MCA, one and two phases, against the oracle."""
+    rng = np.random.default_rng(77)
+    m, k, n = 900, 700, 5000
+    mdeg = np.arange(m) % 13
+    rows, cols = [], []
+    for i in range(m):
+        c = np.sort(rng.choice(n, size=int(mdeg[i]), replace=False))
+        rows.append(np.full(len(c), i))
+        cols.append(c)
+    M = synth.coo_to_csr(m, n, np.concatenate(rows).astype(np.int32), np.concatenate(cols).astype(np.int32))
+    q = synth.random_problem(m, k, n, 10.0, 30.0, 1.0, 78, GEN[semiring])
+    q["M"] = M
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring)
+    handle.set_option(_lib.OPT_QTEAM_FLOPS, qflops)
+    try:
+        for force in ("auto", "mca"):
+            for phases in (1, 2):
+                handle.set_option(_lib.OPT_PHASES, phases)
+                res = run(handle, q, semiring, False, force)
+                assert_parity(res, ref, semiring, ctx=f"q={qflops} force={force} phases={phases}")
+                nq = handle.bin_counts()["mca_q"]
+                assert (nq > 0) == (qflops > 0), nq
+    finally:
+        handle.set_option(_lib.OPT_PHASES, 1)
+        handle.set_option(_lib.OPT_QTEAM_FLOPS, 1024)
+        handle.force("auto")
+
+
+def test_team_of_eight_gradient_form(handle):
+    """The backward's dA product (mask = pattern(A), values at each mask
+    entry's own slot) through the team-of-eight rows: every row of A has at
+    most 8 entries, so with a high flop bound every row qualifies."""
+    m, k, n = 600, 500, 700
+    p = synth.random_problem(m, k, n, 4.0, 5.0, 30.0, 79, "f32")
+    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_times_f32")
+    G = synth.Csr(m, n, ref["rowptr"].astype(np.int32), ref["colidx"], synth.upstream_grad(len(ref["colidx"]), 79))
+    dA_ref, dB_ref = O.grad(p["A"], p["B"], G)
+    SA, SB = _grad_bounds(p, G)
+    d = to_dev(p, "plus_times_f32")
+    handle.set_option(_lib.OPT_QTEAM_FLOPS, 1 << 20)
+    handle.set_option(_lib.OPT_DOT, 0)
+    try:
+        dA, dB = _lib.msgemm_backward(handle, d["A"], d["B"], _lib.DeviceCsr.from_host(G))
+        handle.sync_status()
+    finally:
+        handle.set_option(_lib.OPT_QTEAM_FLOPS, 1024)
+        handle.set_option(_lib.OPT_DOT, 1)
+    assert np.all(np.abs(dA.cpu().numpy().astype(np.float64) - dA_ref) <= 1e-5 * SA + 1e-30)
+    assert np.all(np.abs(dB.cpu().numpy().astype(np.float64) - dB_ref) <= 1e-5 * SB + 1e-30)

@@ -147,14 +147,19 @@ def test_autograd_problem_scale18_full(handle):
         assert np.all(eB <= 1e-5 * SB + 1e-30), f"dB: {(eB > 1e-5 * SB).sum()} entries outside (rep {rep})"
 
 
-def test_batched_full_size_sampled_products(handle):
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_full_size_all_products(handle, use_graph):
+    """The 256-product batch at its full size, every product against the
+    oracle (eagerly, and replayed from a captured CUDA graph)."""
     ps = synth.batched_problems(nprod=256)
     devs = [to_dev(q, "plus_times_f32") for q in ps]
-    outs = _lib.msgemm_run_batched(handle, [x["M"] for x in devs], [x["A"] for x in devs], [x["B"] for x in devs],
-                                   "plus_times_f32")
+    args = ([x["M"] for x in devs], [x["A"] for x in devs], [x["B"] for x in devs])
+    outs = _lib.msgemm_run_batched(handle, *args, "plus_times_f32", use_graph=use_graph)
+    if use_graph:   # a second call replays the graph
+        outs = _lib.msgemm_run_batched(handle, *args, "plus_times_f32", use_graph=True)
     handle.sync_status()
-    for pidx in (0, 1, 2, 100, 255):
-        q = ps[pidx]
+    assert handle.bin_counts()["mca_q"] > 0
+    for pidx, q in enumerate(ps):
         ref = O.masked_spgemm(q["M"], q["A"], q["B"], "plus_times_f32")
         assert_parity(outs[pidx].trimmed(), ref, "plus_times_f32", ctx=f"product {pidx}")
 
