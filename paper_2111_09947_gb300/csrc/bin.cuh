@@ -172,11 +172,13 @@ __device__ __forceinline__ long long warp_len_sum_until(const int *idx, const in
 }
 
 // Flops, pull work, kind and temporary room of every row.  A warp takes up
-// to 32 consecutive rows, one per lane: rows whose A row and (when pull is
-// possible) mask row have at most SHORT_ROW entries are summed by their own
-// lane; longer rows up to LONG_ROW entries are then summed by the whole warp
-// one at a time; rows beyond go to a list that k_bin_long sums with a whole
-// CTA each.  Every lane then picks its row's kind.
+// to 32 consecutive rows, one per lane: a row whose A row has at most
+// SHORT_ROW entries is summed by its own lane, and so is its pull work over
+// up to SHORT_ROW mask entries (the partial sum usually decides against pull
+// after a few); rows with longer A rows, or whose pull work is still open,
+// are then summed by the whole warp one at a time; rows beyond LONG_ROW
+// entries go to a list that k_bin_long sums with a whole CTA each.  Every
+// lane then picks its row's kind.
 constexpr int SHORT_ROW = 32;
 constexpr int LONG_ROW = 1024;
 
@@ -219,23 +221,30 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
             m0 = __ldg(P.m_rp + i); m1 = __ldg(P.m_rp + i + 1);
         }
         const bool dot_ok = valid && !P.complement && P.bt_rp != nullptr && P.a_sorted && pol.allow_dot;
-        const bool is_short = a1 - a0 <= SHORT_ROW && (!dot_ok || m1 - m0 <= SHORT_ROW);
+        const bool a_short = a1 - a0 <= SHORT_ROW;
         const bool is_huge = a1 - a0 > LONG_ROW || (dot_ok && m1 - m0 > LONG_ROW);
         long long f = 0, pull = 0;
-        if (valid && is_short) {
+        bool pull_open = false;   // pull work not yet decided by the lane's own partial sum
+        if (valid && a_short && !is_huge) {
             for (int t = a0; t < a1; ++t) {
                 const int k = __ldg(P.a_ci + t);
                 f += __ldg(P.b_rp + k + 1) - __ldg(P.b_rp + k);
             }
-            if (dot_ok)
-                for (int q = m0; q < m1; ++q) {
+            if (dot_ok) {
+                // the lane sums up to SHORT_ROW mask entries and stops once the
+                // partial sum rules pull out; rows still open go to the warp
+                const int qe = min(m1, m0 + SHORT_ROW);
+                bool decided = false;
+                for (int q = m0; q < qe; ++q) {
                     const int j = __ldg(P.m_ci + q);
                     pull += __ldg(P.bt_rp + j + 1) - __ldg(P.bt_rp + j);
-                    if ((double)pull * pol.dot_ratio >= (double)f) break;   // decided: no pull
+                    if ((double)pull * pol.dot_ratio >= (double)f) { decided = true; break; }   // no pull
                 }
+                pull_open = !decided && m1 - m0 > SHORT_ROW;
+            }
         }
         if (valid && is_huge) ra.perm[atomicAdd(ra.nlong, 1)] = (int)r;   // to k_bin_long
-        unsigned longs = __ballot_sync(FULL, valid && !is_short && !is_huge);
+        unsigned longs = __ballot_sync(FULL, valid && !is_huge && (!a_short || pull_open));
         while (longs) {
             const int u = __ffs(longs) - 1;
             longs &= longs - 1;
@@ -243,7 +252,9 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
             const int ua0 = __shfl_sync(FULL, a0, u), ua1 = __shfl_sync(FULL, a1, u);
             const int um0 = __shfl_sync(FULL, m0, u), um1 = __shfl_sync(FULL, m1, u);
             const bool udot = __shfl_sync(FULL, dot_ok, u);
-            const long long fu = warp_len_sum(Q.a_ci, Q.b_rp, ua0, ua1);
+            const bool ushort = __shfl_sync(FULL, a_short, u);
+            const long long fl = __shfl_sync(FULL, f, u);
+            const long long fu = ushort ? fl : warp_len_sum(Q.a_ci, Q.b_rp, ua0, ua1);
             const long long pu = udot ? warp_len_sum_until(Q.m_ci, Q.bt_rp, um0, um1, pol.dot_ratio, fu) : 0;
             if (lane == u) {
                 f = fu;

@@ -1381,6 +1381,21 @@ struct GridIns {
             atomicOr(err, ERR_INTERNAL);
             return;
         }
+        if (COMP && !track) {
+            // speculative complemented tile: every product is added, with no
+            // state read; the gather drops (and clears) the columns the mask
+            // holds.  One shared access per product instead of two.
+            const typename S::acc_t v = S::mul(a, b);
+            if constexpr (TA::split) {
+                const unsigned l = (unsigned)v;
+                const unsigned old = atomicAdd(&vals[jj], l);
+                if (!grid_safe<SR>(v) || old + l < old) *unsafe = 1;
+            } else {
+                TA::add(vals, hi, jj, v);
+                if (!grid_safe<SR>(v)) *unsafe = 1;
+            }
+            return;
+        }
         const unsigned w = st[jj >> 4] >> (2 * (jj & 15));
         if ((w & 1u) != (COMP ? 1u : 0u)) {
             const typename S::acc_t v = S::mul(a, b);
@@ -1456,13 +1471,19 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
     }
     // gather the SET columns in ascending order; each thread owns a run of
     // state words (16 columns each), and clears them
-    auto set_bits = [&](int w) -> unsigned {   // bit 2b + 1 set for SET column 16 w + b
-        if (tracked) return (st[w] >> 1) & 0x55555555u;
+    // speculative complemented tiles also added products to the columns the
+    // mask holds (NOTALLOWED, bit 2b of the state word): those are dropped here
+    auto nonzero_bits = [&](int w) -> unsigned {   // bit 2b set for column 16 w + b with a non-zero value
         unsigned m = 0;
         const int cend = min(16, (c1 - c0) - 16 * w);
         for (int b = 0; b < cend; ++b)
             if (vals[16 * w + b] != 0) m |= 1u << (2 * b);
         return m;
+    };
+    auto set_bits = [&](int w) -> unsigned {   // bit 2b set for SET column 16 w + b
+        if (tracked) return (st[w] >> 1) & 0x55555555u;
+        const unsigned m = nonzero_bits(w);
+        return COMP ? m & ~(st[w] & 0x55555555u) : m;
     };
     const int nwords = (c1 - c0 + 15) >> 4;
     const int per = (nwords + team.size() - 1) / team.size();
@@ -1498,6 +1519,14 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
                 L.tmp.ci[o] = c0 + jj;
                 tv[o] = v;
                 ++o;
+            }
+        }
+        if (COMP && !tracked) {   // clear the dropped columns' sums for the next item
+            unsigned d = nonzero_bits(w) & st[w] & 0x55555555u;
+            while (d) {
+                const int b = __ffs(d) - 1;
+                d &= d - 1;
+                vals[w * 16 + (b >> 1)] = 0;
             }
         }
         st[w] = 0;
