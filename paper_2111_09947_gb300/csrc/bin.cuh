@@ -81,11 +81,15 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
                          (n + pol.tileT[0] - 1) / pol.tileT[0] <= GRID_MAX_TILES;
     if (grid_ok && (pol.grid == 2 ? (pol.force == F_AUTO || pol.force == F_MSA) : flops >= pol.grid_min_flops))
         return K_MSA_G;
+    // pull rows with tiny masks and little pull work: pull on a team of eight
+    const bool dot_q = dot_ok && pol.q_flops_max > 0 && mnz <= QDMASK && pull <= pol.q_flops_max;
     if (pol.force != F_AUTO) {
+        if (pol.force == F_DOT && dot_q) return K_DOT_Q;
         const int k = pick_family<SR>(pol, pol.force, warp, flops, mnz, anz, n, dot_ok, true);
         return k >= 0 ? k : K_MSA_T;
     }
     if (dot_ok && (double)pull * pol.dot_ratio < (double)flops) {
+        if (dot_q) return K_DOT_Q;
         const int k = pick_family<SR>(pol, F_DOT, warp, flops, mnz, anz, n, dot_ok, false);
         if (k >= 0) return k;
     }
@@ -117,7 +121,7 @@ __device__ __forceinline__ void finish_row(const DevProd &P, const RowArrays &ra
     }
     atomicAdd(&hist[kind], 1);
     atomicAdd(&hsub[kind * NCLS_FLOPS + flops_sub(f)], 1);
-    if (kind == K_DOT_W || kind == K_DOT_B) *ra.any_dot = 1;
+    if (kind == K_DOT_W || kind == K_DOT_B || kind == K_DOT_Q) *ra.any_dot = 1;
 }
 
 __device__ __forceinline__ void flush_hist(const RowArrays &ra, const int *hist, const int *hsub) {

@@ -163,7 +163,7 @@ struct PScope {
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
                                        "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g",
-                                       "heap_w", "heapdot_w", "cheap_w", "mca_q"};
+                                       "heap_w", "heapdot_w", "cheap_w", "mca_q", "dot_q"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -192,10 +192,17 @@ int out_bytes(msgemm_semiring sr) { return sr == MSGEMM_PLUS_TIMES_F32 ? 4 : 8; 
 // hash table (an Erdos-Renyi sweep of n 2^12..2^20 and degrees 4..64 x 1..256
 // had MCA ahead of hash on nearly every such point, by up to 4x); hash first
 // for heavier rows.
+// Default class preferences (row_class: flop bands <= 512, <= 8192, <= 131072,
+// above; mask bands <= 8, <= 64, <= 512, above): MSA where the dense row
+// fits a warp, then MCA for mask rows of at most 8 entries and for rows of at
+// most 512 push products with mask rows up to 512 entries (setup dominates:
+// MCA clears nnz(m) values, the hash table 4 nnz(m) slots), hash otherwise
+// (two shared loads per product against MCA's log2 nnz(m) search steps).
+// From the Erdos-Renyi density sweep (bench.py --sweep er).
 void default_pref(unsigned char pref[NCLASS][4]) {
     for (int c = 0; c < NCLASS; ++c) {
         const int fb = c / 4, mb = c % 4;
-        if (mb == 0 || (fb <= 1 && mb <= 2)) { pref[c][0] = F_MSA; pref[c][1] = F_MCA; pref[c][2] = F_HASH; }
+        if (mb == 0 || (fb == 0 && mb <= 2)) { pref[c][0] = F_MSA; pref[c][1] = F_MCA; pref[c][2] = F_HASH; }
         else { pref[c][0] = F_MSA; pref[c][1] = F_HASH; pref[c][2] = F_MCA; }
         pref[c][3] = F_AUTO;
     }
@@ -526,7 +533,10 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         if (pl.pol.q_flops_max > 0) pl.kinds.push_back(K_MCA_Q);
         if (!pl.bd.empty() ||
             std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))
+        {
             pl.kinds.insert(pl.kinds.end(), {K_DOT_W, K_DOT_B});
+            if (pl.pol.q_flops_max > 0) pl.kinds.push_back(K_DOT_Q);
+        }
         if (uses(F_HEAP)) pl.kinds.push_back(K_HEAP_W);
         if (uses(F_HEAPDOT)) pl.kinds.push_back(K_HEAPDOT_W);
         pl.kinds.push_back(K_MSA_T);

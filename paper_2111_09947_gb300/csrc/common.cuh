@@ -37,12 +37,19 @@ enum Kind : int {
     K_HEAPDOT_W,   // plain: the same with NInspect unbounded
     K_CHEAP_W,     // complemented: multiway merge, NInspect = 0
     K_MCA_Q,       // plain, tiny rows: MCA on an eight-lane team, mask row in registers
+    K_DOT_Q,       // plain, tiny masks: pull on an eight-lane team, A_i* searched in global memory
     NKIND
 };
 
 // K_MCA_Q rows: at most QMASK mask entries and at most Policy.q_flops_max
-// push products; QTEAM lanes per row.
+// push products; K_DOT_Q rows: pull rows with at most QDMASK mask entries and
+// at most Policy.q_flops_max pull pairs; QTEAM lanes per row.
 constexpr int QMASK = 8, QTEAM = 8;
+// K_DOT_Q: mask entries per row (QDMASK / QTEAM per lane).  32 was measured
+// slower than the warp pull kernel on the batch's 16-entry mask rows: the
+// team walks mask entries one after another, each a chain of dependent
+// global loads, while the warp kernel searches a staged copy of A_i*.
+constexpr int QDMASK = 8;
 
 // Families (msgemm_accumulator) for preference lists.
 enum Family : int { F_AUTO = 0, F_MSA = 1, F_HASH = 2, F_MCA = 3, F_DOT = 4, F_HEAP = 5, F_HEAPDOT = 6 };

@@ -1278,6 +1278,108 @@ __global__ void __launch_bounds__(256) k_rows_q(const __grid_constant__ ProdSet 
     }
 }
 
+// --------------------------------------------------------------- DOT, team of eight
+// Sec. 4.1's pull form for rows with at most QDMASK mask entries and little
+// pull work (in a batch of small products: rows whose single mask entry meets
+// a heavy row of A): an eight-lane team per row, four rows per warp.  For each
+// mask entry j the team's lanes stride the column B_*j (row j of B^T); each
+// entry k is found in the sorted row A_i* by a binary search in global memory
+// (the row is read through L1 by all eight lanes; nothing is staged), and the
+// products a_ik b_kj are summed per lane, then over the team by shuffles.
+template <int SR>
+__global__ void __launch_bounds__(256) k_rows_dq(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
+    using S = Sr<SR>;
+    using acc_t = typename S::acc_t;
+    using out_t = typename S::out_t;
+    const int lane = lane_id(), g = lane >> 3, tl = lane & 7;
+    const unsigned tmask = 0xffu << (8 * g);   // the team's lanes
+    const int count = L.ra.kind_count[K_DOT_Q];
+    const int off = L.ra.kind_off[K_DOT_Q];
+    for (;;) {
+        int x = 0;
+        if (lane == 0) x = atomicAdd(&L.ra.kind_next[K_DOT_Q], 4);
+        x = __shfl_sync(FULL, x, 0);
+        if (x >= count) break;   // uniform over the warp
+        const int xr = x + g;
+        const bool have = xr < count;
+        const long long r = have ? (long long)L.ra.perm[off + xr] : 0;
+        const DevProd &P = prod_at(ps, have ? row_prod(ps, L.ra.prod, r) : 0);
+        int a0 = 0, a1 = 0, m0 = 0, mnz = 0;
+        long long tmp = 0;
+        if (have) {
+            const long long i = r - P.row0;
+            a0 = __ldg(P.a_rp + i);
+            a1 = __ldg(P.a_rp + i + 1);
+            m0 = __ldg(P.m_rp + i);
+            mnz = __ldg(P.m_rp + i + 1) - m0;
+            tmp = L.ra.tmpoff[r];
+        }
+        // mask entry w sits in slot w / 8 of lane w % 8 (up to QDMASK entries)
+        int mv[QDMASK / QTEAM];
+        acc_t v[QDMASK / QTEAM];
+        unsigned setm = 0;   // bit s: this lane's slot s is SET
+#pragma unroll
+        for (int sl = 0; sl < QDMASK / QTEAM; ++sl) {
+            const int w = sl * QTEAM + tl;
+            mv[sl] = w < mnz ? __ldg(P.m_ci + m0 + w) : -1;
+            v[sl] = 0;
+        }
+        for (int w = 0; w < mnz; ++w) {   // uniform over the team
+            int jm = mv[0];
+#pragma unroll
+            for (int sl = 1; sl < QDMASK / QTEAM; ++sl)
+                if ((w >> 3) == sl) jm = mv[sl];
+            const int j = __shfl_sync(tmask, jm, (g << 3) + (w & 7));
+            const int s = __ldg(P.bt_rp + j), e = __ldg(P.bt_rp + j + 1);
+            acc_t part = 0;
+            bool hit = false;
+            for (int q = s + tl; q < e; q += QTEAM) {
+                const int k = __ldg(P.bt_ci + q);
+                int lo = a0, hi = a1;   // first entry of A_i* with column >= k
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (__ldg(P.a_ci + mid) < k) lo = mid + 1; else hi = mid;
+                }
+                if (lo < a1 && __ldg(P.a_ci + lo) == k) {
+                    part += S::mul(load_val<SR>(P.a_v, lo), load_val<SR>(P.bt_v, q));
+                    hit = true;
+                }
+            }
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) part += shfl_xor_acc<SR>(tmask, part, o);
+            const bool any = (__ballot_sync(tmask, hit) & tmask) != 0;
+            if (tl == (w & 7)) {
+#pragma unroll
+                for (int sl = 0; sl < QDMASK / QTEAM; ++sl)
+                    if ((w >> 3) == sl) {
+                        v[sl] = part;
+                        if (any) setm |= 1u << sl;
+                    }
+            }
+        }
+        // SET entries in mask order: slot by slot, the team's lanes in order
+        const TmpOut T = out_of(P, L);
+        out_t *tv = static_cast<out_t *>(T.v);
+        int base = 0;
+#pragma unroll
+        for (int sl = 0; sl < QDMASK / QTEAM; ++sl) {
+            const bool keep = have && ((setm >> sl) & 1u);
+            const unsigned bal = (__ballot_sync(FULL, keep) >> (8 * g)) & 0xffu;
+            if (keep) {
+                if (L.aligned) {
+                    tv[tmp + sl * QTEAM + tl] = S::out(v[sl]);
+                } else if (!L.count_only) {
+                    const long long o = tmp + base + __popc(bal & ((1u << tl) - 1u));
+                    T.ci[o] = mv[sl];
+                    tv[o] = S::out(v[sl]);
+                }
+            }
+            base += __popc(bal);
+        }
+        if (have && tl == 0) L.ra.cnt[r] = base;
+    }
+}
+
 template <int SR, int KIND>
 __global__ void __launch_bounds__(256, 4) k_rows_b(const __grid_constant__ ProdSet ps, const __grid_constant__ RowLaunch L) {
     extern __shared__ __align__(16) unsigned char smem[];

@@ -65,6 +65,7 @@ cudaError_t MSG_CAT(launch_kind_, MSG_SUFFIX)(int kind, const ProdSet &ps, const
     case K_HEAPDOT_W: return go<k_rows_w<MSG_SR, K_HEAPDOT_W>>(ps, L, th, sm, st, nsm);
     case K_CHEAP_W: return go<k_rows_w<MSG_SR, K_CHEAP_W>>(ps, L, th, sm, st, nsm);
     case K_MCA_Q: return go<k_rows_q<MSG_SR>>(ps, L, th, sm, st, nsm);
+    case K_DOT_Q: return go<k_rows_dq<MSG_SR>>(ps, L, th, sm, st, nsm);
     case K_HASH_B: return go<k_rows_b<MSG_SR, K_HASH_B>>(ps, L, th, sm, st, nsm);
     case K_MCA_B: return go<k_rows_b<MSG_SR, K_MCA_B>>(ps, L, th, sm, st, nsm);
     case K_DOT_B: return go<k_rows_b<MSG_SR, K_DOT_B>>(ps, L, th, sm, st, nsm);

@@ -401,3 +401,39 @@ def test_team_of_eight_gradient_form(handle):
         handle.set_option(_lib.OPT_DOT, 1)
     assert np.all(np.abs(dA.cpu().numpy().astype(np.float64) - dA_ref) <= 1e-5 * SA + 1e-30)
     assert np.all(np.abs(dB.cpu().numpy().astype(np.float64) - dB_ref) <= 1e-5 * SB + 1e-30)
+
+
+@pytest.mark.parametrize("semiring", SEMIRINGS)
+@pytest.mark.parametrize("qflops", [0, 1024, 1 << 20])
+def test_team_of_eight_dot(handle, semiring, qflops):
+    """Pull rows (Sec. 4.1) with at most 8 mask entries and at most
+    MSGEMM_OPT_QTEAM_FLOPS pull pairs run on an eight-lane team that
+    binary-searches A_i* in global memory.  Mask rows of 0 to 36 entries (the
+    longer ones take the warp kinds), A rows up to ~200 entries (so pull is cheaper
+    than push), forced pull and AUTO, one and two phases, against the oracle."""
+    rng = np.random.default_rng(88)
+    m, k, n = 800, 900, 3000
+    mdeg = np.arange(m) % 37
+    rows, cols = [], []
+    for i in range(m):
+        c = np.sort(rng.choice(n, size=int(mdeg[i]), replace=False))
+        rows.append(np.full(len(c), i))
+        cols.append(c)
+    M = synth.coo_to_csr(m, n, np.concatenate(rows).astype(np.int32), np.concatenate(cols).astype(np.int32))
+    q = synth.random_problem(m, k, n, 60.0, 20.0, 1.0, 89, GEN[semiring])
+    q["M"] = M
+    ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring)
+    handle.set_option(_lib.OPT_QTEAM_FLOPS, qflops)
+    try:
+        for force in ("dot", "auto"):
+            for phases in (1, 2):
+                handle.set_option(_lib.OPT_PHASES, phases)
+                res = run(handle, q, semiring, False, force)
+                assert_parity(res, ref, semiring, ctx=f"q={qflops} force={force} phases={phases}")
+                nq = handle.bin_counts()["dot_q"]
+                if force == "dot":
+                    assert (nq > 0) == (qflops > 0), nq
+    finally:
+        handle.set_option(_lib.OPT_PHASES, 1)
+        handle.set_option(_lib.OPT_QTEAM_FLOPS, 1024)
+        handle.force("auto")
