@@ -67,6 +67,8 @@ def parse_args(argv=None):
                     help="policy sweeps instead of the benchmark line: Erdos-Renyi n x degrees with every "
                          "accumulator forced vs AUTO, or triangle counting over R-MAT scales")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--batch-products", type=int, default=256,
+                    help="products of the batched workload (256; fewer for a small profiling case)")
     ap.add_argument("--sweep-out", default=None, help="write the sweep's table (with the kernel source hash) "
                                                        "to this JSON file")
     ap.add_argument("--sweep-max-log2", type=int, default=22, help="largest n = 2^x of the Erdos-Renyi sweep")
@@ -250,7 +252,7 @@ class Workload:
         self.nnz_c = None
 
 
-def build_workload(name, scale, seed):
+def build_workload(name, scale, seed, nprod=256):
     from paper_2111_09947_gb300 import synth
     if name == "tc":
         scale = scale or 20
@@ -274,8 +276,8 @@ def build_workload(name, scale, seed):
                "nnz_visited": b["M"].nnz, "nnz_A": b["B"].nnz}
         return Workload(name, "plus_times_i64", cfg, [(b["M"], b["A"], b["B"], True)], "int64")
     if name == "batched":
-        ps = synth.batched_problems(nprod=256, seed=seed)
-        cfg = {"workload": "256 independent fp32 products in one call: n log-uniform in [2^10, 2^16], A/B R-MAT "
+        ps = synth.batched_problems(nprod=nprod, seed=seed)
+        cfg = {"workload": f"{nprod} independent fp32 products in one call: n log-uniform in [2^10, 2^16], A/B R-MAT "
                            "ef 8, M Erdos-Renyi with {1,16,256} entries per row",
                "rows": int(sum(p["n"] for p in ps)), "nnz_M": int(sum(p["M"].nnz for p in ps))}
         return Workload(name, "plus_times_f32", cfg, [(p["M"], p["A"], p["B"], False) for p in ps], "f32")
@@ -728,7 +730,7 @@ def run_ours(args):
 
     log(f"generating {args.workload} workload")
     t_gen = time.perf_counter()
-    wl = build_workload(args.workload, args.scale, seed)
+    wl = build_workload(args.workload, args.scale, seed, args.batch_products)
     sharding = None
     if sharded:
         from paper_2111_09947_gb300 import shard
@@ -881,7 +883,7 @@ def run_reference(args):
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
     from paper_2111_09947_gb300 import synth
     name = args.workload if args.workload in ("tc", "er", "bfs", "autograd") else "tc"
-    wl = build_workload(name, args.scale, synth.BASE_SEED)
+    wl = build_workload(name, args.scale, synth.BASE_SEED, args.batch_products)
     M, A, B, comp = wl.mats[0]
     per_step = max(0.5, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     nrows, fixed, per_row = oracle_plan(M, A, B, wl.semiring, comp, per_step, rng_seed=11)
