@@ -1464,6 +1464,13 @@ __device__ __forceinline__ bool grid_safe(typename Sr<SR>::acc_t v) {
     else return true;                                              // plus-pair: counts >= 1
 }
 
+// Position of tile column jj in the grid kinds' value arrays: its low five
+// bits XORed with the next five, a permutation within every 32-column group
+// (tile widths are multiples of 32).  A warp walking a sorted row of B meets
+// columns at near-regular spacing, and spacings that share factors with 32
+// put many lanes on few shared-memory banks; the swizzle spreads them.
+__device__ __forceinline__ int vswz(int jj) { return jj ^ ((jj >> 5) & 31); }
+
 template <int SR, bool COMP>
 struct GridIns {
     using S = Sr<SR>;
@@ -1490,10 +1497,10 @@ struct GridIns {
             const typename S::acc_t v = S::mul(a, b);
             if constexpr (TA::split) {
                 const unsigned l = (unsigned)v;
-                const unsigned old = atomicAdd(&vals[jj], l);
+                const unsigned old = atomicAdd(&vals[vswz(jj)], l);
                 if (!grid_safe<SR>(v) || old + l < old) *unsafe = 1;
             } else {
-                TA::add(vals, hi, jj, v);
+                TA::add(vals, hi, vswz(jj), v);
                 if (!grid_safe<SR>(v)) *unsafe = 1;
             }
             return;
@@ -1502,15 +1509,15 @@ struct GridIns {
         if ((w & 1u) != (COMP ? 1u : 0u)) {
             const typename S::acc_t v = S::mul(a, b);
             if (track) {
-                TA::add(vals, hi, jj, v);
+                TA::add(vals, hi, vswz(jj), v);
                 if (!(w & 2u)) atomicOr(&st[jj >> 4], 2u << (2 * (jj & 15)));
             } else if constexpr (TA::split) {
                 // int64: the low word only; a carry would need the high word
                 const unsigned l = (unsigned)v;
-                const unsigned old = atomicAdd(&vals[jj], l);
+                const unsigned old = atomicAdd(&vals[vswz(jj)], l);
                 if (!grid_safe<SR>(v) || old + l < old) *unsafe = 1;
             } else {
-                TA::add(vals, hi, jj, v);
+                TA::add(vals, hi, vswz(jj), v);
                 if (!grid_safe<SR>(v)) *unsafe = 1;
             }
         }
@@ -1562,8 +1569,9 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
         cta_sync();
         if (tracked || *s_unsafe == 0) break;   // uniform over the CTA
         if (threadIdx.x == 0) *(volatile int *)L.spec_off = 1;
-        // clear the tile's values (low and high words) and run again with SET bits
-        for (int x = team.tid(); x < c1 - c0; x += team.size()) {
+        // clear the tile's values (low and high words) and run again with SET
+        // bits; swizzled positions stay inside the last 32-column group
+        for (int x = team.tid(); x < min(T, ((c1 - c0) + 31) & ~31); x += team.size()) {
             vals[x] = 0;
             if constexpr (TA::split) hi[x] = 0;
         }
@@ -1579,7 +1587,7 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
         unsigned m = 0;
         const int cend = min(16, (c1 - c0) - 16 * w);
         for (int b = 0; b < cend; ++b)
-            if (vals[16 * w + b] != 0) m |= 1u << (2 * b);
+            if (vals[vswz(16 * w + b)] != 0) m |= 1u << (2 * b);
         return m;
     };
     auto set_bits = [&](int w) -> unsigned {   // bit 2b set for SET column 16 w + b
@@ -1604,10 +1612,10 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
             const int jj = w * 16 + (b >> 1);
             out_t v;
             if (tracked) {
-                v = S::out(TA::take(vals, hi, jj));
+                v = S::out(TA::take(vals, hi, vswz(jj)));
             } else {   // no carry reached the high word: the low word is the value
-                v = S::out((typename S::acc_t)vals[jj]);
-                vals[jj] = 0;
+                v = S::out((typename S::acc_t)vals[vswz(jj)]);
+                vals[vswz(jj)] = 0;
             }
             if (!COMP && L.aligned) {
                 // the column's rank in the mask row (SET columns are mask columns)
@@ -1628,7 +1636,7 @@ __device__ __forceinline__ int grid_tile(const DevProd &P, const RowCtx &c, cons
             while (d) {
                 const int b = __ffs(d) - 1;
                 d &= d - 1;
-                vals[w * 16 + (b >> 1)] = 0;
+                vals[vswz(w * 16 + (b >> 1))] = 0;
             }
         }
         st[w] = 0;
