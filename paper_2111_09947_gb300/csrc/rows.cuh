@@ -47,6 +47,7 @@ struct RowLaunch {
     int count_only;
     int direct;
     int hash_kicks;    // HASH kinds: moves allowed per cuckoo insertion; 0 = linear probing
+    int md_ratio;      // HASH kinds: mask-driven ranges when a * md_ratio < |B_k*| (0 = never)
 };
 
 // Where a row's entries go: the shared temporary output, or (two-phase
@@ -161,9 +162,72 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
 constexpr int BIG_SEG = 2048;
 constexpr int BIG_LIST = 128;
 
-template <int SR, bool CTA, bool OUTV, bool WSYNC = false, class Seg, class F>
+// Mask-driven ranges (plain masks, Sec. 4.3's choice between pushing a row of
+// B through the accumulator and pulling the mask's columns, made per (i, k)):
+// for a long range B_k* [s, e) whose column span holds few entries of the
+// sorted mask row m (a = entries of m in [first(B_k*), last(B_k*)], with
+// a * ratio < e - s), the warp binary-searches each of those a mask columns
+// in B_k* instead of walking all e - s entries; each found column is one
+// product, handed to f like a walked one.  Off unless a kind passes one.
+struct NoMaskDrive {
+    static constexpr bool on = false;
+};
+struct MaskDrive {
+    static constexpr bool on = true;
+    const int *m;   // the sorted mask row
+    int mnz;
+    int ratio;      // mask-driven when a * ratio < e - s
+};
+
+// lower_bound of x in the sorted m[0..n) (global memory)
+__device__ __forceinline__ int lower_bound_g(const int *m, int n, int x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(m + mid) < x) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Tries range [s, e) of the inner CSR mask-driven; returns false (nothing
+// done) when walking it is cheaper.  Warp-uniform arguments.
+template <int SR, bool WSYNC, class F>
+__device__ __forceinline__ bool mask_driven(const MaskDrive &md, int t, typename Sr<SR>::in_t a, int s, int e,
+                                            const int *__restrict__ ici, const void *iv, F &f) {
+    using in_t = typename Sr<SR>::in_t;
+    const int lane = lane_id();
+    int pos = 0;
+    if (lane < 2) {   // lane 0: first mask entry >= first(B_k*); lane 1: first > last(B_k*)
+        const int key = lane ? __ldg(ici + e - 1) + 1 : __ldg(ici + s);
+        pos = lower_bound_g(md.m, md.mnz, key);
+    }
+    const int lo = __shfl_sync(FULL, pos, 0), hi = __shfl_sync(FULL, pos, 1);
+    if ((long long)(hi - lo) * md.ratio >= (long long)(e - s)) return false;
+    for (int q0 = lo; q0 < hi; q0 += 32) {
+        const int q = q0 + lane;
+        int j = -1;
+        in_t bv{};
+        if (q < hi) {
+            const int x = __ldg(md.m + q);
+            int l = s, r = e;   // first entry of B_k* with column >= x
+            while (l < r) {
+                const int mid = (l + r) >> 1;
+                if (__ldg(ici + mid) < x) l = mid + 1; else r = mid;
+            }
+            if (l < e && __ldg(ici + l) == x) {
+                j = x;
+                bv = load_val<SR>(iv, l);
+            }
+        }
+        if (WSYNC || j >= 0) f(t, a, j, bv);
+    }
+    return true;
+}
+
+template <int SR, bool CTA, bool OUTV, bool WSYNC = false, class Seg, class F, class MD = NoMaskDrive>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
-                                              const Seg &seg, const int *__restrict__ ici, const void *iv, F &f) {
+                                              const Seg &seg, const int *__restrict__ ici, const void *iv, F &f,
+                                              const MD &md = MD{}) {
     using in_t = typename Sr<SR>::in_t;
     Team<CTA> team;
     const int lane = lane_id();
@@ -206,6 +270,9 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             lmask &= lmask - 1;
             const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
             const in_t au = shfl_val<SR>(av, u);
+            if constexpr (MD::on) {
+                if (mask_driven<SR, WSYNC>(md, tbase + nw * u, au, su, eu, ici, iv, f)) continue;
+            }
             walk_range<SR, WSYNC>(tbase + nw * u, au, su, eu, 0, 1, ici, iv, f);
         }
         // short ranges: load-balanced flat enumeration, two products per lane
@@ -483,7 +550,11 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
             const bool f1 = ok & ((k1 & KMASK) == x), f2 = ok & ((k2 & KMASK) == x);
             if (f1 | f2) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
         };
-        enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+        if (L.md_ratio > 0)
+            enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins,
+                                               MaskDrive{mcols, mnz, L.md_ratio});
+        else
+            enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     } else {
         auto ins = [&](int, in_t a, int j, in_t b) {
             unsigned h = ch.h1((unsigned)j);

@@ -148,6 +148,7 @@ def test_autotune_keeps_parity_and_writes_cache(batch, tmp_path):
     e = d[key]
     assert len(e["pref"]) == 16 and all(len(r) == 4 for r in e["pref"])
     assert e["warp_flops_max"] > 0 and e["dot_ratio"] > 0
+    assert e["q_flops_max"] >= 0 and e["md_ratio"] >= 0
 
 
 def test_autotune_reads_cache(batch, tmp_path):
@@ -168,4 +169,25 @@ def test_autotune_reads_cache(batch, tmp_path):
     finally:
         h.close()
     assert counts["hash_w"] == 0 and counts["hash_b"] == 0 and counts["msa_w"] == 0
-    assert counts["mca_w"] + counts["mca_b"] > 0
+    assert counts["mca_w"] + counts["mca_b"] + counts["mca_q"] > 0
+
+
+def test_autotune_cache_trailing_fields(batch, tmp_path):
+    """A cached entry's team flop bound and mask-driven ratio are applied: with
+    the bound at 0 no row takes the eight-lane kinds."""
+    ps, devs, refs = batch
+    key = torch.cuda.get_device_name() + "|plus_times_f32"
+    entry = {"warp_flops_max": 65536, "dot_ratio": 2, "warp_slab": 4608, "grid_min_flops": 1 << 20,
+             "pref": [[3, 2, 1, 0]] * 16, "q_flops_max": 0, "md_ratio": 0}
+    cache = tmp_path / "tune.json"
+    cache.write_text(json.dumps({key: entry}))
+    h = _lib.Handle()
+    try:
+        _lib.msgemm_autotune(h, [], [], [], "plus_times_f32", cache_path=cache)
+        outs = _run(h, devs, False)
+        counts = h.bin_counts()
+        for o, ref in zip(outs, refs):
+            assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+    assert counts["mca_q"] == 0 and counts["dot_q"] == 0
