@@ -124,17 +124,11 @@ typedef enum {
                                      falls back to linear probing.  0 = linear probing only.
                                      The result never depends on it (tests use 0 and 1 to run
                                      every build path). */
-    MSGEMM_OPT_QTEAM_FLOPS = 11,  /* value 0..2^20 (default 1024): plain rows with at most 8 mask
+    MSGEMM_OPT_QTEAM_FLOPS = 11   /* value 0..2^20 (default 1024): plain rows with at most 8 mask
                                      entries and at most this many push products take the
                                      mask-compressed accumulator (Sec. 5.4) on a team of eight
                                      lanes (four rows per warp, the mask row and its accumulators
                                      in registers) -- under AUTO and when MCA is forced; 0 = never */
-    MSGEMM_OPT_MASK_DRIVEN = 12   /* value 0..4096 (default 8): in the hash rows (Sec. 5.3), a row
-                                     B_k* of at least 64 entries whose column span holds a entries
-                                     of the mask row with a * value < nnz(B_k*) is not walked: each
-                                     of those a mask columns is binary-searched in B_k* instead
-                                     (the push/pull choice of Sec. 4.3 made per (i, k)).  The
-                                     result never depends on it; 0 = always walk */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
     __shared__ int hsub[NKIND * NCLS_FLOPS];
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
     for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x) hsub[x] = 0;
-    __syncthreads();
+    block_sync();
     const int lane = lane_id();
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
@@ -267,7 +267,7 @@ __global__ void __launch_bounds__(256, 4) k_bin_score(const __grid_constant__ Pr
         }
         if (valid && !is_huge) finish_row<SR>(P, ra, pol, room, hist, hsub, r, a0, a1, m0, m1, dot_ok, f, pull);
     }
-    __syncthreads();
+    block_sync();
     flush_hist(ra, hist, hsub);
 }
 
@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
     __shared__ long long s_f;
     for (int x = threadIdx.x; x < NKIND; x += blockDim.x) hist[x] = 0;
     for (int x = threadIdx.x; x < NKIND * NCLS_FLOPS; x += blockDim.x) hsub[x] = 0;
-    __syncthreads();
+    block_sync();
     const int nlong = *ra.nlong;
     const int w = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     for (int x = blockIdx.x; x < nlong; x += gridDim.x) {
@@ -302,13 +302,13 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
         share(a0, a1, s0, s1);
         const long long f = warp_len_sum(P.a_ci, P.b_rp, s0, s1);
         if (lane_id() == 0) part[0][w] = f;
-        __syncthreads();
+        block_sync();
         if (threadIdx.x == 0) {
             long long ft = 0;
             for (int q = 0; q < nwarp; ++q) ft += part[0][q];
             s_f = ft;
         }
-        __syncthreads();
+        block_sync();
         const long long ft = s_f;
         long long pull = 0;
         if (dot_ok) {   // a warp whose share alone decides against pull stops early
@@ -316,15 +316,15 @@ __global__ void __launch_bounds__(256) k_bin_long(const __grid_constant__ ProdSe
             pull = warp_len_sum_until(P.m_ci, P.bt_rp, s0, s1, pol.dot_ratio, ft);
         }
         if (lane_id() == 0) part[1][w] = pull;
-        __syncthreads();
+        block_sync();
         if (threadIdx.x == 0) {
             long long pt = 0;
             for (int q = 0; q < nwarp; ++q) pt += part[1][q];
             finish_row<SR>(P, ra, pol, room, hist, hsub, r, a0, a1, m0, m1, dot_ok, ft, pt);
         }
-        __syncthreads();
+        block_sync();
     }
-    __syncthreads();
+    block_sync();
     flush_hist(ra, hist, hsub);
 }
 

@@ -39,7 +39,6 @@ struct msgemm_handle {
     int force = 0, validate = 0, allow_dot = 1, tile_index = 1, grid = 1;
     int phases = 1;   // 1: one-phase, 2: symbolic + numeric (MSGEMM_OPT_PHASES)
     int hash_kicks = CUCKOO_KICKS;   // MSGEMM_OPT_HASH_KICKS
-    int md_ratio = 8;                // MSGEMM_OPT_MASK_DRIVEN
     long long tile_index_budget = 4LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
@@ -461,7 +460,6 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     // products left without one walk their tiles with per-entry cursors
     pl.L.aligned = pl.aligned ? 1 : 0;
     pl.L.hash_kicks = h->hash_kicks;
-    pl.L.md_ratio = h->md_ratio;
     pl.nts.assign(P, 0);
     pl.tpos.assign(P, nullptr);
     if (any_tiled) {
@@ -955,7 +953,6 @@ struct Tuned {
     long long grid_min_flops = 1LL << 20;
     unsigned char pref[NCLASS][4];
     int q_flops_max = 1024;
-    int md_ratio = 8;
 };
 
 Tuned current_tuned(const msgemm_handle *h) {
@@ -966,7 +963,6 @@ Tuned current_tuned(const msgemm_handle *h) {
     t.grid_min_flops = h->grid_min_flops;
     memcpy(t.pref, h->pref, sizeof t.pref);
     t.q_flops_max = h->q_flops_max;
-    t.md_ratio = h->md_ratio;
     return t;
 }
 
@@ -977,15 +973,13 @@ void apply_tuned(msgemm_handle *h, const Tuned &t) {
     h->grid_min_flops = t.grid_min_flops;
     memcpy(h->pref, t.pref, sizeof t.pref);
     h->q_flops_max = t.q_flops_max;
-    h->md_ratio = t.md_ratio;
 }
 
 // Cache file: a JSON object, one entry per line,
 //   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "grid_min_flops": G,
-//                                "pref": [[f,f,f,f], ...], "q_flops_max": Q, "md_ratio": R}
+//                                "pref": [[f,f,f,f], ...], "q_flops_max": Q}
 // with NCLASS preference rows of accumulator families (msgemm_accumulator);
-// an entry without the trailing fields (written before they existed) keeps
-// their defaults.
+// an entry without q_flops_max (written before it existed) keeps its default.
 void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
     FILE *f = fopen(path, "r");
     if (!f) return;
@@ -1006,7 +1000,7 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ++c;
             }
         }
-        if (num.size() < 4 + NCLASS * 4 || num.size() > 6 + NCLASS * 4) continue;
+        if (num.size() != 4 + NCLASS * 4 && num.size() != 5 + NCLASS * 4) continue;
         Tuned t;
         if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
         if (num[2] < 1024 || num[2] > 24576 || (int)num[2] % 16) continue;
@@ -1022,15 +1016,10 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ok &= v >= F_AUTO && v <= F_HEAPDOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
-        if (num.size() >= 5 + NCLASS * 4) {
+        if (num.size() == 5 + NCLASS * 4) {
             const double q = num[4 + NCLASS * 4];
             ok &= q >= 0 && q <= (1 << 20) && q == (int)q;
             t.q_flops_max = (int)q;
-        }
-        if (num.size() == 6 + NCLASS * 4) {
-            const double r = num[5 + NCLASS * 4];
-            ok &= r >= 0 && r <= 4096 && r == (int)r;
-            t.md_ratio = (int)r;
         }
         if (ok) out[key] = t;
     }
@@ -1049,8 +1038,7 @@ bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
                 kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab, t.grid_min_flops);
         for (int c = 0; c < NCLASS; ++c)
             fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
-        fprintf(f, "], \"q_flops_max\": %d, \"md_ratio\": %d}%s\n", t.q_flops_max, t.md_ratio,
-                ++i < m.size() ? "," : "");
+        fprintf(f, "], \"q_flops_max\": %d}%s\n", t.q_flops_max, ++i < m.size() ? "," : "");
     }
     fprintf(f, "}\n");
     const bool ok = fclose(f) == 0;
@@ -1191,16 +1179,6 @@ struct Tuner {
             if (t < best * keep) { best = t; qbest = q; }
         }
         h->q_flops_max = qbest;
-        const int mbest0 = h->md_ratio;
-        int mbest = mbest0;
-        for (int r : {0, 2, 4, 8, 16, 32}) {
-            if (r == mbest0) continue;
-            h->md_ratio = r;
-            float t;
-            CKS(measure(&t));
-            if (t < best * keep) { best = t; mbest = r; }
-        }
-        h->md_ratio = mbest;
         const int sbest0 = h->warp_slab;
         int sbest = sbest0;
         for (int sl : {3072, 3584, 4096, 4608, 6144, 9216}) {
@@ -1313,10 +1291,6 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_QTEAM_FLOPS:
         if (value < 0 || value > (1 << 20)) return fail(h, MSGEMM_ERR_INVALID, "team-of-eight flop bound is 0..2^20");
         h->q_flops_max = (int)value;
-        return MSGEMM_OK;
-    case MSGEMM_OPT_MASK_DRIVEN:
-        if (value < 0 || value > 4096) return fail(h, MSGEMM_ERR_INVALID, "mask-driven ratio is 0..4096");
-        h->md_ratio = (int)value;
         return MSGEMM_OK;
     case MSGEMM_OPT_HASH_KICKS:
         if (value < 0 || value > 4096) return fail(h, MSGEMM_ERR_INVALID, "hash kicks is 0..4096");

@@ -383,6 +383,27 @@ __host__ __device__ __forceinline__ int msa_tile_width(long long slab, int acc) 
     return t > 0 ? (int)t : 0;
 }
 
+// ------------------------------------------------------------------ barriers
+// Block barrier after divergent work: lanes leave data-dependent loops (a
+// probe chain inside a product callback, a per-lane range walk) at different
+// times, so each warp first reconverges (__syncwarp) and then meets the
+// other warps.
+__device__ __forceinline__ void block_sync() {
+    __syncwarp();
+    __syncthreads();
+}
+
+// Read of a shared-memory word that other threads of the team set with
+// atomics before the last team barrier, as a volatile load: the compiler
+// neither reuses an earlier read of the word nor moves the read.  With plain
+// loads, the linear-probe lookups of CTA hash rows missed keys that the build
+// had inserted before the barrier: now and then at first, and in every run
+// once the team barrier reconverged the warp first; with volatile loads none
+// did.
+template <class T> __device__ __forceinline__ T ld_vol(const T *p) {
+    return *static_cast<const volatile T *>(p);
+}
+
 // ------------------------------------------------------------------ teams
 // A team cooperates on one row: one warp (_W kinds) or the whole CTA.
 template <bool CTA> struct Team {
@@ -391,13 +412,18 @@ template <bool CTA> struct Team {
     __device__ __forceinline__ int warp() const { return CTA ? (int)(threadIdx.x >> 5) : 0; }
     __device__ __forceinline__ int nwarps() const { return CTA ? (int)(blockDim.x >> 5) : 1; }
     // Barrier that also publishes the team's shared-memory atomics (hash
-    // keys, bitmaps, accumulators) to the plain loads that follow it.  An
-    // explicit block-scope fence before the barrier is required: without it a
-    // lookup after the barrier was seen to miss a key another warp had just
-    // inserted with atomicCAS.
+    // keys, bitmaps, accumulators) to the plain loads that follow it: the
+    // warp reconverges, fences its shared-memory writes, then meets the
+    // other warps (block_sync).
     __device__ __forceinline__ void sync() const {
-        __threadfence_block();
-        if (CTA) __syncthreads(); else __syncwarp();
+        if (CTA) {
+            __syncwarp();
+            __threadfence_block();
+            __syncthreads();
+        } else {
+            __threadfence_block();
+            __syncwarp();
+        }
     }
 };
 
@@ -422,6 +448,7 @@ __device__ __forceinline__ void stage_async(void *dst, const void *src, int n) {
 __device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ void cta_sync() {
+    __syncwarp();
     __threadfence_block();
     __syncthreads();
 }
@@ -451,17 +478,17 @@ __device__ __forceinline__ int block_excl_scan(int v, int *scratch, int *total) 
     const int lane = lane_id(), w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     int incl = warp_incl_scan(v);
     if (lane == 31) scratch[w] = incl;
-    __syncthreads();
+    block_sync();
     if (w == 0) {
         int x = lane < nw ? scratch[lane] : 0;
         int xi = warp_incl_scan(x);
         if (lane < nw) scratch[lane] = xi - x;
         if (lane == 31) scratch[32] = xi;
     }
-    __syncthreads();
+    block_sync();
     int res = scratch[w] + incl - v;
     *total = scratch[32];
-    __syncthreads();
+    block_sync();
     return res;
 }
 

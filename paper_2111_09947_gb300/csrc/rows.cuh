@@ -47,7 +47,6 @@ struct RowLaunch {
     int count_only;
     int direct;
     int hash_kicks;    // HASH kinds: moves allowed per cuckoo insertion; 0 = linear probing
-    int md_ratio;      // HASH kinds: mask-driven ranges when a * md_ratio < |B_k*| (0 = never)
 };
 
 // Where a row's entries go: the shared temporary output, or (two-phase
@@ -162,72 +161,9 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
 constexpr int BIG_SEG = 2048;
 constexpr int BIG_LIST = 128;
 
-// Mask-driven ranges (plain masks, Sec. 4.3's choice between pushing a row of
-// B through the accumulator and pulling the mask's columns, made per (i, k)):
-// for a long range B_k* [s, e) whose column span holds few entries of the
-// sorted mask row m (a = entries of m in [first(B_k*), last(B_k*)], with
-// a * ratio < e - s), the warp binary-searches each of those a mask columns
-// in B_k* instead of walking all e - s entries; each found column is one
-// product, handed to f like a walked one.  Off unless a kind passes one.
-struct NoMaskDrive {
-    static constexpr bool on = false;
-};
-struct MaskDrive {
-    static constexpr bool on = true;
-    const int *m;   // the sorted mask row
-    int mnz;
-    int ratio;      // mask-driven when a * ratio < e - s
-};
-
-// lower_bound of x in the sorted m[0..n) (global memory)
-__device__ __forceinline__ int lower_bound_g(const int *m, int n, int x) {
-    int lo = 0, hi = n;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(m + mid) < x) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
-
-// Tries range [s, e) of the inner CSR mask-driven; returns false (nothing
-// done) when walking it is cheaper.  Warp-uniform arguments.
-template <int SR, bool WSYNC, class F>
-__device__ __forceinline__ bool mask_driven(const MaskDrive &md, int t, typename Sr<SR>::in_t a, int s, int e,
-                                            const int *__restrict__ ici, const void *iv, F &f) {
-    using in_t = typename Sr<SR>::in_t;
-    const int lane = lane_id();
-    int pos = 0;
-    if (lane < 2) {   // lane 0: first mask entry >= first(B_k*); lane 1: first > last(B_k*)
-        const int key = lane ? __ldg(ici + e - 1) + 1 : __ldg(ici + s);
-        pos = lower_bound_g(md.m, md.mnz, key);
-    }
-    const int lo = __shfl_sync(FULL, pos, 0), hi = __shfl_sync(FULL, pos, 1);
-    if ((long long)(hi - lo) * md.ratio >= (long long)(e - s)) return false;
-    for (int q0 = lo; q0 < hi; q0 += 32) {
-        const int q = q0 + lane;
-        int j = -1;
-        in_t bv{};
-        if (q < hi) {
-            const int x = __ldg(md.m + q);
-            int l = s, r = e;   // first entry of B_k* with column >= x
-            while (l < r) {
-                const int mid = (l + r) >> 1;
-                if (__ldg(ici + mid) < x) l = mid + 1; else r = mid;
-            }
-            if (l < e && __ldg(ici + l) == x) {
-                j = x;
-                bv = load_val<SR>(iv, l);
-            }
-        }
-        if (WSYNC || j >= 0) f(t, a, j, bv);
-    }
-    return true;
-}
-
-template <int SR, bool CTA, bool OUTV, bool WSYNC = false, class Seg, class F, class MD = NoMaskDrive>
+template <int SR, bool CTA, bool OUTV, bool WSYNC = false, class Seg, class F>
 __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restrict__ oci, const void *ov,
-                                              const Seg &seg, const int *__restrict__ ici, const void *iv, F &f,
-                                              const MD &md = MD{}) {
+                                              const Seg &seg, const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
     Team<CTA> team;
     const int lane = lane_id();
@@ -238,7 +174,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
     __shared__ in_t s_biga[CTA ? BIG_LIST : 1];
     if constexpr (CTA) {
         if (threadIdx.x == 0) s_nbig = 0;
-        __syncthreads();
+        block_sync();
     }
     for (int b0 = 0; wq + nw * b0 < cnt; b0 += 32) {
         const int t = o0 + wq + nw * (b0 + lane);
@@ -270,9 +206,6 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             lmask &= lmask - 1;
             const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
             const in_t au = shfl_val<SR>(av, u);
-            if constexpr (MD::on) {
-                if (mask_driven<SR, WSYNC>(md, tbase + nw * u, au, su, eu, ici, iv, f)) continue;
-            }
             walk_range<SR, WSYNC>(tbase + nw * u, au, su, eu, 0, 1, ici, iv, f);
         }
         // short ranges: load-balanced flat enumeration, two products per lane
@@ -313,7 +246,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
     if constexpr (CTA) {
         // listed ranges: their 128-entry chunks, concatenated, dealt to the
         // warps round-robin
-        __syncthreads();
+        block_sync();
         const int nb = min(s_nbig, BIG_LIST);
         long long g = 0;   // chunks of the ranges before this one
         for (int i = 0; i < nb; ++i) {
@@ -322,7 +255,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             walk_range<SR, WSYNC>(s_big[i][0], s_biga[i], s0, e0, first, nw, ici, iv, f);
             g += (e0 - s0 + 127) / 128;
         }
-        __syncthreads();   // the list is reused by the team's next call
+        block_sync();   // the list is reused by the team's next call
     }
 }
 
@@ -533,9 +466,9 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
         unsigned h, h2;
         ch.pos(x, h, h2);
         if (!linear) {
-            return (key[h] & KMASK) == x ? h : h2;
+            return (ld_vol(&key[h]) & KMASK) == x ? h : h2;
         }
-        while ((key[h] & KMASK) != x) h = h + 1 == H ? 0u : h + 1;
+        while ((ld_vol(&key[h]) & KMASK) != x) h = h + 1 == H ? 0u : h + 1;
         return h;
     };
     if (!linear) {
@@ -545,21 +478,17 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
             const unsigned x = (unsigned)j;
             unsigned p1, p2;
             ch.pos(x, p1, p2);
-            const unsigned k1 = key[p1], k2 = key[p2];
+            const unsigned k1 = ld_vol(&key[p1]), k2 = ld_vol(&key[p2]);
             const bool ok = j >= 0;
             const bool f1 = ok & ((k1 & KMASK) == x), f2 = ok & ((k2 & KMASK) == x);
             if (f1 | f2) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
         };
-        if (L.md_ratio > 0)
-            enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins,
-                                               MaskDrive{mcols, mnz, L.md_ratio});
-        else
-            enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
+        enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
     } else {
         auto ins = [&](int, in_t a, int j, in_t b) {
             unsigned h = ch.h1((unsigned)j);
             for (;;) {   // terminates: at least half of the slots are empty
-                const unsigned kk = key[h];
+                const unsigned kk = ld_vol(&key[h]);
                 if ((kk & KMASK) == (unsigned)j) {
                     hit(h, kk, a, b);
                     return;
@@ -573,9 +502,9 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
     team.sync();
     auto get = [&](int q, acc_t &v) -> bool {
         const unsigned p = slot_of((unsigned)__ldg(mcols + q));
-        v = acc[p];
+        v = ld_vol(&acc[p]);
         if constexpr (Sr<SR>::count_set) return v != 0;
-        else return (key[p] & KEY_SET) != 0;
+        else return (ld_vol(&key[p]) & KEY_SET) != 0;
     };
     gather_by<SR, CTA>(mcols, mnz, get, c.tmp, out_of(P, L), L.ra.cnt + c.r, scratch, L.aligned, !L.count_only);
     team.sync();
@@ -828,11 +757,11 @@ __device__ __forceinline__ void row_chash(const DevProd &P, const RowCtx &c, con
     } else {
         __shared__ int red;
         if (threadIdx.x == 0) red = 0;
-        __syncthreads();
+        block_sync();
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cntl += __shfl_xor_sync(FULL, cntl, o);
         if (lane_id() == 0) atomicAdd(&red, cntl);
-        __syncthreads();
+        block_sync();
         if (threadIdx.x == 0) L.ra.cnt[c.r] = red;
     }
     team.sync();
@@ -1460,9 +1389,9 @@ __global__ void __launch_bounds__(256, 4) k_rows_b(const __grid_constant__ ProdS
     const int off = L.ra.kind_off[KIND];
     // rows from a device counter, heavy rows first (bucket order)
     for (;;) {
-        __syncthreads();
+        block_sync();
         if (threadIdx.x == 0) s_row = atomicAdd(&L.ra.kind_next[KIND], 1);
-        __syncthreads();
+        block_sync();
         const int x = s_row;
         if (x >= count) break;
         const long long r = L.ra.perm[off + x];
@@ -1738,7 +1667,7 @@ __device__ __forceinline__ void grid_pack(const RowCtx &c, const RowLaunch &L, c
                     col = __ldcg(tci + c.tmp + src + q);
                     v = __ldcg(tv + c.tmp + src + q);
                 }
-                __syncthreads();
+                block_sync();
                 if (q < nt) {
                     tci[c.tmp + dst + q] = col;
                     tv[c.tmp + dst + q] = v;

@@ -148,7 +148,7 @@ def test_autotune_keeps_parity_and_writes_cache(batch, tmp_path):
     e = d[key]
     assert len(e["pref"]) == 16 and all(len(r) == 4 for r in e["pref"])
     assert e["warp_flops_max"] > 0 and e["dot_ratio"] > 0
-    assert e["q_flops_max"] >= 0 and e["md_ratio"] >= 0
+    assert e["q_flops_max"] >= 0
 
 
 def test_autotune_reads_cache(batch, tmp_path):
@@ -172,13 +172,13 @@ def test_autotune_reads_cache(batch, tmp_path):
     assert counts["mca_w"] + counts["mca_b"] + counts["mca_q"] > 0
 
 
-def test_autotune_cache_trailing_fields(batch, tmp_path):
-    """A cached entry's team flop bound and mask-driven ratio are applied: with
-    the bound at 0 no row takes the eight-lane kinds."""
+def test_autotune_cache_team_bound(batch, tmp_path):
+    """A cached entry's team flop bound is applied: with the bound at 0 no row
+    takes the eight-lane kinds."""
     ps, devs, refs = batch
     key = torch.cuda.get_device_name() + "|plus_times_f32"
     entry = {"warp_flops_max": 65536, "dot_ratio": 2, "warp_slab": 4608, "grid_min_flops": 1 << 20,
-             "pref": [[3, 2, 1, 0]] * 16, "q_flops_max": 0, "md_ratio": 0}
+             "pref": [[3, 2, 1, 0]] * 16, "q_flops_max": 0}
     cache = tmp_path / "tune.json"
     cache.write_text(json.dumps({key: entry}))
     h = _lib.Handle()

@@ -262,33 +262,18 @@ def test_hash_build_paths(handle, semiring, kicks):
     ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring)
     handle.set_option(_lib.OPT_HASH_KICKS, kicks)
     try:
-        for md in (0, 1, 8):   # mask-driven ranges: never, whenever a < |B_k*|, the default
-            handle.set_option(_lib.OPT_MASK_DRIVEN, md)
-            for phases in (1, 2):
-                handle.set_option(_lib.OPT_PHASES, phases)
+        for phases in (1, 2):
+            handle.set_option(_lib.OPT_PHASES, phases)
+            # repeated: a lookup that reads the table before the build is
+            # visible loses products only in some runs
+            for rep in range(3):
                 res = run(handle, q, semiring, False, "hash")
-                assert_parity(res, ref, semiring, ctx=f"kicks={kicks} md={md} phases={phases}")
-                counts = handle.bin_counts()
-                assert counts["hash_w"] > 0 and counts["hash_b"] > 0
+                assert_parity(res, ref, semiring, ctx=f"kicks={kicks} phases={phases} rep={rep}")
+            counts = handle.bin_counts()
+            assert counts["hash_w"] > 0 and counts["hash_b"] > 0
     finally:
         handle.set_option(_lib.OPT_PHASES, 1)
         handle.set_option(_lib.OPT_HASH_KICKS, 64)
-        handle.set_option(_lib.OPT_MASK_DRIVEN, 8)
-        handle.force("auto")
-
-
-@pytest.mark.parametrize("md", [0, 1, 8, 64])
-def test_triangle_count_mask_driven(handle, md):
-    """Triangle counting (R-MAT scale 14) with the hash rows' mask-driven
-    ranges at several ratios: the count and every entry equal the oracle's."""
-    p = synth.triangle_counting(scale=14, ef=16, seed=5)
-    ref = O.masked_spgemm(p["M"], p["A"], p["B"], "plus_pair_i64")
-    handle.set_option(_lib.OPT_MASK_DRIVEN, md)
-    try:
-        res = run(handle, p, "plus_pair_i64", False, "hash")
-        assert_parity(res, ref, "plus_pair_i64", ctx=f"md={md}")
-    finally:
-        handle.set_option(_lib.OPT_MASK_DRIVEN, 8)
         handle.force("auto")
 
 
