@@ -316,46 +316,42 @@ __host__ __device__ __forceinline__ long long words32(long long bits) { return (
 
 // Hash (mask-keyed) table: per slot a 32-bit key (the mask column; bit 31
 // marks the SET state where the semiring keeps one) and the slot's
-// accumulator.  Slots: 4 x nnz(m) (load factor 0.25, Sec. 5.3), at least 32,
-// or as many as the slab holds down to 2 x nnz(m) (load 0.5); any count, not
-// only powers of two (positions come from a multiply-high).  Returns 0 if
-// the row does not fit.
+// accumulator.  Slots: the power of two at or above 4 x nnz(m) (load factor
+// at most 0.25, Sec. 5.3), at least 32, halved while the slab is too small
+// and the load stays at most 0.5.  Returns 0 if the row does not fit.
 __host__ __device__ __forceinline__ long long hash_table_bytes(long long H, int acc) {
     return align8(4 * H) + H * acc;   // keys, then the (8-byte aligned) accumulators
 }
 __host__ __device__ __forceinline__ long long hash_slots(long long mnz, int acc, long long slab) {
+    // a power of two: 4 nnz(m) slots (load 1/4), halved toward load 1/2 to fit the slab
     if (mnz <= 0 || mnz > (1 << 24)) return 0;
-    long long h = 4 * mnz < 32 ? 32 : 4 * mnz;
-    const long long fit = (slab - 8) / (4 + acc);
-    if (h > fit) h = fit;
-    return h >= 2 * mnz ? h : 0;
+    long long h = 32;
+    while (h < 4 * mnz) h <<= 1;
+    while (h / 2 >= 2 * mnz && hash_table_bytes(h, acc) > slab) h >>= 1;
+    return hash_table_bytes(h, acc) <= slab ? h : 0;
 }
 
-// Two-choice (cuckoo) positions of key x in a table of H >= 32 slots: with
-// u = x * c (mod 2^32) and w = u * H (64 bits), p1 = the high word of w (a
-// multiply-high into [0, H)); the low word gives the second position,
-// p2 = p1 + 1 + (low >> sh) mod H, where sh makes the offset at most H - 2,
-// so p2 != p1.  Two multiplies per key.  Every key of a built table sits at
-// one of its two positions, so a lookup reads exactly two slots (Pagh and
-// Rodler's cuckoo hashing; parallel insertion by atomic exchange as in
-// Alcantara et al.'s GPU hash tables).
+// Two-choice (cuckoo) positions of key x in a table of H = 2^lg >= 32 slots,
+// from one multiply u = x * c (mod 2^32): p1 = the top lg bits of u, and
+// p2 = p1 xor (d | 1) with d the next lg bits of u, so p2 != p1 and either
+// position gives the other from the key alone (the partial-key form of
+// Fan et al.'s cuckoo filters).  Every key of a built table sits at one of its
+// two positions, so a lookup reads exactly two slots (Pagh and Rodler's
+// cuckoo hashing; parallel insertion by atomic exchange as in Alcantara et
+// al.'s GPU hash tables).
 struct CuckooHash {
-    unsigned c, H, sh;
+    unsigned c, H, s1, s2;   // s1 = 32 - lg, s2 = 32 - 2 lg (0 when 2 lg > 32)
     __device__ __forceinline__ void pos(unsigned x, unsigned &p1, unsigned &p2) const {
-        const unsigned long long w = (unsigned long long)(x * c) * H;
-        p1 = (unsigned)(w >> 32);
-        const unsigned t = p1 + 1u + ((unsigned)w >> sh);
-        p2 = t >= H ? t - H : t;
+        const unsigned u = x * c;
+        p1 = u >> s1;
+        p2 = p1 ^ (((u >> s2) & (H - 1u)) | 1u);
     }
-    __device__ __forceinline__ unsigned h1(unsigned x) const {
-        return (unsigned)(((unsigned long long)(x * c) * H) >> 32);
-    }
+    __device__ __forceinline__ unsigned h1(unsigned x) const { return (x * c) >> s1; }
 };
-// sh for a table of H slots: 32 - floor(log2(H - 1)).
-__host__ __device__ __forceinline__ unsigned cuckoo_shift(unsigned H) {
-    unsigned l = 0;
-    while ((2u << l) <= H - 1) ++l;
-    return 32u - l;
+__host__ __device__ __forceinline__ CuckooHash cuckoo_hash(unsigned c, unsigned H) {
+    unsigned lg = 0;
+    while ((1u << lg) < H) ++lg;
+    return CuckooHash{c, H, 32u - lg, 2 * lg < 32 ? 32u - 2 * lg : 0u};
 }
 // Multipliers of the first attempt and of the retry (odd constants).
 constexpr unsigned CUCKOO_A = 0x9E3779B1u, CUCKOO_B = 0xC2B2AE3Du;

@@ -124,11 +124,15 @@ struct TileSeg {
 #define MSG_LONG_SEG 64
 #endif
 constexpr int LONG_SEG = MSG_LONG_SEG;
+// Column of an empty product slot; below zero and, as a 32-bit key, neither
+// a column (< 2^31) nor the empty-slot word 2^32 - 1.
+constexpr int NO_PRODUCT = -2;
 
 // The walk of one range [s, e) by the whole warp, chunks of 128 entries
 // (4 loads per lane in flight), from chunk c0 in steps of cstep chunks.
-// With WSYNC every lane calls f for every slot (column -1: no product), so f
-// may use warp-wide votes; otherwise only lanes holding a product call it.
+// With WSYNC every lane calls f for every slot (column NO_PRODUCT: no
+// product), so f may use warp-wide votes; otherwise only lanes holding a
+// product call it.
 template <int SR, bool WSYNC = false, class F>
 __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
                                            const int *__restrict__ ici, const void *iv, F &f) {
@@ -141,7 +145,7 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
         for (int x = 0; x < 4; ++x) {
             // q0 < e < 2^31, so q stays below 2^32: 32-bit index arithmetic
             const unsigned q = (unsigned)q0 + (unsigned)(x * 32 + lane);
-            col[x] = -1;
+            col[x] = NO_PRODUCT;
             bv[x] = in_t{};
             if (q < (unsigned)e) {
                 col[x] = __ldg(ici + q);
@@ -229,7 +233,7 @@ __device__ __forceinline__ void enum_products(int o0, int o1, const int *__restr
             const int q0 = __shfl_sync(FULL, s, k0) + p0 - __shfl_sync(FULL, excl, k0);
             const int q1 = __shfl_sync(FULL, s, k1) + p1 - __shfl_sync(FULL, excl, k1);
             const in_t a0 = shfl_val<SR>(av, k0), a1 = shfl_val<SR>(av, k1);
-            int col0 = -1, col1 = -1;
+            int col0 = NO_PRODUCT, col1 = NO_PRODUCT;
             in_t b0{}, b1{};
             if (p0 < total) {
                 col0 = __ldg(ici + q0);
@@ -441,7 +445,7 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
         acc[h] = 0;
     }
     team.sync();
-    CuckooHash ch{CUCKOO_A, H, cuckoo_shift(H)};
+    CuckooHash ch = cuckoo_hash(CUCKOO_A, H);
     const int kicks = L.hash_kicks;
     bool linear = kicks <= 0;
     if (linear) {
@@ -472,15 +476,15 @@ __device__ __forceinline__ void row_hash(const DevProd &P, const RowCtx &c, cons
         return h;
     };
     if (!linear) {
-        // called on every lane for every product slot (j < 0: none), so the
+        // called on every lane for every product slot (NO_PRODUCT: none), so the
         // lookup runs without a branch around it
         auto ins = [&](int, in_t a, int j, in_t b) {
+            // NO_PRODUCT (2^32 - 2 as a key) equals neither a column nor an empty slot
             const unsigned x = (unsigned)j;
             unsigned p1, p2;
             ch.pos(x, p1, p2);
             const unsigned k1 = ld_vol(&key[p1]), k2 = ld_vol(&key[p2]);
-            const bool ok = j >= 0;
-            const bool f1 = ok & ((k1 & KMASK) == x), f2 = ok & ((k2 & KMASK) == x);
+            const bool f1 = (k1 & KMASK) == x, f2 = (k2 & KMASK) == x;
             if (f1 | f2) hit(f1 ? p1 : p2, f1 ? k1 : k2, a, b);
         };
         enum_products<SR, CTA, true, true>(c.a0, c.a1, P.a_ci, P.a_v, RowSeg{P.b_rp}, P.b_ci, P.b_v, ins);
