@@ -137,19 +137,20 @@ template <int SR, bool WSYNC = false, class F>
 __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
                                            const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
-    const int lane = lane_id();
-    for (long long q0 = s + 128LL * c0; q0 < e; q0 += 128LL * cstep) {
+    const unsigned lane = (unsigned)lane_id(), ue = (unsigned)e;
+    // unsigned 32-bit indices (e < 2^31, steps below 2^13: no wrap); the four
+    // loads of a chunk share one address with immediate offsets
+    for (unsigned q0 = (unsigned)s + 128u * (unsigned)c0 + lane; q0 - lane < ue; q0 += 128u * (unsigned)cstep) {
+        const int *cp = ici + q0;
         int col[4];
         in_t bv[4];
 #pragma unroll
         for (int x = 0; x < 4; ++x) {
-            // q0 < e < 2^31, so q stays below 2^32: 32-bit index arithmetic
-            const unsigned q = (unsigned)q0 + (unsigned)(x * 32 + lane);
             col[x] = NO_PRODUCT;
             bv[x] = in_t{};
-            if (q < (unsigned)e) {
-                col[x] = __ldg(ici + q);
-                bv[x] = load_val<SR>(iv, q);
+            if (q0 + 32u * x < ue) {
+                col[x] = __ldg(cp + 32 * x);
+                bv[x] = load_val<SR>(iv, q0 + 32u * x);
             }
         }
 #pragma unroll
