@@ -30,7 +30,8 @@ OPT_QTEAM_FLOPS = 11
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_SHAPE", 3: "ERR_UNSORTED", 4: "ERR_UNSUPPORTED", 5: "ERR_OOM",
           6: "ERR_OVERFLOW", 7: "ERR_CUDA", 8: "ERR_TIMEOUT"}
 KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "dot_w", "dot_b",
-              "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g", "heap_w", "heapdot_w", "cheap_w", "mca_q", "dot_q"]
+              "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g", "heap_w", "heapdot_w", "cheap_w", "mca_q", "dot_q",
+              "hash_l"]
 
 # Exported symbols that include/msgemm.h declares.
 EXPORTS = ["msgemm_create", "msgemm_set_stream", "msgemm_set_option", "msgemm_run", "msgemm_backward",

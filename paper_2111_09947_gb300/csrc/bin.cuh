@@ -31,6 +31,7 @@ __device__ __forceinline__ int pick_family(const Policy &pol, int fam, bool warp
     case F_HASH:
         if (warp && pol.slab[K_HASH_W] > 0 && hash_slots(mnz, acc, pol.slab[K_HASH_W])) return K_HASH_W;
         if (pol.slab[K_HASH_B] > 0 && hash_slots(mnz, acc, pol.slab[K_HASH_B])) return K_HASH_B;
+        if (pol.slab[K_HASH_L] > 0 && hash_slots(mnz, acc, pol.slab[K_HASH_L])) return K_HASH_L;
         return -1;
     case F_MCA:
         if (warp && pol.slab[K_MCA_W] > 0 && mca_bytes(mnz, acc, sb) <= pol.slab[K_MCA_W]) return K_MCA_W;

@@ -163,7 +163,7 @@ struct PScope {
 const char *kind_name(int k) {
     static const char *names[NKIND] = {"empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w",
                                        "mca_b", "dot_w", "dot_b", "chash_w", "chash_b", "cmsa_t", "cmsa_g", "msa_g",
-                                       "heap_w", "heapdot_w", "cheap_w", "mca_q", "dot_q"};
+                                       "heap_w", "heapdot_w", "cheap_w", "mca_q", "dot_q", "hash_l"};
     return (k >= 0 && k < NKIND) ? names[k] : "?";
 }
 
@@ -218,9 +218,11 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     const int acc = acc_bytes(sr);
     const int wslab = h->warp_slab;   // default 4.5 KB: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
     const int bslab = 32 * 1024;  // per CTA-row: 7 CTAs per SM
+    const int lslab = 96 * 1024;  // hash rows too long for bslab: 2 CTAs per SM
     const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
     p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
     p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;
+    p.slab[K_HASH_L] = lslab;
     const long long msaw = (msa_bytes(max_n, acc) + 15) & ~15LL;
     p.slab[K_MSA_W] = msaw <= 24 * 1024 ? (int)msaw : 0;
     p.slab[K_MSA_T] = p.slab[K_CMSA_T] = p.slab[K_CMSA_G] = p.slab[K_MSA_G] = tslab;
@@ -529,7 +531,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     };
     if (any_plain) {
         if (pl.pol.slab[K_MSA_W]) pl.kinds.push_back(K_MSA_W);
-        pl.kinds.insert(pl.kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_MCA_B});
+        pl.kinds.insert(pl.kinds.end(), {K_HASH_W, K_MCA_W, K_HASH_B, K_HASH_L, K_MCA_B});
         if (pl.pol.q_flops_max > 0) pl.kinds.push_back(K_MCA_Q);
         if (!pl.bd.empty() ||
             std::any_of(in.begin(), in.end(), [](const ProdIn &x) { return x.bt_rp != nullptr; }))

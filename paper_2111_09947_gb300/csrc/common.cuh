@@ -38,6 +38,7 @@ enum Kind : int {
     K_CHEAP_W,     // complemented: multiway merge, NInspect = 0
     K_MCA_Q,       // plain, tiny rows: MCA on an eight-lane team, mask row in registers
     K_DOT_Q,       // plain, tiny masks: pull on an eight-lane team, A_i* searched in global memory
+    K_HASH_L,      // Sec. 5.3 hash on one CTA with a large slab: mask rows too long for K_HASH_B
     NKIND
 };
 

@@ -1402,7 +1402,7 @@ __global__ void __launch_bounds__(256, 4) k_rows_b(const __grid_constant__ ProdS
         const long long r = L.ra.perm[off + x];
         const DevProd &P = prod_at(ps, row_prod(ps, L.ra.prod, r));
         const RowCtx c = row_ctx(P, r, L.ra);
-        if (KIND == K_HASH_B) row_hash<SR, true>(P, c, L, smem, scratch);
+        if (KIND == K_HASH_B || KIND == K_HASH_L) row_hash<SR, true>(P, c, L, smem, scratch);
         else if (KIND == K_MCA_B) row_mca<SR, true>(P, c, L, smem, scratch);
         else if (KIND == K_DOT_B) row_dot<SR, true>(P, c, L, smem, scratch);
         else if (KIND == K_CHASH_B) row_chash<SR, true>(P, c, L, smem);

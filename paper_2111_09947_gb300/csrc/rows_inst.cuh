@@ -67,6 +67,7 @@ cudaError_t MSG_CAT(launch_kind_, MSG_SUFFIX)(int kind, const ProdSet &ps, const
     case K_MCA_Q: return go<k_rows_q<MSG_SR>>(ps, L, th, sm, st, nsm);
     case K_DOT_Q: return go<k_rows_dq<MSG_SR>>(ps, L, th, sm, st, nsm);
     case K_HASH_B: return go<k_rows_b<MSG_SR, K_HASH_B>>(ps, L, th, sm, st, nsm);
+    case K_HASH_L: return go<k_rows_b<MSG_SR, K_HASH_L>>(ps, L, th, sm, st, nsm);
     case K_MCA_B: return go<k_rows_b<MSG_SR, K_MCA_B>>(ps, L, th, sm, st, nsm);
     case K_DOT_B: return go<k_rows_b<MSG_SR, K_DOT_B>>(ps, L, th, sm, st, nsm);
     case K_CHASH_B: return go<k_rows_b<MSG_SR, K_CHASH_B>>(ps, L, th, sm, st, nsm);

@@ -246,8 +246,9 @@ def test_hash_build_paths(handle, semiring, kicks):
     move limit at its default (64), at 1 (insertions run out often: the retry
     with the second hash pair and the linear fallback both run) and at 0
     (linear probing only).  Mask rows from 1 to 1500 entries put warp and CTA
-    rows at load factors from 0.25 up to 0.5; the gradient form (values at the
-    mask's slots) and the two-phase form go through the same lookups."""
+    rows (both slab sizes) at load factors from 1/8 up to 1/2; the gradient
+    form (values at the mask's slots) and the two-phase form go through the
+    same lookups."""
     rng = np.random.default_rng(500 + kicks)
     m, k, n = 600, 500, 40000
     mdeg = np.array([1, 7, 60, 140, 230, 287, 700, 1500])[np.arange(m) % 8]
@@ -271,6 +272,8 @@ def test_hash_build_paths(handle, semiring, kicks):
                 assert_parity(res, ref, semiring, ctx=f"kicks={kicks} phases={phases} rep={rep}")
             counts = handle.bin_counts()
             assert counts["hash_w"] > 0 and counts["hash_b"] > 0
+            if semiring == "plus_times_i64":   # 12-byte slots: the 1500-entry rows need the large slab
+                assert counts["hash_l"] > 0
     finally:
         handle.set_option(_lib.OPT_PHASES, 1)
         handle.set_option(_lib.OPT_HASH_KICKS, 64)
