@@ -1193,7 +1193,7 @@ struct Tuner {
         h->warp_slab = sbest;
         const long long gbest0 = h->grid_min_flops;
         long long gbest = gbest0;
-        for (long long g : {1LL << 18, 1LL << 20, 1LL << 22, 1LL << 62}) {
+        for (long long g : {1LL << 18, 1LL << 19, 1LL << 20, 1LL << 21, 1LL << 22, 1LL << 62}) {
             if (g == gbest0) continue;
             h->grid_min_flops = g;
             float t;
