@@ -3,6 +3,8 @@
 // MSG_SUFFIX defined, so the three semirings compile in parallel.
 #pragma once
 
+#include <mutex>
+
 #include "bin.cuh"
 #include "launch.h"
 #include "rows.cuh"
@@ -13,23 +15,38 @@ namespace {
 using RowKernel = void (*)(ProdSet, RowLaunch);
 
 // Grid of a persistent kernel: resident CTAs per SM x SMs.  The dynamic
-// shared-memory attribute and occupancy are cached per kernel.
+// shared-memory limit (a per-device attribute of the kernel, raised for any
+// size: static shared memory counts against the default 48 KB too) and the
+// occupancy of the last size asked are cached per kernel and device.
 template <RowKernel K>
 cudaError_t go(const ProdSet &ps, const RowLaunch &L, int threads, size_t smem, cudaStream_t st, int nsm) {
-    static size_t attr_set = 0;
-    static size_t occ_smem = ~size_t(0);
-    static int occ = 0;
-    if (smem > 48 * 1024 && smem > attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set = smem;
-    }
-    if (occ_smem != smem) {
-        int nb = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K, threads, smem);
-        if (e != cudaSuccess) return e;
-        occ = nb;
-        occ_smem = smem;
+    struct DevState {
+        size_t attr = 0, occ_smem = ~size_t(0);
+        int occ = 0;
+    };
+    static std::mutex mu;
+    static DevState cache[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        DevState spare;
+        DevState &d = (dev >= 0 && dev < 64) ? cache[dev] : spare;
+        if (smem > d.attr) {
+            e = cudaFuncSetAttribute(K, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            d.attr = smem;
+        }
+        if (d.occ_smem != smem) {
+            int nb = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, K, threads, smem);
+            if (e != cudaSuccess) return e;
+            d.occ = nb;
+            d.occ_smem = smem;
+        }
+        occ = d.occ;
     }
     if (occ < 1) return cudaErrorInvalidConfiguration;
     K<<<occ * nsm, threads, smem, st>>>(ps, L); g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
