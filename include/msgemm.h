@@ -99,8 +99,8 @@ typedef enum {
                                      0: never (one CTA walks all tiles of a row); needs the
                                      tile index (or a single tile) */
     MSGEMM_OPT_WARP_SLAB = 7,     /* value 1024..24576, a multiple of 16 (default 4608): shared
-                                     bytes per warp of the one-warp row kinds (hash, MCA, pull);
-                                     rows whose table does not fit go to the one-CTA kinds */
+                                     bytes per warp of the one-warp MCA and pull kinds; rows
+                                     whose arrays do not fit go to the one-CTA kinds */
     MSGEMM_OPT_GRID_MIN_FLOPS = 8, /* value >= 0 (default 2^20): plain-mask rows with at least
                                      this many push products, in products wider than one
                                      column tile, are processed as (row, tile) items over the
@@ -124,11 +124,15 @@ typedef enum {
                                      falls back to linear probing.  0 = linear probing only.
                                      The result never depends on it (tests use 0 and 1 to run
                                      every build path). */
-    MSGEMM_OPT_QTEAM_FLOPS = 11   /* value 0..2^20 (default 1024): plain rows with at most 8 mask
+    MSGEMM_OPT_QTEAM_FLOPS = 11,  /* value 0..2^20 (default 1024): plain rows with at most 8 mask
                                      entries and at most this many push products take the
                                      mask-compressed accumulator (Sec. 5.4) on a team of eight
                                      lanes (four rows per warp, the mask row and its accumulators
                                      in registers) -- under AUTO and when MCA is forced; 0 = never */
+    MSGEMM_OPT_HASH_SLAB = 12     /* value 1024..24576, a multiple of 16 (default 4608): shared
+                                     bytes per warp of the one-warp hash kinds (their table is a
+                                     power of two of 4-byte keys and accumulators); rows whose
+                                     table does not fit go to the one-CTA hash kinds */
 } msgemm_option;
 
 /* Input CSR matrix (device pointers, borrowed). */

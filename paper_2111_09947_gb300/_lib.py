@@ -27,6 +27,7 @@ OPT_FORCE_ACCUM, OPT_VALIDATE, OPT_DOT, OPT_PROFILE, OPT_TILE_INDEX, OPT_GRID, O
 OPT_PHASES = 9
 OPT_HASH_KICKS = 10
 OPT_QTEAM_FLOPS = 11
+OPT_HASH_SLAB = 12
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_SHAPE", 3: "ERR_UNSORTED", 4: "ERR_UNSUPPORTED", 5: "ERR_OOM",
           6: "ERR_OVERFLOW", 7: "ERR_CUDA", 8: "ERR_TIMEOUT"}
 KIND_NAMES = ["empty", "msa_w", "msa_t", "hash_w", "hash_b", "mca_w", "mca_b", "dot_w", "dot_b",

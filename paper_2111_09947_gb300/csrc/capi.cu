@@ -44,7 +44,8 @@ struct msgemm_handle {
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
     int q_flops_max = 1024;   // MSGEMM_OPT_QTEAM_FLOPS: K_MCA_Q rows (0: never)
-    int warp_slab = 4608;   // shared bytes per warp of the one-warp row kinds
+    int warp_slab = 4608;   // shared bytes per warp of the one-warp MCA and pull kinds
+    int hash_slab = 4608;   // shared bytes per warp of the one-warp hash kinds
     long long grid_min_flops = 1LL << 20;   // MSA_G: plain CTA rows with at least this push work
     int *last_kind_count = nullptr;
     unsigned char *last_kind = nullptr;
@@ -217,10 +218,12 @@ Policy make_policy(const msgemm_handle *h, msgemm_semiring sr, int max_n) {
     p.q_flops_max = h->q_flops_max;
     const int acc = acc_bytes(sr);
     const int wslab = h->warp_slab;   // default 4.5 KB: 8 warps x 4.5 KB = 36 KB per CTA, 6 CTAs per SM
+    const int hslab = h->hash_slab;
     const int bslab = 32 * 1024;  // per CTA-row: 7 CTAs per SM
     const int lslab = 96 * 1024;  // hash rows too long for bslab: 2 CTAs per SM
     const int tslab = std::min(h->smem_optin - 4096, 216 * 1024) & ~1023;
-    p.slab[K_HASH_W] = p.slab[K_MCA_W] = p.slab[K_DOT_W] = p.slab[K_CHASH_W] = wslab;
+    p.slab[K_MCA_W] = p.slab[K_DOT_W] = wslab;
+    p.slab[K_HASH_W] = p.slab[K_CHASH_W] = hslab;
     p.slab[K_HASH_B] = p.slab[K_MCA_B] = p.slab[K_DOT_B] = p.slab[K_CHASH_B] = bslab;
     p.slab[K_HASH_L] = lslab;
     const long long msaw = (msa_bytes(max_n, acc) + 15) & ~15LL;
@@ -955,6 +958,7 @@ struct Tuned {
     long long grid_min_flops = 1LL << 20;
     unsigned char pref[NCLASS][4];
     int q_flops_max = 1024;
+    int hash_slab = 4608;
 };
 
 Tuned current_tuned(const msgemm_handle *h) {
@@ -965,6 +969,7 @@ Tuned current_tuned(const msgemm_handle *h) {
     t.grid_min_flops = h->grid_min_flops;
     memcpy(t.pref, h->pref, sizeof t.pref);
     t.q_flops_max = h->q_flops_max;
+    t.hash_slab = h->hash_slab;
     return t;
 }
 
@@ -975,13 +980,15 @@ void apply_tuned(msgemm_handle *h, const Tuned &t) {
     h->grid_min_flops = t.grid_min_flops;
     memcpy(h->pref, t.pref, sizeof t.pref);
     h->q_flops_max = t.q_flops_max;
+    h->hash_slab = t.hash_slab;
 }
 
 // Cache file: a JSON object, one entry per line,
 //   "<device name>|<semiring>": {"warp_flops_max": W, "dot_ratio": D, "warp_slab": S, "grid_min_flops": G,
-//                                "pref": [[f,f,f,f], ...], "q_flops_max": Q}
+//                                "pref": [[f,f,f,f], ...], "q_flops_max": Q, "hash_slab": S2}
 // with NCLASS preference rows of accumulator families (msgemm_accumulator);
-// an entry without q_flops_max (written before it existed) keeps its default.
+// an entry without q_flops_max or hash_slab (written before they existed)
+// keeps their defaults.
 void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
     FILE *f = fopen(path, "r");
     if (!f) return;
@@ -1002,7 +1009,7 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ++c;
             }
         }
-        if (num.size() != 4 + NCLASS * 4 && num.size() != 5 + NCLASS * 4) continue;
+        if (num.size() < 4 + NCLASS * 4 || num.size() > 6 + NCLASS * 4) continue;
         Tuned t;
         if (num[0] < 0 || num[0] > 1e9 || !(num[1] > 0) || num[1] > 1e6) continue;
         if (num[2] < 1024 || num[2] > 24576 || (int)num[2] % 16) continue;
@@ -1018,10 +1025,15 @@ void read_tuned(const char *path, std::map<std::string, Tuned> &out) {
                 ok &= v >= F_AUTO && v <= F_HEAPDOT && v == (int)v;
                 t.pref[c][x] = (unsigned char)v;
             }
-        if (num.size() == 5 + NCLASS * 4) {
+        if (num.size() >= 5 + NCLASS * 4) {
             const double q = num[4 + NCLASS * 4];
             ok &= q >= 0 && q <= (1 << 20) && q == (int)q;
             t.q_flops_max = (int)q;
+        }
+        if (num.size() == 6 + NCLASS * 4) {
+            const double s = num[5 + NCLASS * 4];
+            ok &= s >= 1024 && s <= 24576 && s == (int)s && (int)s % 16 == 0;
+            t.hash_slab = (int)s;
         }
         if (ok) out[key] = t;
     }
@@ -1040,7 +1052,7 @@ bool write_tuned(const char *path, const std::map<std::string, Tuned> &m) {
                 kv.first.c_str(), t.warp_flops_max, (double)t.dot_ratio, t.warp_slab, t.grid_min_flops);
         for (int c = 0; c < NCLASS; ++c)
             fprintf(f, "%s[%d, %d, %d, %d]", c ? ", " : "", t.pref[c][0], t.pref[c][1], t.pref[c][2], t.pref[c][3]);
-        fprintf(f, "], \"q_flops_max\": %d}%s\n", t.q_flops_max, ++i < m.size() ? "," : "");
+        fprintf(f, "], \"q_flops_max\": %d, \"hash_slab\": %d}%s\n", t.q_flops_max, t.hash_slab, ++i < m.size() ? "," : "");
     }
     fprintf(f, "}\n");
     const bool ok = fclose(f) == 0;
@@ -1191,6 +1203,16 @@ struct Tuner {
             if (t < best * keep) { best = t; sbest = sl; }
         }
         h->warp_slab = sbest;
+        const int hbest0 = h->hash_slab;
+        int hbest = hbest0;
+        for (int sl : {3072, 4608, 6144, 9216, 12288}) {
+            if (sl == hbest0) continue;
+            h->hash_slab = sl;
+            float t;
+            CKS(measure(&t));
+            if (t < best * keep) { best = t; hbest = sl; }
+        }
+        h->hash_slab = hbest;
         const long long gbest0 = h->grid_min_flops;
         long long gbest = gbest0;
         for (long long g : {1LL << 18, 1LL << 19, 1LL << 20, 1LL << 21, 1LL << 22, 1LL << 62}) {
@@ -1277,6 +1299,10 @@ msgemm_status msgemm_set_option(msgemm_handle *h, msgemm_option opt, int64_t val
     case MSGEMM_OPT_WARP_SLAB:
         if (value < 1024 || value > 24576 || value % 16) return fail(h, MSGEMM_ERR_INVALID, "warp slab bytes");
         h->warp_slab = (int)value;
+        return MSGEMM_OK;
+    case MSGEMM_OPT_HASH_SLAB:
+        if (value < 1024 || value > 24576 || value % 16) return fail(h, MSGEMM_ERR_INVALID, "hash slab bytes");
+        h->hash_slab = (int)value;
         return MSGEMM_OK;
     case MSGEMM_OPT_GRID_MIN_FLOPS:
         if (value < 0) return fail(h, MSGEMM_ERR_INVALID, "grid flop bound must be >= 0");

@@ -149,6 +149,7 @@ def test_autotune_keeps_parity_and_writes_cache(batch, tmp_path):
     assert len(e["pref"]) == 16 and all(len(r) == 4 for r in e["pref"])
     assert e["warp_flops_max"] > 0 and e["dot_ratio"] > 0
     assert e["q_flops_max"] >= 0
+    assert 1024 <= e["hash_slab"] <= 24576 and e["hash_slab"] % 16 == 0
 
 
 def test_autotune_reads_cache(batch, tmp_path):
@@ -191,3 +192,31 @@ def test_autotune_cache_team_bound(batch, tmp_path):
     finally:
         h.close()
     assert counts["mca_q"] == 0 and counts["dot_q"] == 0
+
+
+@pytest.mark.parametrize("hash_slab", [1024, 12288])
+def test_autotune_cache_hash_slab(batch, tmp_path, hash_slab):
+    """A cached entry's hash slab is applied to the one-warp hash kind only:
+    hash first for every class; with 1 KB per warp the longer mask rows go to
+    the CTA hash kind, with 12 KB none do, and the MCA and pull warp kinds keep
+    their own slab."""
+    ps, devs, refs = batch
+    key = torch.cuda.get_device_name() + "|plus_times_f32"
+    entry = {"warp_flops_max": 65536, "dot_ratio": 1e6, "warp_slab": 4608, "grid_min_flops": 1 << 62,
+             "pref": [[2, 0, 0, 0]] * 16, "q_flops_max": 0, "hash_slab": hash_slab}
+    cache = tmp_path / "tune.json"
+    cache.write_text(json.dumps({key: entry}))
+    h = _lib.Handle()
+    try:
+        _lib.msgemm_autotune(h, [], [], [], "plus_times_f32", cache_path=cache)
+        outs = _run(h, devs, False)
+        counts = h.bin_counts()
+        for o, ref in zip(outs, refs):
+            assert_parity(o.trimmed(), ref, "plus_times_f32")
+    finally:
+        h.close()
+    assert counts["hash_w"] > 0
+    if hash_slab == 1024:
+        assert counts["hash_b"] > 0
+    else:
+        assert counts["hash_b"] == 0
