@@ -242,8 +242,9 @@ class Workload:
     mats: list of (M, A, B, complement) host products one step runs;
     kept: products kept by the masks per step; masked flops = 2 * kept."""
 
-    def __init__(self, name, semiring, config, mats, dtype):
+    def __init__(self, name, semiring, config, mats, dtype, pattern_b=False):
         self.name = name
+        self.pattern_b = pattern_b   # B goes to the device without values (every value 1)
         self.semiring = semiring
         self.config = dict(config, l2="GPU arm: flushed before every timed step (256 MiB write)")
         self.mats = mats
@@ -271,10 +272,10 @@ def build_workload(name, scale, seed, nprod=256):
         scale = scale or 20
         b = synth.bfs_step(scale=scale, ef=16, nsrc=512, seed=seed)
         cfg = {"workload": f"multi-source BFS step, complemented mask: C = !Visited .* (F A), plus-times int64; "
-                           f"A = R-MAT scale {scale} ef 16 symmetrised (values 1), F = level-2 frontier of 512 "
-                           "random sources with path counts", "n": b["B"].nrows, "nnz_F": b["A"].nnz,
-               "nnz_visited": b["M"].nnz, "nnz_A": b["B"].nnz}
-        return Workload(name, "plus_times_i64", cfg, [(b["M"], b["A"], b["B"], True)], "int64")
+                           f"A = R-MAT scale {scale} ef 16 symmetrised (values 1, passed as a pattern operand), "
+                           "F = level-2 frontier of 512 random sources with path counts", "n": b["B"].nrows,
+               "nnz_F": b["A"].nnz, "nnz_visited": b["M"].nnz, "nnz_A": b["B"].nnz}
+        return Workload(name, "plus_times_i64", cfg, [(b["M"], b["A"], b["B"], True)], "int64", pattern_b=True)
     if name == "batched":
         ps = synth.batched_problems(nprod=nprod, seed=seed)
         cfg = {"workload": f"{nprod} independent fp32 products in one call: n log-uniform in [2^10, 2^16], A/B R-MAT "
@@ -309,7 +310,7 @@ class DeviceRun:
                     d.values = None
                 cache[key] = d
             return cache[key]
-        self.prods = [(dv(M, False), dv(A, keep), dv(B, keep), c) for (M, A, B, c) in wl.mats]
+        self.prods = [(dv(M, False), dv(A, keep), dv(B, keep and not wl.pattern_b), c) for (M, A, B, c) in wl.mats]
         self.G = None
         self.plan = None
         self.allreduce = None

@@ -17,8 +17,11 @@
  *    the column indices are strictly ascending (sorted, no duplicates);
  *    nnz < 2^31.  Input pointers are DEVICE pointers, borrowed for the call.
  *  - Values: float for MSGEMM_PLUS_TIMES_F32, int64_t for the two int64
- *    semirings.  PLUS_PAIR ignores input values (they may be NULL).  Mask
- *    values are never read.
+ *    semirings.  PLUS_PAIR ignores input values (they may be NULL).  Under
+ *    the plus-times semirings, NULL values make A or B of a masked product a
+ *    pattern operand: every stored value is 1 (a 0/1 adjacency, as in the
+ *    BFS step, needs no value array).  The gradients (msgemm_backward) need
+ *    the values.  Mask values are never read.
  *  - Shapes: M is m x n, A is m x k, B is k x n; any of m, n, k may be 0.
  *  - Every call is asynchronous on the handle's stream and returns as soon as
  *    its work is enqueued, except where a call says it synchronises.  Errors
@@ -141,7 +144,7 @@ typedef struct {
     int64_t nnz;                 /* == rowptr[nrows]; must be < 2^31 */
     const int32_t *rowptr;       /* nrows + 1 entries */
     const int32_t *colidx;       /* nnz entries, strictly ascending per row */
-    const void *values;          /* nnz entries, or NULL (plus-pair, masks) */
+    const void *values;          /* nnz entries, or NULL (plus-pair, masks, pattern operands) */
 } msgemm_csr;
 
 /* Output CSR matrix.  The library fills every field; the arrays come from the

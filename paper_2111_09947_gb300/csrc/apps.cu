@@ -126,12 +126,6 @@ __global__ void __launch_bounds__(256) k_filter_write(const int *rp, const int *
     }
 }
 
-template <class T>
-__global__ void __launch_bounds__(256) k_fill(T *p, long long n, T v) {
-    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        p[e] = v;
-}
-
 // p[e] = e: the position of every entry, carried through a transpose as its
 // value so that the transpose's entries can later be filled by a gather.
 __global__ void __launch_bounds__(256) k_iota(int *p, long long n) {
@@ -197,11 +191,6 @@ cudaError_t launch_filter_write(const int *rp, const int *ci, int nrows, const l
     k_filter_write<<<blocks_for((long long)nrows * 32, nsm, 16), 256, 0, st>>>(rp, ci, nrows, sup, thr, nrp, nci, nsup);
     return counted(cudaGetLastError());
 }
-cudaError_t launch_fill_i64(long long *p, long long n, long long v, cudaStream_t st, int nsm) {
-    if (n == 0) return cudaSuccess;
-    k_fill<long long><<<blocks_for(n, nsm, 16), 256, 0, st>>>(p, n, v);
-    return counted(cudaGetLastError());
-}
 cudaError_t launch_iota_i32(int *p, long long n, cudaStream_t st, int nsm) {
     if (n == 0) return cudaSuccess;
     k_iota<<<blocks_for(n, nsm, 16), 256, 0, st>>>(p, n);
@@ -210,11 +199,6 @@ cudaError_t launch_iota_i32(int *p, long long n, cudaStream_t st, int nsm) {
 cudaError_t launch_gather_f32(const int *perm, const float *src, long long n, float *dst, cudaStream_t st, int nsm) {
     if (n == 0) return cudaSuccess;
     k_gather_f32<<<blocks_for(n, nsm, 16), 256, 0, st>>>(perm, src, n, dst);
-    return counted(cudaGetLastError());
-}
-cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t st, int nsm) {
-    if (n == 0) return cudaSuccess;
-    k_fill<float><<<blocks_for(n, nsm, 16), 256, 0, st>>>(p, n, v);
     return counted(cudaGetLastError());
 }
 

@@ -443,7 +443,7 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
             if (!want_bt(in[p])) continue;
             dp[p].bt_rp = pl.bt_rp_all + pl.bd[q].co;
             dp[p].bt_ci = pl.bt_ci;
-            dp[p].bt_v = in_bytes(sr) ? pl.bt_v : nullptr;
+            dp[p].bt_v = in_bytes(sr) && pl.bd[q].v ? pl.bt_v : nullptr;   // none for a pattern B
             ++q;
         }
     }
@@ -940,10 +940,11 @@ msgemm_status alloc_out(msgemm_handle *h, const msgemm_csr *M, int comp, msgemm_
 msgemm_status check_product(msgemm_handle *h, const msgemm_csr *M, const msgemm_csr *A, const msgemm_csr *B,
                             msgemm_semiring sr) {
     if (sr < MSGEMM_PLUS_TIMES_F32 || sr > MSGEMM_PLUS_PAIR_I64) return fail(h, MSGEMM_ERR_INVALID, "unknown semiring");
-    const bool v = sr != MSGEMM_PLUS_PAIR_I64;
+    // values may be NULL: plus-pair never reads them, and under plus-times a
+    // NULL value array makes A or B a pattern operand (every stored value 1)
     CKS(check_csr(h, M, "M", false));
-    CKS(check_csr(h, A, "A", v));
-    CKS(check_csr(h, B, "B", v));
+    CKS(check_csr(h, A, "A", false));
+    CKS(check_csr(h, B, "B", false));
     if (M->nrows != A->nrows || A->ncols != B->nrows || M->ncols != B->ncols)
         return fail(h, MSGEMM_ERR_SHAPE, "shapes do not chain: M %dx%d, A %dx%d, B %dx%d", M->nrows, M->ncols, A->nrows,
                     A->ncols, B->nrows, B->ncols);
@@ -1647,10 +1648,8 @@ msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *so
             for (void *p : v) dev_free(h, p);
         }
     } guard{h, owned};
-    // A with int64 ones (forward), and A^T with fp32 ones, rows sorted
-    // (backward right operand; its transpose, A with fp32 ones, serves pull rows)
-    long long *a1 = static_cast<long long *>(take(sizeof(long long) * (size_t)std::max(nnz, 1LL)));
-    float *f1 = static_cast<float *>(take(sizeof(float) * (size_t)std::max(nnz, 1LL)));
+    // A (forward) and A^T with rows sorted (backward right operand; its
+    // transpose, A, serves pull rows) as pattern operands: every value 1
     int *at_rp = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
     int *at_cur = static_cast<int *>(take(sizeof(int) * ((size_t)n + 1)));
     int *at_ci = static_cast<int *>(take(sizeof(int) * (size_t)std::max(nnz, 1LL)));
@@ -1659,18 +1658,16 @@ msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *so
     int *vrp = static_cast<int *>(take(sizeof(int) * ((size_t)nsrc + 1)));
     int *vcnt = static_cast<int *>(take(sizeof(int) * ((size_t)nsrc + 1)));
     long long *vtb = static_cast<long long *>(take(sizeof(long long) * ((size_t)nsrc / STILE + 4)));
-    if (!a1 || !f1 || !at_rp || !at_cur || !at_ci || !tb || !bm || !vrp || !vcnt || !vtb)
+    if (!at_rp || !at_cur || !at_ci || !tb || !bm || !vrp || !vcnt || !vtb)
         return fail(h, MSGEMM_ERR_OOM, "bc workspace allocation failed");
-    CK(launch_fill_i64(a1, nnz, 1, st, h->nsm));
-    CK(launch_fill_f32(f1, nnz, 1.0f, st, h->nsm));
     CK(launch_col_counts(A->colidx, nnz, n, at_cur, st, h->nsm));
     CK(launch_excl_scan_int(at_cur, n, at_rp, tb, st, h->nsm));
     CK(cudaMemcpyAsync(at_cur, at_rp, sizeof(int) * ((size_t)n + 1), cudaMemcpyDeviceToDevice, st));
     CK(launch_transpose_fill(A->rowptr, A->colidx, nullptr, 0, n, n, at_cur, at_ci, nullptr, nullptr, st, h->nsm));
     CK(launch_segsort(at_rp, at_ci, nullptr, 0, n, at_cur, st, h->nsm));
     CK(cudaMemsetAsync(bm, 0, sizeof(unsigned) * (size_t)(nsrc * wpr), st));
-    const msgemm_csr Aone{n, n, nnz, A->rowptr, A->colidx, a1};
-    const msgemm_csr AtOne{n, n, nnz, at_rp, at_ci, f1};
+    const msgemm_csr Aone{n, n, nnz, A->rowptr, A->colidx, nullptr};
+    const msgemm_csr AtOne{n, n, nnz, at_rp, at_ci, nullptr};
 
     // ---- forward: level 0 = the sources, level d + 1 = !visited .* (level d A)
     struct Level {
@@ -1735,7 +1732,7 @@ msgemm_status msgemm_bc(msgemm_handle *h, const msgemm_csr *A, const int32_t *so
         const msgemm_csr Wx{nsrc, n, L.nnz, L.rp, L.ci, W};
         std::vector<ProdIn> in(1);
         in[0].M = &Mx; in[0].A = &Wx; in[0].B = &AtOne; in[0].comp = 0;
-        in[0].bt_rp = A->rowptr; in[0].bt_ci = A->colidx; in[0].bt_v = f1;
+        in[0].bt_rp = A->rowptr; in[0].bt_ci = A->colidx; in[0].bt_v = nullptr;
         in[0].aligned_out = Tp;
         if (P.nnz > 0) CKS(run_pipeline(h, in, MSGEMM_PLUS_TIMES_F32, false, false));
         CK(launch_bc_accum(P.ci, P.sigma, Tp, P.nnz, centrality, st, h->nsm));

@@ -242,7 +242,9 @@ template <> struct Sr<MSGEMM_PLUS_PAIR_I64> {
 template <int SR>
 __device__ __forceinline__ typename Sr<SR>::in_t load_val(const void *base, long long idx) {
     if constexpr (Sr<SR>::vals) {
-        return __ldg(static_cast<const typename Sr<SR>::in_t *>(base) + idx);
+        // a pattern operand (no value array) has every stored value 1
+        using in_t = typename Sr<SR>::in_t;
+        return base ? __ldg(static_cast<const in_t *>(base) + idx) : in_t(1);
     } else {
         return typename Sr<SR>::in_t{};
     }

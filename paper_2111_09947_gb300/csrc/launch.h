@@ -101,8 +101,6 @@ cudaError_t launch_filter_counts(const int *rp, const int *ci, int nrows, const 
                                  cudaStream_t, int nsm);
 cudaError_t launch_filter_write(const int *rp, const int *ci, int nrows, const long long *sup, long long thr,
                                 const int *nrp, int *nci, long long *nsup, cudaStream_t, int nsm);
-cudaError_t launch_fill_i64(long long *p, long long n, long long v, cudaStream_t, int nsm);
-cudaError_t launch_fill_f32(float *p, long long n, float v, cudaStream_t, int nsm);
 cudaError_t launch_iota_i32(int *p, long long n, cudaStream_t, int nsm);
 cudaError_t launch_gather_f32(const int *perm, const float *src, long long n, float *dst, cudaStream_t, int nsm);
 

@@ -738,7 +738,7 @@ __global__ void __launch_bounds__(256) k_transpose_fill_multi(const BtDesc *d, i
         for (int t = s + lane; t < e; t += 32) {
             const int pos = atomicAdd(&cursor[b.co + b.ci[t]], 1);
             tci[pos] = i;
-            if (VB) static_cast<V *>(tv)[pos] = static_cast<const V *>(b.v)[t];
+            if (VB && b.v) static_cast<V *>(tv)[pos] = static_cast<const V *>(b.v)[t];   // none for a pattern B
         }
     }
 }

@@ -570,8 +570,12 @@ __device__ __forceinline__ void row_dot(const DevProd &P, const RowCtx &c, const
     unsigned *sb = reinterpret_cast<unsigned *>(reinterpret_cast<unsigned char *>(acc) + align8((long long)mnz * sizeof(acc_t)));
     // the row A_i* (columns and values), in flight while the arrays clear
     stage_async<4, CTA>(acol, P.a_ci + c.a0, anz);
-    if constexpr (Sr<SR>::vals)
-        stage_async<(int)sizeof(in_t), CTA>(aval, static_cast<const in_t *>(P.a_v) + c.a0, anz);
+    if constexpr (Sr<SR>::vals) {
+        if (P.a_v)
+            stage_async<(int)sizeof(in_t), CTA>(aval, static_cast<const in_t *>(P.a_v) + c.a0, anz);
+        else   // a pattern operand: every value 1
+            for (int q = team.tid(); q < anz; q += team.size()) aval[q] = in_t(1);
+    }
     for (int q = team.tid(); q < mnz; q += team.size()) acc[q] = 0;
     if constexpr (SrSizes<SR>::setbits)
         for (int w = team.tid(); w < (int)words32(mnz); w += team.size()) sb[w] = 0;

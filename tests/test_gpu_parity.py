@@ -92,6 +92,33 @@ def test_random_complement(handle, semiring, force):
         assert_parity(res, ref, semiring, ctx=f"shape {s} force {force}")
 
 
+@pytest.mark.parametrize("semiring", ["plus_times_f32", "plus_times_i64"])
+@pytest.mark.parametrize("which", ["A", "B", "AB"])
+@pytest.mark.parametrize("force", ["auto", "msa", "hash", "mca", "dot", "heap"])
+def test_pattern_operands(handle, semiring, which, force):
+    """Under plus-times an operand passed without values is a pattern: every
+    stored value is 1 (the oracle gets explicit ones).  Plain and
+    complemented masks; the pull kind reads B^T built without values."""
+    one = {"plus_times_f32": np.float32, "plus_times_i64": np.int64}[semiring]
+    for s in (1, 2, 3, 4, 8):
+        m, k, n, da, db, dm = SHAPES[s]
+        p = synth.random_problem(m, k, n, min(da, max(k, 1)), min(db, max(n, 1)), min(dm, max(n, 1)), 3900 + s,
+                                 GEN[semiring])
+        q = dict(p)
+        for x in which:
+            q[x] = p[x].with_values(np.ones(p[x].nnz, dtype=one))
+        for comp in ((False, True) if force in ("auto", "msa", "hash") else (False,)):
+            ref = O.masked_spgemm(q["M"], q["A"], q["B"], semiring, complement=comp,
+                                  method=O.ESC if comp else O.MERGE)
+            d = to_dev(p, semiring)
+            for x in which:
+                d[x].values = None
+            handle.force(force)
+            res = _lib.msgemm_run(handle, d["M"], d["A"], d["B"], semiring, comp).trimmed()
+            handle.sync_status()
+            assert_parity(res, ref, semiring, ctx=f"shape {s} {which} complement={comp}")
+
+
 @pytest.mark.parametrize("complement", [False, True])
 @pytest.mark.parametrize("force", ["auto", "msa", "hash", "mca", "dot"])
 def test_int64_wide_values_wrap(handle, complement, force):
