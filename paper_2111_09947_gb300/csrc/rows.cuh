@@ -133,9 +133,9 @@ constexpr int NO_PRODUCT = -2;
 // With WSYNC every lane calls f for every slot (column NO_PRODUCT: no
 // product), so f may use warp-wide votes; otherwise only lanes holding a
 // product call it.
-template <int SR, bool WSYNC = false, class F>
-__device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
-                                           const int *__restrict__ ici, const void *iv, F &f) {
+template <int SR, bool WSYNC, bool PAT, class F>
+__device__ __forceinline__ void walk_range_v(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
+                                             const int *__restrict__ ici, const void *iv, F &f) {
     using in_t = typename Sr<SR>::in_t;
     const unsigned lane = (unsigned)lane_id(), ue = (unsigned)e;
     // unsigned 32-bit indices (e < 2^31, steps below 2^13: no wrap); the four
@@ -150,13 +150,23 @@ __device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s
             bv[x] = in_t{};
             if (q0 + 32u * x < ue) {
                 col[x] = __ldg(cp + 32 * x);
-                bv[x] = load_val<SR>(iv, q0 + 32u * x);
+                if constexpr (Sr<SR>::vals)
+                    bv[x] = PAT ? in_t(1) : __ldg(static_cast<const in_t *>(iv) + (q0 + 32u * x));
             }
         }
 #pragma unroll
         for (int x = 0; x < 4; ++x)
             if (WSYNC || col[x] >= 0) f(t, a, col[x], bv[x]);
     }
+}
+
+// The walk, with the pattern test (no value array: every value 1) taken once
+// per range instead of per entry.
+template <int SR, bool WSYNC = false, class F>
+__device__ __forceinline__ void walk_range(int t, typename Sr<SR>::in_t a, int s, int e, int c0, int cstep,
+                                           const int *__restrict__ ici, const void *iv, F &f) {
+    if (!Sr<SR>::vals || iv) walk_range_v<SR, WSYNC, false>(t, a, s, e, c0, cstep, ici, iv, f);
+    else walk_range_v<SR, WSYNC, true>(t, a, s, e, c0, cstep, ici, iv, f);
 }
 
 // CTA teams: ranges of BIG_SEG or more entries (hub rows of B) are not walked
