@@ -152,18 +152,22 @@ def push_products(A, B) -> int:
     return int(bl[A.colidx].sum())
 
 
-def q_min_bytes(M, A, B, nnz_c, vb_in, vb_out, complement=False) -> int:
-    """Compulsory bytes (read A, B, M once, write C once)."""
+def q_min_bytes(M, A, B, nnz_c, vb_in, vb_out, complement=False, vb_b=None) -> int:
+    """Compulsory bytes (read A, B, M once, write C once); vb_b = value bytes
+    of B (0 for a pattern operand), by default vb_in."""
+    vb_b = vb_in if vb_b is None else vb_b
     q = 4 * (A.nrows + 1) + A.nnz * (4 + vb_in)
-    q += 4 * (B.nrows + 1) + B.nnz * (4 + vb_in)
+    q += 4 * (B.nrows + 1) + B.nnz * (4 + vb_b)
     q += 4 * (M.nrows + 1) + 4 * M.nnz
     q += 4 * (M.nrows + 1) + nnz_c * (4 + vb_out)
     return int(q)
 
 
-def kernel_bytes(kinds, kind_id, M, A, B, C_rp, vb_in, vb_out) -> int:
+def kernel_bytes(kinds, kind_id, M, A, B, C_rp, vb_in, vb_out, vb_b=None) -> int:
     """Compulsory bytes of the rows one accumulator kernel processes: their
-    rows of A and M, the distinct rows of B they touch, their output."""
+    rows of A and M, the distinct rows of B they touch (vb_b value bytes per
+    entry: 0 for a pattern operand, by default vb_in), their output."""
+    vb_b = vb_in if vb_b is None else vb_b
     rows = np.nonzero(kinds == kind_id)[0]
     if len(rows) == 0:
         return 0
@@ -176,7 +180,7 @@ def kernel_bytes(kinds, kind_id, M, A, B, C_rp, vb_in, vb_out) -> int:
     rowmask = np.repeat(sel, anz)
     ks = np.unique(A.colidx[rowmask])
     bl = np.diff(B.rowptr).astype(np.int64)
-    q += int((8 + bl[ks] * (4 + vb_in)).sum())
+    q += int((8 + bl[ks] * (4 + vb_b)).sum())
     return q
 
 
@@ -633,7 +637,7 @@ def roofline_of(_lib, wl, meas):
     vb_in, vb_out = VB[wl.semiring]
     r, _ = meas["run"].step()
     C_rp = r.rowptr.cpu().numpy()
-    kb = kernel_bytes(meas["kinds"], kind_ids[dom], M, A, B, C_rp, vb_in, vb_out)
+    kb = kernel_bytes(meas["kinds"], kind_ids[dom], M, A, B, C_rp, vb_in, vb_out, 0 if wl.pattern_b else vb_in)
     achieved = kb / (dom_ms * 1e-3) / 1e9
     prof = profile_entry(dom, wl.name)
     roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 2), "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -691,7 +695,8 @@ def form_summary(wl, meas):
     if len(wl.mats) == 1:
         M, A, B, comp = wl.mats[0]
         vb_in, vb_out = VB[wl.semiring]
-        d["hbm_min_gbs"] = round(q_min_bytes(M, A, B, wl.nnz_c, vb_in, vb_out) / (ms * 1e-3) / 1e9, 2)
+        d["hbm_min_gbs"] = round(q_min_bytes(M, A, B, wl.nnz_c, vb_in, vb_out, vb_b=0 if wl.pattern_b else None)
+                                 / (ms * 1e-3) / 1e9, 2)
         d["push_products"] = push_products(A, B)
     if meas["per_phase"]:
         d["phase_ms"] = {n: round(statistics.mean(v), 4) for n, v in meas["per_phase"].items()}
