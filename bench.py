@@ -655,6 +655,14 @@ def roofline_of(_lib, wl, meas):
     smem = {"bound": "smem", "kernel": dom, "achieved": round(lookups, 2), "peak": round(speak, 1),
             "unit": "G shared accesses/s", "frac": round(lookups / speak, 5), "push_products_per_launch": prods,
             "peak_source": f"{SMS} SMs x 32 lanes x {clk:.0f} MHz (one conflict-free wavefront per SM per clock)"}
+    # the committed full-set capture of the same kernel: shared-memory
+    # wavefronts actually issued (bank conflicts included) per SM and clock,
+    # and the busy share of the L1/shared data pipe
+    if prof.get("smem_wavefronts_per_launch") and prof.get("smem_duration_ns"):
+        wps = prof["smem_wavefronts_per_launch"] / (prof["smem_duration_ns"] * 1e-9)
+        smem["ncu_wavefronts_per_sm_clock"] = round(wps / (SMS * clk * 1e6), 3)
+    if prof.get("l1tex_throughput_pct") is not None:
+        smem["ncu_l1tex_throughput_pct"] = prof["l1tex_throughput_pct"]
     return roof, smem
 
 

@@ -27,6 +27,9 @@ def test_q_min_and_kernel_bytes():
         (8 + np.diff(B.rowptr)[ks] * 8).sum()
     assert kb == want
     assert bench.kernel_bytes(kinds, 5, M, A, B, crp, 4, 4) == 0
+    # a pattern B (no value array) reads no value bytes of B
+    assert bench.q_min_bytes(M, A, B, 10, 4, 4, vb_b=0) == q - B.nnz * 4
+    assert bench.kernel_bytes(kinds, 3, M, A, B, crp, 4, 4, 0) == want - (np.diff(B.rowptr)[ks] * 4).sum()
 
 
 def test_oracle_sample_rate_runs():
