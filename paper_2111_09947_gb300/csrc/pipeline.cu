@@ -727,18 +727,42 @@ __global__ void __launch_bounds__(256) k_transpose_fill_multi(const BtDesc *d, i
                                                               int *tci, void *tv, const int *gate) {
     if (gate && *gate == 0) return;
     using V = typename std::conditional<VB == 4, unsigned, unsigned long long>::type;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, grp = lane >> 3, gl = lane & 7;
     const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long r = gw; r < rows; r += nw) {
-        const int q = bt_of(d, Q, r, true);
-        const BtDesc &b = d[q];
-        const int i = (int)(r - b.ro);
-        const int s = b.rp[i], e = b.rp[i + 1];
-        for (int t = s + lane; t < e; t += 32) {
+    // four rows per warp at a time: a row of at most eight entries is
+    // scattered by its group of eight lanes, one entry per lane, so the four
+    // rows' cursor atomics are in flight together; longer rows then take the
+    // whole warp
+    for (long long r0 = 4 * gw; r0 < rows; r0 += 4 * nw) {
+        const long long r = r0 + grp;
+        int q = 0, i = 0, s = 0, e = 0;
+        if (r < rows) {
+            q = bt_of(d, Q, r, true);
+            i = (int)(r - d[q].ro);
+            s = d[q].rp[i];
+            e = d[q].rp[i + 1];
+        }
+        const bool lng = e - s > 8;
+        if (!lng && s + gl < e) {
+            const BtDesc &b = d[q];
+            const int t = s + gl;
             const int pos = atomicAdd(&cursor[b.co + b.ci[t]], 1);
             tci[pos] = i;
             if (VB && b.v) static_cast<V *>(tv)[pos] = static_cast<const V *>(b.v)[t];   // none for a pattern B
+        }
+        unsigned todo = __ballot_sync(FULL, lng && gl == 0);
+        while (todo) {
+            const int u = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int qu = __shfl_sync(FULL, q, u), iu = __shfl_sync(FULL, i, u);
+            const int su = __shfl_sync(FULL, s, u), eu = __shfl_sync(FULL, e, u);
+            const BtDesc &b = d[qu];
+            for (int t = su + lane; t < eu; t += 32) {
+                const int pos = atomicAdd(&cursor[b.co + b.ci[t]], 1);
+                tci[pos] = iu;
+                if (VB && b.v) static_cast<V *>(tv)[pos] = static_cast<const V *>(b.v)[t];
+            }
         }
     }
 }
@@ -754,7 +778,7 @@ cudaError_t launch_bt_counts_multi(const BtDesc *d, int Q, long long total_nnz, 
 cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, int vbytes, int *cursor, int *tci,
                                  void *tv, const int *gate, cudaStream_t st, int nsm) {
     if (total_rows == 0) return cudaSuccess;
-    const int g = grid_cap((total_rows + 7) / 8, nsm, 16);
+    const int g = grid_cap((total_rows + 31) / 32, nsm, 16);
     if (vbytes == 4) { k_transpose_fill_multi<4><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     else if (vbytes == 8) { k_transpose_fill_multi<8><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, tv, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
     else { k_transpose_fill_multi<0><<<g, 256, 0, st>>>(d, Q, total_rows, cursor, tci, nullptr, gate); g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
