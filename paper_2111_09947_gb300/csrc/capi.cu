@@ -473,14 +473,14 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
         for (int p = 0; p < P; ++p) {
             if (dp[p].n <= T) continue;
             pl.nts[p] = (dp[p].n + T - 1) / T;
-            need += (long long)carve_size<int>((size_t)in[p].B->nrows * (pl.nts[p] + 1));
+            need += (long long)carve_size<int>((size_t)in[p].B->nrows * pl.nts[p] * 2);
         }
         if (h->tile_index && need <= h->tile_index_budget) {
             CKS(grow(h, h->tix, (size_t)need + 256));
             Carver ct(h->tix.p);
             for (int p = 0; p < P; ++p) {
                 if (!pl.nts[p]) continue;
-                pl.tpos[p] = ct.take<int>((size_t)in[p].B->nrows * (pl.nts[p] + 1));
+                pl.tpos[p] = ct.take<int>((size_t)in[p].B->nrows * pl.nts[p] * 2);
                 dp[p].tpos = pl.tpos[p];
                 dp[p].tstride = in[p].B->nrows;   // tile-major planes
             }

@@ -76,7 +76,7 @@ struct DevProd {
     long long abase;                          // first cursor slot (stored entries of A before this product)
     long long tmp0;                           // first temporary-output slot of this product (plain mask)
     const int *tpos;                          // tile index of B, tile-major planes, or null
-    int tstride;                              // plane length (rows of B): row c, boundary t at tpos[t * tstride + c]
+    int tstride;                              // plane length (rows of B): row c, tile t at int2 tpos[t * tstride + c]
     int *c_rp, *c_ci; void *c_v; long long *c_nnz;  // outputs
 };
 

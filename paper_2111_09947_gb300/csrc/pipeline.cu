@@ -790,11 +790,11 @@ cudaError_t launch_bt_fill_multi(const BtDesc *d, int Q, long long total_rows, i
 namespace msg {
 
 // ------------------------------------------------------------ tile index
-// For every row k of B and column tile t (width T): tpos[t * nrows + k] =
-// first position of row k whose column is >= t * T (the row end if none), so
-// the part of row k inside tile t is [tpos[t * nrows + k], tpos[(t + 1) *
-// nrows + k]).  Tile-major planes: kernels that sweep one tile for many rows
-// read one plane.  One thread per row, the warp's 32 rows consecutive, planes
+// For every row k of B and column tile t (width T), the part of row k inside
+// tile t as a pair of positions, (first position whose column is >= t * T,
+// the same for t + 1; the row end if none), at tpos[t * nrows + k] (int2):
+// one aligned 8-byte load gives both bounds.  Tile-major planes: kernels that
+// sweep one tile for many rows read one plane.  One thread per row, the warp's 32 rows consecutive, planes
 // in order: each lane advances a cursor through its (sorted) row -- linearly
 // for short rows, by binary search from the cursor for long ones -- and the
 // warp writes 32 consecutive slots of a plane at a time.
@@ -809,6 +809,7 @@ __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *c
         int pos = valid ? rp[k] : 0;
         const int e = valid ? rp[k + 1] : 0;
         const bool longrow = e - pos > 64;
+        int prev = pos;
         for (int t = 0; t <= nt; ++t) {
             if (valid) {
                 if (t == nt) {
@@ -826,7 +827,8 @@ __global__ void __launch_bounds__(256) k_tile_bounds(const int *rp, const int *c
                         pos = lo;
                     }
                 }
-                tpos[(long long)t * nrows + k] = pos;
+                if (t > 0) reinterpret_cast<int2 *>(tpos)[(long long)(t - 1) * nrows + k] = make_int2(prev, pos);
+                prev = pos;
             }
         }
     }

@@ -101,12 +101,12 @@ struct RowSeg {
     }
 };
 struct TileSeg {
-    const int *tpos;   // row c, tile t: [tpos[t * stride + c], tpos[(t + 1) * stride + c])
+    const int *tpos;   // row c, tile t: [x, y) of the int2 at tpos[t * stride + c]
     int stride, tile;
     __device__ __forceinline__ void operator()(int c, int &s, int &e) const {
-        const int *p = tpos + (long long)tile * stride + c;
-        s = __ldg(p);
-        e = __ldg(p + stride);
+        const int2 v = __ldg(reinterpret_cast<const int2 *>(tpos) + (long long)tile * stride + c);
+        s = v.x;
+        e = v.y;
     }
 };
 
