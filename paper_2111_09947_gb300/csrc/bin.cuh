@@ -64,7 +64,7 @@ __device__ __forceinline__ int choose_kind(const Policy &pol, long long flops, i
         // heavy rows: the grid of (row, tile) items when the output is dense
         // (its room is then all open columns, at most 4x the bound)
         const int heavy = (pol.grid > 0 && index_ok && (n + pol.tileT[1] - 1) / pol.tileT[1] <= GRID_MAX_TILES &&
-                           (pol.grid == 2 || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
+                           (pol.grid == 2 || pol.comp_grid_all || 4 * bound >= open)) ? K_CMSA_G : K_CMSA_T;
         if (pol.force == F_MSA) return heavy;
         if (pol.force == F_HEAP || pol.force == F_HEAPDOT)   // NInspect is 0 under a complement
             return anz <= HEAP_MAX_ITERS ? K_CHEAP_W : heavy;

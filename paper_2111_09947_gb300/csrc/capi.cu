@@ -40,6 +40,10 @@ struct msgemm_handle {
     int phases = 1;   // 1: one-phase, 2: symbolic + numeric (MSGEMM_OPT_PHASES)
     int hash_kicks = CUCKOO_KICKS;   // MSGEMM_OPT_HASH_KICKS
     long long tile_index_budget = 4LL << 30;   // bytes
+    // complemented rows on the grid take a room of all their open columns;
+    // when those rooms of every complemented row fit this, sparse rows take
+    // the grid too instead of one CTA walking all their tiles
+    long long comp_room_budget = 16LL << 30;   // bytes
     unsigned char pref[NCLASS][4];
     float dot_ratio = 2.0f;
     int warp_flops_max = 65536;
@@ -349,6 +353,12 @@ msgemm_status plan_prepare(msgemm_handle *h, std::vector<ProdIn> &in, msgemm_sem
     if (R >= (1LL << 31)) return fail(h, MSGEMM_ERR_OVERFLOW, "total rows >= 2^31");
     pl.pol = make_policy(h, sr, max_n);
     if (two_phase) pl.pol.grid = 0;   // grid pieces need a temporary's room
+    {
+        double comp_room = 0.0;   // bytes if every complemented row took its full room
+        for (int p = 0; p < P; ++p)
+            if (in[p].comp) comp_room += (double)in[p].M->nrows * in[p].M->ncols * (4 + out_bytes(sr));
+        pl.pol.comp_grid_all = comp_room <= (double)h->comp_room_budget;
+    }
 
     // ---- per-row workspace
     const size_t rows_bytes = carve_size<long long>(R) * 3 + carve_size<int>(R) * 3 + carve_size<unsigned char>(R) +

@@ -168,6 +168,7 @@ struct Policy {
     int slab[NKIND];              // bytes per warp (_W) or per CTA (_B, _T); 0 = disabled
     int tileT[2];                 // MSA_T tile width for [plain, complemented]
     int grid;                     // grid kinds: 0 off, 1 by the rules below, 2 for every heavy row
+    int comp_grid_all;            // grid 1: every heavy complemented row (the full rooms fit), not only dense ones
     long long grid_min_flops;     // MSA_G: CTA rows with at least this much push work (grid 1)
     int grid_cap;                 // MSA_G: most rows per call
     unsigned char pref[NCLASS][4];  // families in preference order (F_AUTO = end)
